@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the restarted reflected-Halpern PDHG hot path (cuPDLPx, arXiv 2507.14051).
+
+One step = one solve on the device from the all-zero start (Section 4) to relative KKT
+`--tol` (default 1e-8) or `--max-iter` iterations: the iteration loop S1-S9 (primal step,
+SpMV A x, dual step, fixed-point residual, SpMV A^T y, restart test + PID, reflected Halpern
+update, KKT test) as one CUDA graph.  Setup (S0: validation, transpose, binning,
+preconditioning, power iteration) runs once in lp_create and is reported as `setup_ms`
+and inside `time_to_tol_s` and the end-to-end number.
+
+Workload (default): the MIPLIB-relaxation-shaped LP, m = 50k, n = 100k, nnz ~ 600k, seeded
+synthetic data with a planted optimum (paper_2507_14051_b300.gen.miplib_like, seed = rank).
+Timing: W untimed warm-up solves, then K solves each bracketed by CUDA events on the solve
+stream, L2 flushed (256 MiB write) between solves outside the events, barrier +
+synchronize around the timed region, MAX over ranks.  value = total PDHG iterations / time.
+
+--impl reference times the FP64 CPU oracle (the method's plain reference implementation) on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-8 rel KKT, PDHG iter/s, SpMV+update HBM GB/s vs peak"
+FP64_NOMINAL_GOPS = 625.0  # 1.25 TFLOP/s FP64 per GPU (nominal) / 2 flops per DFMA
+FP64_MEASURED_GOPS = 474.0  # DFMA/DADD/DMUL issue rate measured by a register-only loop on a B300
+KERNEL_SOURCES = ("paper_2507_14051_b300/csrc/iterate.cu", "paper_2507_14051_b300/csrc/device.cuh")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="miplib", choices=["miplib", "mcf", "small"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--max-iter", type=int, default=100000)
+    ap.add_argument("--kernel-iters", type=int, default=300)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tol-run-max-iter", type=int, default=0,
+                    help="> 0: one extra untimed solve with this cap to report time to tol")
+    return ap.parse_args()
+
+
+def make_workload(name: str, seed: int):
+    from paper_2507_14051_b300 import gen
+    if name == "miplib":
+        return gen.miplib_like(seed)
+    if name == "mcf":
+        return gen.multicommodity(seed)
+    return gen.small_lp(seed)
+
+
+def workload_name(name: str, lp) -> str:
+    base = {"miplib": "MIPLIB-relaxation-shaped LP (power-law rows 1..2000, mixed scales)",
+            "mcf": "multicommodity flow LP (200k nodes, 1M arcs, 4 commodities)",
+            "small": "small LP (2 % density, N(0,1))"}[name]
+    return f"{base}, m={lp.m}, n={lp.n}, nnz={lp.nnz}, FP64"
+
+
+def kernel_work(lp):
+    """Algorithmic bytes and FP64 operations of one launch of each iteration kernel.
+    Bytes (what the method must move, FP64 values, 32-bit indices):
+      row kernel:    12 nnz (A values + columns) + 8 (m+1) row offsets + 8 n gathered xhat
+                     + 56 m (y, y0, l_c, u_c, y read; y, yhat written)
+      column kernel: 12 nnz + 8 (n+1) + 8 m gathered yhat + 56 n (x, x0, c, l_v, u_v read;
+                     x, xhat written)
+    FP64 operations (fma/add/mul issued by the kernel's arithmetic): one fma per nonzero plus
+    17 per row (row kernel) or 12 per column (column kernel)."""
+    m, n, nnz = lp.m, lp.n, lp.nnz
+    return {"k1_rows": (12 * nnz + 8 * (m + 1) + 8 * n + 56 * m, nnz + 17 * m),
+            "k2_cols": (12 * nnz + 8 * (n + 1) + 8 * m + 56 * n, nnz + 12 * n)}
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernels."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = data.get(kernel, {})
+    if ent.get("source_digest") != source_digest() or ent.get("workload") != workload:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.file.flush()
+        with open(self.file.name) as f:
+            rows = [r.strip().split(", ") for r in f if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(lp, eta, seconds, workload):
+    """The FP64 oracle as it stands, single-threaded, on the first iterations of the same
+    solve (same preconditioning, explicit step size): iterations per second."""
+    import oracle
+    probe = 20
+    t0 = time.perf_counter()
+    oracle.solve(lp, tol=0.0, max_iter=probe, eta=eta)
+    per = (time.perf_counter() - t0) / probe
+    iters = max(probe, int(seconds / max(per, 1e-9)))
+    t0 = time.perf_counter()
+    out = oracle.solve(lp, tol=0.0, max_iter=iters, eta=eta)
+    dt = time.perf_counter() - t0
+    return {"value": out["iters"] / dt, "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {out['iters']} iterations from zero of the {workload} "
+                      f"(tolerance off, oracle's own preconditioning included), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, _, world = _env()
+    if rank != 0:
+        return 0
+    import oracle
+    lp = make_workload(args.workload, 0)
+    wl = workload_name(args.workload, lp)
+    probe = 10
+    t0 = time.perf_counter()
+    eta = oracle.solve(lp, tol=0.0, max_iter=1)["eta"]
+    oracle.solve(lp, tol=0.0, max_iter=probe, eta=eta)
+    per = (time.perf_counter() - t0) / probe
+    # each step: a bounded sample of about 8 s of the same solve
+    step_iters = max(5, int(8.0 / max(per, 1e-9)))
+    for _ in range(args.warmup):
+        oracle.solve(lp, tol=args.tol, max_iter=min(step_iters, 3), eta=eta)
+    total_it, total_s = 0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out = oracle.solve(lp, tol=args.tol, max_iter=step_iters, eta=eta)
+        total_s += time.perf_counter() - t0
+        total_it += out["iters"]
+    value = total_it / total_s
+    sample = f"{step_iters} iterations per step from zero of the {wl}, single-threaded FP64 oracle"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl, "tol": args.tol, "step_iters": step_iters},
+            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _env():
+    from paper_2507_14051_b300.dist import env_rank_world
+    return env_rank_world()
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2507_14051_b300 as lpx
+    from paper_2507_14051_b300.dist import instance_seeds, reduce_elapsed_and_work
+
+    rank, local, world = _env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seed = instance_seeds(rank, world)[0]
+    lp = make_workload(args.workload, seed)
+    wl = workload_name(args.workload, lp)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+
+    t0 = time.perf_counter()
+    solver = lpx.Solver(lp)
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    prm = solver.params
+    unroll = int(prm.unroll)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    for _ in range(args.warmup):
+        solver.solve(args.tol, args.max_iter, sp)
+        lpx.lp_get(solver.h)
+    torch.cuda.synchronize()
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, total_iters, launches = 0.0, 0, 0
+    statuses, kkts = [], []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.solve(args.tol, args.max_iter, sp)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        st, kkt, it = lpx.lp_get(solver.h)
+        statuses.append(st)
+        kkts.append(kkt.tolist())
+        total_iters += it
+        launches += 3 + math.ceil(it / unroll) * (2 * unroll + 1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed_s, all_iters = reduce_elapsed_and_work(total_ms / 1e3, total_iters)
+    value = all_iters / elapsed_s
+    info = lpx.lp_get_info(solver.h)
+
+    # live kernel durations (same kernels, launched one by one with events) for the roofline
+    kt = lpx.lp_time_kernels(solver.h, args.kernel_iters, sp)
+    work = kernel_work(lp)
+    hbm_peak, peak_src = load_peaks()
+    per = {"k1_rows": kt[0], "k2_cols": kt[1]}
+    dom = max(per, key=per.get)
+    bytes_, ops = work[dom]
+    ms = per[dom]
+    gbs = bytes_ / (ms * 1e-3) / 1e9
+    gops = ops / (ms * 1e-3) / 1e9
+    f_hbm, f_alu = gbs / hbm_peak, gops / FP64_NOMINAL_GOPS
+    traffic = measured_traffic(dom, wl)
+    if f_alu > f_hbm:
+        roof = {"bound": "alu", "achieved": gops, "peak": FP64_NOMINAL_GOPS, "unit": "FP64 Gop/s",
+                "frac": f_alu, "traffic": traffic, "kernel": dom}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm,
+                "traffic": traffic, "kernel": dom}
+    roof.update({"peak_source": f"HBM {peak_src} copy {hbm_peak} GB/s; FP64 nominal {FP64_NOMINAL_GOPS} Gop/s "
+                                f"(measured issue rate {FP64_MEASURED_GOPS})",
+                 "kernels": {k: {"ms": per[k], "alg_bytes": work[k][0], "fp64_ops": work[k][1],
+                                 "GB/s": work[k][0] / (per[k] * 1e-3) / 1e9,
+                                 "frac_hbm": work[k][0] / (per[k] * 1e-3) / 1e9 / hbm_peak,
+                                 "frac_fp64": work[k][1] / (per[k] * 1e-3) / 1e9 / FP64_NOMINAL_GOPS}
+                             for k in per},
+                 "timing": f"mean of {int(kt[2])} launches each, CUDA events on the solve stream"})
+
+    # end to end through the C ABI with host buffers: create (H2D inside) + solve + get (D2H)
+    arrs = [np.ascontiguousarray(lp.row_ptr, np.int64), np.ascontiguousarray(lp.col_idx, np.int32),
+            np.ascontiguousarray(lp.val, np.float64)] + \
+           [np.ascontiguousarray(getattr(lp, k), np.float64) for k in ("c", "l_c", "u_c", "l_v", "u_v")]
+    pinned = [torch.from_numpy(a).pin_memory() for a in arrs]
+    h2d = sum(int(a.nbytes) for a in arrs)
+    xo = torch.zeros(lp.n, dtype=torch.float64).pin_memory()
+    yo = torch.zeros(lp.m, dtype=torch.float64).pin_memory()
+    d2h = 8 * (lp.m + lp.n) + 8 * 4 + 8 + 4
+    e2e_s, e2e_it = 0.0, 0
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = lpx.lp_create(lp.m, lp.n, lp.nnz, *pinned, where=lpx.LP_HOST)
+        lpx.lp_solve(h, args.tol, args.max_iter, sp)
+        st, kkt, it = lpx.lp_get(h, xo, yo)
+        e2e_s += time.perf_counter() - t0
+        e2e_it += it
+        lpx.lp_destroy(h)
+    e2e_s, e2e_it = reduce_elapsed_and_work(e2e_s, e2e_it)
+    e2e_value = e2e_it / e2e_s if e2e_s > 0 else None
+
+    tol_run = None
+    if args.tol_run_max_iter > 0:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.solve(args.tol, args.tol_run_max_iter, sp)
+        e1.record(stream)
+        e1.synchronize()
+        st, kkt, it = lpx.lp_get(solver.h)
+        tol_run = {"status": st, "iters": it, "solve_s": e0.elapsed_time(e1) / 1e3,
+                   "time_to_tol_s": (e0.elapsed_time(e1) + setup_ms) / 1e3 if st == 1 else None,
+                   "rel_kkt": kkt.tolist()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(lp, float(info[0]), args.cpu_seconds, wl)
+
+    if rank == 0:
+        solved = all(s == 1 for s in statuses)
+        line = {
+            "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl, "instances": f"one per GPU, seed = rank", "tol": args.tol,
+                       "max_iter": args.max_iter, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"independent instances x{world}",
+                       "params": {k: getattr(prm, k) for k, _ in prm._fields_}},
+            "status_per_step": statuses, "rel_kkt_last": kkts[-1], "iters_per_step": total_iters / args.steps,
+            "time_to_tol_s": (setup_ms / 1e3 + elapsed_s / args.steps) if solved else None,
+            "setup_ms": setup_ms, "eta": float(info[0]), "restarts_last": int(info[2]),
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+                    "includes": "lp_create from pinned host arrays (validation, transpose, binning, "
+                                "preconditioning, power iteration, H2D) + lp_solve + lp_get to host"},
+            "gpu_launches": launches, "clocks": clocks, "tol_run": tol_run,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

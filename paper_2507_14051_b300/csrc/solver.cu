@@ -1,0 +1,769 @@
+// Host runtime of the solver and its C ABI (include/lp.h).
+//
+// lp_create: validation -> row/column length binning and one permutation of rows and columns
+// (rows of similar length contiguous, longest first) -> CSR of A and of A^T with 32-bit offsets
+// -> upload -> diagonal preconditioning on the device -> power iteration on the device ->
+// capture of the iteration loop as one CUDA graph (a conditional while node whose body is
+// `unroll` pairs of the two iteration kernels plus the kernel that sets the loop condition).
+// lp_solve: resets the scalar state, runs the first primal step, launches the graph.
+// lp_get: waits, un-permutes and un-scales the last PDHG output.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lp.h"
+#include "kernels.cuh"
+
+using namespace pdhg;
+
+namespace {
+
+thread_local std::string g_err;
+
+lp_status fail(lp_status code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      lp_status code_ = (e_ == cudaErrorMemoryAllocation) ? LP_ERR_OUT_OF_MEMORY : LP_ERR_CUDA; \
+      return fail(code_, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    }                                                                                    \
+  } while (0)
+
+// Blocks for a binned kernel: at least two warp tasks per warp where there is enough work (the
+// block reduction is a fixed cost per block), every SM busy where there is work for it, and
+// no more blocks than fit on the device at once.
+int grid_for_tasks(int64_t warp_tasks, int num_sms, int max_blocks) {
+  int64_t g = (warp_tasks + 2 * kWarps - 1) / (2 * kWarps);
+  int64_t spread = (warp_tasks + kWarps - 1) / kWarps;
+  if (spread > num_sms) spread = num_sms;
+  if (g < spread) g = spread;
+  if (g > max_blocks) g = max_blocks;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+int grid_for(int64_t work, int per_block, int cap) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+int length_class(int64_t len) {
+  if (len <= 1) return 0;
+  int c = 0;
+  while ((int64_t(1) << c) < len) ++c;
+  return c;  // ceil(log2(len))
+}
+
+}  // namespace
+
+struct lp_solver {
+  int device = 0;
+  int num_sms = 148;
+  int32_t m = 0, n = 0;
+  int64_t nnz = 0;
+  lp_params prm{};
+  std::vector<int32_t> row_perm, col_perm;  // permuted index -> original index
+  BinTable binsA{}, binsT{};
+  int gridA = 1, gridT = 1, gridV = 1, max_grid = 1;
+  // device storage
+  int32_t *rpA = nullptr, *ciA = nullptr, *rpT = nullptr, *ciT = nullptr;
+  double *valA = nullptr, *valT = nullptr;
+  int32_t *d_row_perm = nullptr, *d_col_perm = nullptr;
+  double *c = nullptr, *lv = nullptr, *uv = nullptr, *inv_dc = nullptr, *dc = nullptr;
+  double *lc = nullptr, *uc = nullptr, *inv_dr = nullptr, *dr = nullptr;
+  double *x = nullptr, *x0 = nullptr, *xh0 = nullptr, *xh1 = nullptr, *aty = nullptr, *aty0 = nullptr;
+  double *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
+  double* out_buf = nullptr;
+  double* partials = nullptr;
+  double* trace = nullptr;
+  int64_t trace_cap = 0;
+  Ctl* ctl = nullptr;
+  PwCtl* pw = nullptr;
+  double* pinned = nullptr;  // 8 doubles of pinned host memory for scalar read-back
+  double lu_norm = 0.0, c_norm = 0.0;
+  double eta = 0.0, norm_A = 0.0;
+  int64_t pw_iters = 0;
+  bool power_valid = false;  // norm_A holds the power-iteration estimate for the current settings
+  bool solved = false;
+  cudaStream_t last_stream = nullptr;
+  cudaStream_t setup_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_unroll = 0;
+  std::vector<void*> allocations;
+
+  template <class T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, (count > 0 ? count : 1) * sizeof(T));
+    if (e == cudaSuccess) allocations.push_back(v);
+    *p = static_cast<T*>(v);
+    return e;
+  }
+  ~lp_solver() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (void* p : allocations) cudaFree(p);
+    if (pinned) cudaFreeHost(pinned);
+    if (setup_stream) cudaStreamDestroy(setup_stream);
+  }
+};
+
+namespace {
+
+lp_status check_params(const lp_params& p) {
+  if (!(p.gamma >= 0.0 && p.gamma <= 1.0)) return fail(LP_ERR_INVALID_ARG, "gamma must be in [0, 1]");
+  if (!(p.beta_sufficient >= 0.0) || !(p.beta_necessary >= 0.0) || !(p.beta_artificial >= 0.0))
+    return fail(LP_ERR_INVALID_ARG, "restart betas must be >= 0");
+  if (!std::isfinite(p.k_p) || !std::isfinite(p.k_i) || !std::isfinite(p.k_d))
+    return fail(LP_ERR_INVALID_ARG, "PID gains must be finite");
+  if (!std::isfinite(p.eta)) return fail(LP_ERR_INVALID_ARG, "eta must be finite");
+  if (!(p.omega0 > 0.0) || !std::isfinite(p.omega0)) return fail(LP_ERR_INVALID_ARG, "omega0 must be > 0");
+  if (p.check_every < 1) return fail(LP_ERR_INVALID_ARG, "check_every must be >= 1");
+  if (!(p.power_tol >= 0.0) || p.power_max_iter < 1) return fail(LP_ERR_INVALID_ARG, "bad power iteration settings");
+  if (p.ruiz_iters < 0 || p.ruiz_iters > 1000) return fail(LP_ERR_INVALID_ARG, "ruiz_iters must be in [0, 1000]");
+  if (p.pc_enabled && !(p.pc_alpha >= 0.0 && p.pc_alpha <= 2.0)) return fail(LP_ERR_INVALID_ARG, "pc_alpha must be in [0, 2]");
+  if (p.trace_cap < 0) return fail(LP_ERR_INVALID_ARG, "trace_cap must be >= 0");
+  if (p.unroll < 1 || p.unroll > 64) return fail(LP_ERR_INVALID_ARG, "unroll must be in [1, 64]");
+  if (p.lane_target < 1 || p.lane_target > 64) return fail(LP_ERR_INVALID_ARG, "lane_target must be in [1, 64]");
+  return LP_OK;
+}
+
+// Schedule over rows already sorted by decreasing length class: the leading rows longer than
+// kCtaRowMin go one per CTA; each remaining class becomes a bin with G lanes per row (about
+// lane_target entries per lane and pass) and R rows per warp task (about kTileNnz entries).
+BinTable make_bins(const std::vector<int32_t>& rp, int lane_target) {
+  BinTable bt{};
+  const int32_t rows = (int32_t)rp.size() - 1;
+  int32_t r = 0;
+  while (r < rows && rp[r + 1] - rp[r] > kCtaRowMin) ++r;
+  bt.cta_rows = r;
+  int32_t task = 0;
+  while (r < rows) {
+    const int cls = length_class(rp[r + 1] - rp[r]);
+    int32_t e = r + 1;
+    while (e < rows && length_class(rp[e + 1] - rp[e]) == cls) ++e;
+    const int64_t lc = int64_t(1) << cls;
+    int G = 1;
+    while (G < 32 && int64_t(G) * 2 * lane_target <= lc) G *= 2;
+    int64_t rr = kTileNnz / lc;
+    const int R = (int)(rr < 1 ? 1 : (rr > 32 ? 32 : rr));
+    Bin& b = bt.bin[bt.nbins++];
+    b.row0 = r;
+    b.row1 = e;
+    b.lanes = G;
+    b.rows_per_tile = R;
+    b.task0 = task;
+    task += (e - r + R - 1) / R;
+    r = e;
+  }
+  bt.ntasks = task;
+  return bt;
+}
+
+// Stable order of indices by decreasing length class (counting sort over 32 classes).
+void order_by_class(const std::vector<int64_t>& len, std::vector<int32_t>& perm) {
+  const int32_t N = (int32_t)len.size();
+  std::vector<int64_t> count(33, 0);
+  for (int32_t i = 0; i < N; ++i) count[length_class(len[i])]++;
+  std::vector<int64_t> start(33, 0);
+  int64_t acc = 0;
+  for (int c = 32; c >= 0; --c) {
+    start[c] = acc;
+    acc += count[c];
+  }
+  perm.assign(N, 0);
+  for (int32_t i = 0; i < N; ++i) perm[start[length_class(len[i])]++] = i;
+}
+
+lp_status validate(int32_t m, int32_t n, int64_t nnz, const int64_t* rp, const int32_t* ci,
+                   const double* val, const double* c, const double* lc, const double* uc,
+                   const double* lv, const double* uv) {
+  if (rp[0] != 0) return fail(LP_ERR_INVALID_INPUT, "row_ptr[0] must be 0");
+  for (int32_t i = 0; i < m; ++i)
+    if (rp[i + 1] < rp[i]) return fail(LP_ERR_INVALID_INPUT, "row_ptr must be non-decreasing (row " + std::to_string(i) + ")");
+  if (rp[m] != nnz) return fail(LP_ERR_INVALID_INPUT, "row_ptr[m] must equal nnz");
+  for (int64_t p = 0; p < nnz; ++p) {
+    if (ci[p] < 0 || ci[p] >= n) return fail(LP_ERR_INVALID_INPUT, "column index out of range at entry " + std::to_string(p));
+    if (!std::isfinite(val[p])) return fail(LP_ERR_INVALID_INPUT, "non-finite matrix entry at " + std::to_string(p));
+  }
+  for (int32_t j = 0; j < n; ++j) {
+    if (!std::isfinite(c[j])) return fail(LP_ERR_INVALID_INPUT, "non-finite objective entry " + std::to_string(j));
+    if (std::isnan(lv[j]) || std::isnan(uv[j]) || lv[j] > uv[j] || lv[j] == INFINITY || uv[j] == -INFINITY)
+      return fail(LP_ERR_INVALID_INPUT, "bad variable bounds at column " + std::to_string(j));
+  }
+  for (int32_t i = 0; i < m; ++i) {
+    if (std::isnan(lc[i]) || std::isnan(uc[i]) || lc[i] > uc[i] || lc[i] == INFINITY || uc[i] == -INFINITY)
+      return fail(LP_ERR_INVALID_INPUT, "bad row bounds at row " + std::to_string(i));
+  }
+  return LP_OK;
+}
+
+void fill_args(const lp_solver* h, RowArgs& ra, ColArgs& ca) {
+  ra = RowArgs{};
+  ra.rp = h->rpA; ra.ci = h->ciA; ra.val = h->valA;
+  ra.xh0 = h->xh0; ra.xh1 = h->xh1;
+  ra.y = h->y; ra.y0 = h->y0; ra.yh = h->yh; ra.ax = h->ax; ra.ax0 = h->ax0; ra.axh = h->axh;
+  ra.lc = h->lc; ra.uc = h->uc; ra.inv_dr = h->inv_dr;
+  ra.ctl = h->ctl; ra.partials = h->partials; ra.trace = h->trace_cap > 0 ? h->trace : nullptr;
+  ra.bins = h->binsA;
+  ca = ColArgs{};
+  ca.rp = h->rpT; ca.ci = h->ciT; ca.val = h->valT; ca.yh = h->yh;
+  ca.xh0 = h->xh0; ca.xh1 = h->xh1;
+  ca.x = h->x; ca.x0 = h->x0; ca.aty = h->aty; ca.aty0 = h->aty0;
+  ca.c = h->c; ca.lv = h->lv; ca.uv = h->uv; ca.inv_dc = h->inv_dc;
+  ca.ctl = h->ctl; ca.partials = h->partials; ca.bins = h->binsT;
+}
+
+lp_status build_graph(lp_solver* h) {
+  if (h->exec) {
+    cudaGraphExecDestroy(h->exec);
+    h->exec = nullptr;
+  }
+  if (h->graph) {
+    cudaGraphDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  RowArgs ra{};
+  ColArgs ca{};
+  fill_args(h, ra, ca);
+  CK(cudaGraphCreate(&h->graph, 0));
+  cudaGraphConditionalHandle cond;
+  CK(cudaGraphConditionalHandleCreate(&cond, h->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t s = h->setup_stream;
+  CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  for (int u = 0; u < h->prm.unroll; ++u) {
+    k1_rows<<<h->gridA, kThreads, 0, s>>>(ra);
+    k2_cols<<<h->gridT, kThreads, 0, s>>>(ca);
+  }
+  k_set_cond<<<1, 1, 0, s>>>(cond, h->ctl, h->prm.unroll);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &captured);
+  if (e != cudaSuccess) return fail(LP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+  h->graph_unroll = h->prm.unroll;
+  return LP_OK;
+}
+
+lp_status run_power_iteration(lp_solver* h) {
+  cudaStream_t s = h->setup_stream;
+  h->pw_iters = 0;
+  if (h->m == 0 || h->n == 0) {
+    h->norm_A = 0.0;
+    return LP_OK;
+  }
+  double* u = h->x;  // scratch: the iterate buffers are free until the first solve
+  double* w = h->y;
+  k_pw_start<<<h->gridV, kThreads, 0, s>>>(h->n, h->d_col_perm, h->prm.power_seed, u, h->pw, h->partials);
+  CK(cudaGetLastError());
+  double lam = 0.0, prev = 0.0;
+  int64_t it;
+  for (it = 1; it <= h->prm.power_max_iter; ++it) {
+    k_pw_rows<<<h->gridA, kThreads, 0, s>>>(h->rpA, h->ciA, h->valA, u, w, h->binsA, h->pw, h->partials);
+    CK(cudaMemcpyAsync(h->pinned, &h->pw->lambda, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    lam = h->pinned[0];
+    if (lam == 0.0) break;
+    k_pw_cols<<<h->gridT, kThreads, 0, s>>>(h->rpT, h->ciT, h->valT, w, u, h->binsT, h->pw, h->partials);
+    if (it > 1 && std::fabs(lam - prev) <= h->prm.power_tol * lam) break;
+    prev = lam;
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  h->pw_iters = it > h->prm.power_max_iter ? h->prm.power_max_iter : it;
+  h->norm_A = std::sqrt(lam);
+  return LP_OK;
+}
+
+lp_status set_eta(lp_solver* h) {
+  if (h->prm.eta > 0.0) {
+    h->eta = h->prm.eta;
+    return LP_OK;
+  }
+  if (!h->power_valid) {
+    lp_status st = run_power_iteration(h);
+    if (st != LP_OK) return st;
+    h->power_valid = true;
+  }
+  h->eta = h->norm_A > 0.0 ? 0.998 / h->norm_A : 1.0;
+  return LP_OK;
+}
+
+lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int64_t* rp,
+                      const int32_t* ci, const double* val, const double* c, const double* lc,
+                      const double* uc, const double* lv, const double* uv) {
+  h->m = m;
+  h->n = n;
+  h->nnz = nnz;
+  CK(cudaGetDevice(&h->device));
+  CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  CK(cudaStreamCreateWithFlags(&h->setup_stream, cudaStreamNonBlocking));
+  CK(cudaMallocHost(&h->pinned, 8 * sizeof(double)));
+
+  // KKT denominators on the original data (Section 4): ||c||_2 and ||(L, U)||_2 over the finite
+  // bound entries, summed in natural order.
+  double c2 = 0.0, lu2 = 0.0;
+  for (int32_t j = 0; j < n; ++j) c2 += c[j] * c[j];
+  for (int32_t i = 0; i < m; ++i) {
+    if (std::isfinite(lc[i])) lu2 += lc[i] * lc[i];
+    if (std::isfinite(uc[i])) lu2 += uc[i] * uc[i];
+  }
+  h->c_norm = std::sqrt(c2);
+  h->lu_norm = std::sqrt(lu2);
+
+  // ---- permutation by length class ----
+  std::vector<int64_t> rlen(m), clen(n, 0);
+  for (int32_t i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
+  for (int64_t p = 0; p < nnz; ++p) clen[ci[p]]++;
+  order_by_class(rlen, h->row_perm);
+  order_by_class(clen, h->col_perm);
+  std::vector<int32_t> col_inv(n);
+  for (int32_t j = 0; j < n; ++j) col_inv[h->col_perm[j]] = j;
+
+  // ---- permuted CSR of A and of A^T ----
+  std::vector<int32_t> rpA(m + 1), ciA(nnz);
+  std::vector<double> valA(nnz);
+  rpA[0] = 0;
+  for (int32_t i = 0; i < m; ++i) rpA[i + 1] = rpA[i] + (int32_t)rlen[h->row_perm[i]];
+  for (int32_t i = 0; i < m; ++i) {
+    const int32_t o = h->row_perm[i];
+    int32_t q = rpA[i];
+    for (int64_t p = rp[o]; p < rp[o + 1]; ++p, ++q) {
+      ciA[q] = col_inv[ci[p]];
+      valA[q] = val[p];
+    }
+  }
+  std::vector<int32_t> rpT(n + 1), ciT(nnz), cursor(n);
+  std::vector<double> valT(nnz);
+  rpT[0] = 0;
+  for (int32_t j = 0; j < n; ++j) rpT[j + 1] = rpT[j] + (int32_t)clen[h->col_perm[j]];
+  for (int32_t j = 0; j < n; ++j) cursor[j] = rpT[j];
+  for (int32_t i = 0; i < m; ++i)
+    for (int32_t q = rpA[i]; q < rpA[i + 1]; ++q) {
+      const int32_t pos = cursor[ciA[q]]++;
+      ciT[pos] = i;
+      valT[pos] = valA[q];
+    }
+  h->binsA = make_bins(rpA, h->prm.lane_target);
+  h->binsT = make_bins(rpT, h->prm.lane_target);
+
+  int occA = 0, occT = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k1_rows, kThreads, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occT, k2_cols, kThreads, 0));
+  if (occA < 1) occA = 1;
+  if (occT < 1) occT = 1;
+  h->gridA = grid_for_tasks((int64_t)h->binsA.ntasks + (int64_t)h->binsA.cta_rows * kWarps, h->num_sms,
+                            occA * h->num_sms);
+  h->gridT = grid_for_tasks((int64_t)h->binsT.ntasks + (int64_t)h->binsT.cta_rows * kWarps, h->num_sms,
+                            occT * h->num_sms);
+  h->gridV = grid_for(n > m ? n : m, kThreads, 4 * h->num_sms);
+  h->max_grid = h->gridA > h->gridT ? h->gridA : h->gridT;
+  if (h->gridV > h->max_grid) h->max_grid = h->gridV;
+
+  // ---- device buffers ----
+  CK(h->alloc(&h->rpA, m + 1)); CK(h->alloc(&h->ciA, nnz)); CK(h->alloc(&h->valA, nnz));
+  CK(h->alloc(&h->rpT, n + 1)); CK(h->alloc(&h->ciT, nnz)); CK(h->alloc(&h->valT, nnz));
+  CK(h->alloc(&h->d_row_perm, m)); CK(h->alloc(&h->d_col_perm, n));
+  for (double** p : {&h->c, &h->lv, &h->uv, &h->inv_dc, &h->dc, &h->x, &h->x0, &h->xh0, &h->xh1,
+                     &h->aty, &h->aty0})
+    CK(h->alloc(p, n));
+  for (double** p : {&h->lc, &h->uc, &h->inv_dr, &h->dr, &h->y, &h->y0, &h->yh, &h->ax, &h->ax0, &h->axh})
+    CK(h->alloc(p, m));
+  CK(h->alloc(&h->out_buf, (size_t)(n > m ? n : m) + 1));
+  CK(h->alloc(&h->partials, (size_t)h->max_grid * kNumSums));
+  CK(h->alloc(&h->ctl, 1));
+  CK(h->alloc(&h->pw, 1));
+  CK(cudaMemset(h->ctl, 0, sizeof(Ctl)));
+  CK(cudaMemset(h->pw, 0, sizeof(PwCtl)));
+  h->trace_cap = h->prm.trace_cap;
+  if (h->trace_cap > 0) CK(h->alloc(&h->trace, (size_t)h->trace_cap * 4));
+
+  CK(cudaMemcpy(h->rpA, rpA.data(), sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->rpT, rpT.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+  if (nnz > 0) {
+    CK(cudaMemcpy(h->ciA, ciA.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->valA, valA.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->ciT, ciT.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->valT, valT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
+  }
+  {
+    std::vector<double> tmp(n > m ? n : m);
+    auto up_cols = [&](double* dst, const double* src) -> cudaError_t {
+      for (int32_t j = 0; j < n; ++j) tmp[j] = src[h->col_perm[j]];
+      return n > 0 ? cudaMemcpy(dst, tmp.data(), sizeof(double) * n, cudaMemcpyHostToDevice) : cudaSuccess;
+    };
+    auto up_rows = [&](double* dst, const double* src) -> cudaError_t {
+      for (int32_t i = 0; i < m; ++i) tmp[i] = src[h->row_perm[i]];
+      return m > 0 ? cudaMemcpy(dst, tmp.data(), sizeof(double) * m, cudaMemcpyHostToDevice) : cudaSuccess;
+    };
+    CK(up_cols(h->c, c)); CK(up_cols(h->lv, lv)); CK(up_cols(h->uv, uv));
+    CK(up_rows(h->lc, lc)); CK(up_rows(h->uc, uc));
+    std::vector<double> ones(n > m ? n : m, 1.0);
+    if (n > 0) CK(cudaMemcpy(h->dc, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    if (m > 0) CK(cudaMemcpy(h->dr, ones.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+  }
+  if (m > 0) CK(cudaMemcpy(h->d_row_perm, h->row_perm.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+  if (n > 0) CK(cudaMemcpy(h->d_col_perm, h->col_perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+
+  // ---- diagonal preconditioning (device) ----
+  cudaStream_t s = h->setup_stream;
+  const int passes = h->prm.ruiz_iters + (h->prm.pc_enabled ? 1 : 0);
+  if (passes > 0 && nnz > 0) {
+    double* fr = h->y;  // scratch until the first solve
+    double* fc = h->x;
+    const int gr = grid_for((int64_t)m * 32, 256, 8 * h->num_sms);
+    const int gc = grid_for((int64_t)n * 32, 256, 8 * h->num_sms);
+    for (int pass = 0; pass < passes; ++pass) {
+      const bool pc = (pass == h->prm.ruiz_iters);
+      const int kind = pc ? 1 : 0;
+      if (m > 0) k_row_factor<<<gr, 256, 0, s>>>(m, h->rpA, h->valA, kind, 2.0 - h->prm.pc_alpha, fr);
+      if (n > 0) k_row_factor<<<gc, 256, 0, s>>>(n, h->rpT, h->valT, kind, h->prm.pc_alpha, fc);
+      if (m > 0) k_apply_factors<<<gr, 256, 0, s>>>(m, h->rpA, h->ciA, h->valA, fr, fc, 0);
+      if (n > 0) k_apply_factors<<<gc, 256, 0, s>>>(n, h->rpT, h->ciT, h->valT, fr, fc, 1);
+      if (m > 0) k_mul_inplace<<<h->gridV, 256, 0, s>>>(m, h->dr, fr);
+      if (n > 0) k_mul_inplace<<<h->gridV, 256, 0, s>>>(n, h->dc, fc);
+    }
+    CK(cudaGetLastError());
+  }
+  if (n > 0) k_scale_cols<<<h->gridV, 256, 0, s>>>(n, h->dc, h->c, h->lv, h->uv, h->inv_dc);
+  if (m > 0) k_scale_rows<<<h->gridV, 256, 0, s>>>(m, h->dr, h->lc, h->uc, h->inv_dr);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+
+  lp_status st = set_eta(h);
+  if (st != LP_OK) return st;
+  return build_graph(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+lp_status lp_default_params(lp_params* p) {
+  if (!p) return fail(LP_ERR_INVALID_ARG, "params pointer is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->gamma = 1.0;
+  p->beta_sufficient = 0.2;
+  p->beta_necessary = 0.8;
+  p->beta_artificial = 0.36;
+  p->k_p = 0.5;
+  p->k_i = 0.001;
+  p->k_d = 0.0;
+  p->eta = 0.0;
+  p->omega0 = 1.0;
+  p->check_every = 64;
+  p->restart_enabled = 1;
+  p->pid_enabled = 1;
+  p->power_tol = 1e-7;
+  p->power_max_iter = 10000;
+  p->power_seed = 0;
+  p->ruiz_iters = 10;
+  p->pc_enabled = 1;
+  p->pc_alpha = 1.0;
+  p->trace_cap = 0;
+  p->unroll = 8;
+  p->lane_target = 4;
+  return LP_OK;
+}
+
+lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                    const int32_t* col_idx, const double* val, const double* c,
+                    const double* l_c, const double* u_c, const double* l_v, const double* u_v,
+                    int32_t where, const lp_params* p, lp_handle* out) {
+  g_err.clear();
+  if (!out) return fail(LP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (m < 0 || n < 0 || nnz < 0) return fail(LP_ERR_INVALID_ARG, "negative size");
+  if (where != LP_HOST && where != LP_DEVICE) return fail(LP_ERR_INVALID_ARG, "where must be LP_HOST or LP_DEVICE");
+  if (!row_ptr) return fail(LP_ERR_INVALID_ARG, "row_ptr is NULL");
+  if (nnz > 0 && (!col_idx || !val)) return fail(LP_ERR_INVALID_ARG, "col_idx/val is NULL");
+  if (n > 0 && (!c || !l_v || !u_v)) return fail(LP_ERR_INVALID_ARG, "c/l_v/u_v is NULL");
+  if (m > 0 && (!l_c || !u_c)) return fail(LP_ERR_INVALID_ARG, "l_c/u_c is NULL");
+  if (nnz >= (int64_t(1) << 31)) return fail(LP_ERR_TOO_LARGE, "nnz must be < 2^31");
+  lp_params prm;
+  if (p) prm = *p; else lp_default_params(&prm);
+  lp_status st = check_params(prm);
+  if (st != LP_OK) return st;
+
+  // Device inputs are staged through host memory for the (host-side) structural setup.
+  std::vector<int64_t> h_rp;
+  std::vector<int32_t> h_ci;
+  std::vector<double> h_val, h_c, h_lc, h_uc, h_lv, h_uv;
+  if (where == LP_DEVICE) {
+    auto dl = [](auto& vec, const auto* src, int64_t count) -> cudaError_t {
+      vec.resize(count > 0 ? count : 0);
+      if (count <= 0) return cudaSuccess;
+      return cudaMemcpy(vec.data(), src, sizeof(*src) * count, cudaMemcpyDeviceToHost);
+    };
+    CK(dl(h_rp, row_ptr, (int64_t)m + 1));
+    CK(dl(h_ci, col_idx, nnz)); CK(dl(h_val, val, nnz));
+    CK(dl(h_c, c, n)); CK(dl(h_lv, l_v, n)); CK(dl(h_uv, u_v, n));
+    CK(dl(h_lc, l_c, m)); CK(dl(h_uc, u_c, m));
+    row_ptr = h_rp.data(); col_idx = h_ci.data(); val = h_val.data(); c = h_c.data();
+    l_v = h_lv.data(); u_v = h_uv.data(); l_c = h_lc.data(); u_c = h_uc.data();
+  }
+  st = validate(m, n, nnz, row_ptr, col_idx, val, c, l_c, u_c, l_v, u_v);
+  if (st != LP_OK) return st;
+  lp_solver* h = new (std::nothrow) lp_solver();
+  if (!h) return fail(LP_ERR_OUT_OF_MEMORY, "host allocation failed");
+  h->prm = prm;
+  st = create_impl(h, m, n, nnz, row_ptr, col_idx, val, c, l_c, u_c, l_v, u_v);
+  if (st != LP_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return LP_OK;
+}
+
+lp_status lp_set_params(lp_handle h, const lp_params* p) {
+  g_err.clear();
+  if (!h || !p) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  lp_status st = check_params(*p);
+  if (st != LP_OK) return st;
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->last_stream));
+  const lp_params old = h->prm;
+  h->prm = *p;
+  h->prm.ruiz_iters = old.ruiz_iters;  // preconditioning is fixed at lp_create
+  h->prm.pc_enabled = old.pc_enabled;
+  h->prm.pc_alpha = old.pc_alpha;
+  h->prm.lane_target = old.lane_target;  // the bin tables are built at lp_create
+  if (p->power_seed != old.power_seed || p->power_tol != old.power_tol ||
+      p->power_max_iter != old.power_max_iter)
+    h->power_valid = false;
+  st = set_eta(h);
+  if (st != LP_OK) return st;
+  if (p->trace_cap != h->trace_cap) {
+    if (h->trace) {
+      cudaFree(h->trace);
+      for (auto& a : h->allocations)
+        if (a == h->trace) a = nullptr;
+      h->trace = nullptr;
+    }
+    h->trace_cap = p->trace_cap;
+    if (h->trace_cap > 0) CK(h->alloc(&h->trace, (size_t)h->trace_cap * 4));
+    return build_graph(h);
+  }
+  if (h->prm.unroll != h->graph_unroll) return build_graph(h);
+  return LP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Scalar state, zero iterate and first primal step of a solve, enqueued on s.
+lp_status enqueue_start(lp_solver* h, double tol, int64_t max_iter, cudaStream_t s) {
+  Ctl init{};
+  init.eta = h->eta;
+  init.omega = h->prm.omega0;
+  init.tau = h->eta / h->prm.omega0;
+  init.sigma = h->eta * h->prm.omega0;
+  init.inv_sigma = 1.0 / (h->eta * h->prm.omega0);
+  init.restart_enabled = h->prm.restart_enabled;
+  init.pid_enabled = h->prm.pid_enabled;
+  init.max_iter = max_iter;
+  init.check_every = h->prm.check_every;
+  init.trace_cap = h->trace_cap;
+  init.tol = tol;
+  init.omega_used = h->prm.omega0;
+  for (int q = 0; q < 8; ++q) init.kkt[q] = NAN;
+  init.lu_norm = h->lu_norm;
+  init.c_norm = h->c_norm;
+  init.gamma = h->prm.gamma;
+  init.beta_s = h->prm.beta_sufficient;
+  init.beta_n = h->prm.beta_necessary;
+  init.beta_a = h->prm.beta_artificial;
+  init.kp = h->prm.k_p;
+  init.ki = h->prm.k_i;
+  init.kd = h->prm.k_d;
+  k_init_ctl<<<1, 1, 0, s>>>(h->ctl, init);
+  k_init_rows<<<h->gridV, 256, 0, s>>>(h->m, h->y, h->y0, h->yh, h->ax, h->ax0, h->axh);
+  k_init_cols<<<h->gridV, kThreads, 0, s>>>(h->n, h->c, h->lv, h->uv, h->xh0, h->x, h->x0, h->aty,
+                                            h->aty0, h->ctl, h->partials);
+  CK(cudaGetLastError());
+  return LP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lp_status lp_solve(lp_handle h, double tol, int64_t max_iter, void* stream) {
+  g_err.clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "handle is NULL");
+  if (!(tol >= 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be >= 0");
+  if (max_iter < 1) return fail(LP_ERR_INVALID_ARG, "max_iter must be >= 1");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  lp_status st = enqueue_start(h, tol, max_iter, s);
+  if (st != LP_OK) return st;
+  CK(cudaGraphLaunch(h->exec, s));
+  h->solved = true;
+  h->last_stream = s;
+  return LP_OK;
+}
+
+lp_status lp_get(lp_handle h, double* x, double* y, int32_t* solve_status, double* kkt,
+                 int64_t* iters) {
+  g_err.clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "lp_get before lp_solve");
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->last_stream));
+  Ctl ctl;
+  CK(cudaMemcpy(&ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  const double* xh = (ctl.t & 1) ? h->xh1 : h->xh0;
+  cudaStream_t s = h->setup_stream;
+  if (x && h->n > 0) {
+    k_unpermute_scale<<<h->gridV, 256, 0, s>>>(h->n, h->d_col_perm, xh, h->dc, h->out_buf);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(x, h->out_buf, sizeof(double) * h->n, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (y && h->m > 0) {
+    k_unpermute_scale<<<h->gridV, 256, 0, s>>>(h->m, h->d_row_perm, h->yh, h->dr, h->out_buf);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(y, h->out_buf, sizeof(double) * h->m, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (solve_status) *solve_status = ctl.status;
+  if (kkt)
+    for (int q = 0; q < 4; ++q) kkt[q] = ctl.kkt[q];
+  if (iters) *iters = ctl.iters;
+  return LP_OK;
+}
+
+lp_status lp_get_info(lp_handle h, double* out7) {
+  g_err.clear();
+  if (!h || !out7) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "lp_get_info before lp_solve");
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->last_stream));
+  Ctl ctl;
+  CK(cudaMemcpy(&ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  out7[0] = h->eta;
+  out7[1] = ctl.omega_used;
+  out7[2] = (double)ctl.restarts_used;
+  out7[3] = h->power_valid ? h->norm_A : 0.0;
+  out7[4] = (double)h->pw_iters;
+  out7[5] = ctl.kkt[4];
+  out7[6] = ctl.kkt[5];
+  return LP_OK;
+}
+
+lp_status lp_get_trace(lp_handle h, double* trace, int64_t cap, int64_t* rows) {
+  g_err.clear();
+  if (!h || !trace || !rows || cap < 0) return fail(LP_ERR_INVALID_ARG, "bad argument");
+  if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "lp_get_trace before lp_solve");
+  if (h->trace_cap <= 0) return fail(LP_ERR_INVALID_ARG, "trace_cap is 0");
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->last_stream));
+  Ctl ctl;
+  CK(cudaMemcpy(&ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  int64_t r = ctl.iters < h->trace_cap ? ctl.iters : h->trace_cap;
+  if (r > cap) r = cap;
+  if (r > 0) CK(cudaMemcpy(trace, h->trace, sizeof(double) * 4 * r, cudaMemcpyDeviceToHost));
+  *rows = r;
+  return LP_OK;
+}
+
+void lp_destroy(lp_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->solved) cudaStreamSynchronize(h->last_stream);
+  delete h;
+}
+
+const char* lp_last_error(void) { return g_err.c_str(); }
+
+lp_status lp_time_kernels(lp_handle h, int64_t iters, void* stream, double* ms_out) {
+  g_err.clear();
+  if (!h || !ms_out || iters < 1) return fail(LP_ERR_INVALID_ARG, "bad argument");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  lp_status st = enqueue_start(h, 0.0, iters, s);
+  if (st != LP_OK) return st;
+  RowArgs ra{};
+  ColArgs ca{};
+  fill_args(h, ra, ca);
+  std::vector<cudaEvent_t> ev(2 * iters + 1);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(ev[0], s));
+  for (int64_t t = 0; t < iters; ++t) {
+    k1_rows<<<h->gridA, kThreads, 0, s>>>(ra);
+    CK(cudaEventRecord(ev[2 * t + 1], s));
+    k2_cols<<<h->gridT, kThreads, 0, s>>>(ca);
+    CK(cudaEventRecord(ev[2 * t + 2], s));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  double a = 0.0, b = 0.0;
+  for (int64_t t = 0; t < iters; ++t) {
+    float m1 = 0.f, m2 = 0.f;
+    CK(cudaEventElapsedTime(&m1, ev[2 * t], ev[2 * t + 1]));
+    CK(cudaEventElapsedTime(&m2, ev[2 * t + 1], ev[2 * t + 2]));
+    a += m1;
+    b += m2;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  ms_out[0] = a / (double)iters;
+  ms_out[1] = b / (double)iters;
+  ms_out[2] = (double)iters;
+  h->solved = true;
+  h->last_stream = s;
+  return LP_OK;
+}
+
+lp_status lp_debug_spmv(lp_handle h, int32_t which, const double* x_dev, double* y_dev) {
+  g_err.clear();
+  if (!h || !x_dev || !y_dev || (which != 0 && which != 1)) return fail(LP_ERR_INVALID_ARG, "bad argument");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = h->setup_stream;
+  if (which == 0)
+    k_spmv<<<h->gridA, kThreads, 0, s>>>(h->rpA, h->ciA, h->valA, x_dev, y_dev, h->binsA);
+  else
+    k_spmv<<<h->gridT, kThreads, 0, s>>>(h->rpT, h->ciT, h->valT, x_dev, y_dev, h->binsT);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return LP_OK;
+}
+
+lp_status lp_debug_layout(lp_handle h, int32_t* row_perm, int32_t* col_perm, double* d_r,
+                          double* d_c) {
+  g_err.clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "handle is NULL");
+  CK(cudaSetDevice(h->device));
+  if (row_perm) std::memcpy(row_perm, h->row_perm.data(), sizeof(int32_t) * h->m);
+  if (col_perm) std::memcpy(col_perm, h->col_perm.data(), sizeof(int32_t) * h->n);
+  std::vector<double> tmp(h->n > h->m ? h->n : h->m);
+  if (d_r && h->m > 0) {
+    CK(cudaMemcpy(tmp.data(), h->dr, sizeof(double) * h->m, cudaMemcpyDeviceToHost));
+    for (int32_t i = 0; i < h->m; ++i) d_r[h->row_perm[i]] = tmp[i];
+  }
+  if (d_c && h->n > 0) {
+    CK(cudaMemcpy(tmp.data(), h->dc, sizeof(double) * h->n, cudaMemcpyDeviceToHost));
+    for (int32_t j = 0; j < h->n; ++j) d_c[h->col_perm[j]] = tmp[j];
+  }
+  return LP_OK;
+}
+
+}  // extern "C"
