@@ -193,6 +193,37 @@ LP_API lp_status lp_debug_spmv(lp_handle h, int32_t which, const double* x_dev, 
 LP_API lp_status lp_debug_layout(lp_handle h, int32_t* row_perm, int32_t* col_perm, double* d_r,
                           double* d_c);
 
+/*
+ * ||A||_2 by power iteration, for callers that cannot allocate device memory.  The paper has
+ * no counterpart to this entry point.
+ *
+ * Some callers must not call cudaMalloc: code whose device memory is owned entirely by its
+ * own pool allocator, or latency-critical code that cannot afford the implicit device
+ * synchronisation an allocation may cause.  This entry point allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library call): it computes the same estimate as the
+ * power iteration of lp_create (start vector uniform[-1,1) from splitmix64(seed, j),
+ * w = A v, lambda = |w|^2, v = A^T w / |A^T w|, stop when |lambda - lambda_prev| <= tol *
+ * lambda or after max_iter steps; result sqrt(lambda)) on the caller's matrix as given (no
+ * preconditioning), with all scratch in one static device array of about 6.3 MB that the
+ * library holds on every device that loads it until the process exits.
+ *   m, n       at most 262144 each; larger sizes return LP_ERR_TOO_LARGE.
+ *   row_ptr, col_idx, val   CSR of A in device memory of the current device (int64 offsets,
+ *              0-based int32 column indices, doubles); not validated.
+ *   tol, max_iter, seed     stopping rule and start vector as in lp_params.
+ *   stream     cudaStream_t (NULL: legacy default stream); the call is synchronous.
+ *   norm_out   receives the estimate (0 for an empty matrix); iters_out (may be NULL) the steps.
+ * The first call on a device looks up the device address of the static scratch with that
+ * device current; make that first call before any stream capture.  Every call on a device
+ * shares the same scratch: calls that overlap on the GPU (other threads, other streams) race
+ * and give wrong results.  The transposed product uses atomic adds, so the last bits of the
+ * estimate can differ from run to run.
+ * Errors: LP_ERR_INVALID_ARG, LP_ERR_TOO_LARGE, LP_ERR_CUDA.
+ */
+LP_API lp_status lp_power_norm_noalloc(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                                       const int32_t* col_idx, const double* val, double tol,
+                                       int64_t max_iter, uint64_t seed, void* stream,
+                                       double* norm_out, int64_t* iters_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,7 @@ LP_HOST, LP_DEVICE = 0, 1
 
 EXPORTED = ("lp_default_params", "lp_create", "lp_set_params", "lp_solve", "lp_get",
             "lp_get_info", "lp_get_trace", "lp_destroy", "lp_last_error", "lp_time_kernels",
-            "lp_debug_spmv", "lp_debug_layout")
+            "lp_debug_spmv", "lp_debug_layout", "lp_power_norm_noalloc")
 
 
 class lp_params(C.Structure):
@@ -108,6 +108,8 @@ def load(path: str | None = None) -> C.CDLL:
         L.lp_time_kernels.argtypes = [vp, C.c_int64, vp, dp]
         L.lp_debug_spmv.argtypes = [vp, C.c_int32, vp, vp]
         L.lp_debug_layout.argtypes = [vp, i32p, i32p, dp, dp]
+        L.lp_power_norm_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, C.c_double,
+                                            C.c_int64, C.c_uint64, vp, dp, i64p]
         for name in EXPORTED:
             if name not in ("lp_destroy", "lp_last_error"):
                 getattr(L, name).restype = C.c_int32
@@ -216,6 +218,18 @@ def lp_debug_layout(h, m: int, n: int):
                                   dr.ctypes.data_as(C.POINTER(C.c_double)),
                                   dc.ctypes.data_as(C.POINTER(C.c_double))), "lp_debug_layout")
     return rp, cp, dr, dc
+
+
+def lp_power_norm_noalloc(m, n, nnz, row_ptr, col_idx, val, tol=1e-7, max_iter=10000, seed=0,
+                          stream: int | None = None):
+    """||A||_2 estimate for a device CSR (torch CUDA tensors) without device allocation;
+    returns (norm, steps).  See include/lp.h for the limits and the shared scratch."""
+    out = C.c_double(0.0)
+    it = C.c_int64(0)
+    _check(load().lp_power_norm_noalloc(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val), tol,
+                                        int(max_iter), seed, stream, C.byref(out), C.byref(it)),
+           "lp_power_norm_noalloc")
+    return out.value, it.value
 
 
 class Solver:

@@ -65,6 +65,9 @@ int length_class(int64_t len) {
 
 }  // namespace
 
+// Sets the calling thread's lp_last_error message (used by entry points in other files).
+void pdhg_set_last_error(const std::string& msg) { g_err = msg; }
+
 struct lp_solver {
   int device = 0;
   int num_sms = 148;
