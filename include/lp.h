@@ -83,13 +83,13 @@ typedef struct {
   double pc_alpha;
   int64_t trace_cap;       /* > 0: record (r_t, omega_t, restart_t, k_t) for t < trace_cap */
   int32_t unroll;          /* iterations per body of the device-side loop (1..64) */
-  int32_t lane_target;     /* SpMV schedule: aim for this many nonzeros per lane (1..64) */
+  int32_t lane_target;     /* SpMV schedule: at most this many nonzeros per lane and task (1..64) */
 } lp_params;
 
 /* Fills p with the defaults: gamma 1, betas 0.2 / 0.8 / 0.36, K_P 0.5, K_I 0.001, K_D 0,
  * eta 0 (power iteration), omega0 1, check_every 64, restarts and PID on, power_tol 1e-7,
  * power_max_iter 10000, seed 0, Ruiz 10 + Pock-Chambolle alpha 1, no trace, unroll 8,
- * lane_target 4.  Returns LP_ERR_INVALID_ARG if p is NULL. */
+ * lane_target 8.  Returns LP_ERR_INVALID_ARG if p is NULL. */
 LP_API lp_status lp_default_params(lp_params* p);
 
 typedef struct lp_solver* lp_handle;

@@ -16,9 +16,9 @@ constexpr int kWarps = 8;  // warps per block of the streaming kernels
 constexpr int kThreads = kWarps * 32;
 constexpr int kMaxBins = 34;
 constexpr int kNumSums = 5;  // reduction slots per kernel
-constexpr int kCtaRowMin = 256;  // rows with more entries are processed by a whole CTA
-constexpr int kTileNnz = 1024;   // target nonzeros per warp task
-constexpr int kIlp = 4;          // independent entries a lane loads before accumulating
+constexpr int kLongRowMin = 256;  // rows with more entries are split into chunk tasks
+constexpr int kChunkNnz = 256;    // entries per chunk task of a long row
+constexpr int kIlp = 8;           // independent entries a lane loads before accumulating
 constexpr unsigned kFull = 0xffffffffu;
 
 struct Bin {
@@ -26,14 +26,24 @@ struct Bin {
   int32_t lanes;          // G: lanes per row (1, 2, 4, 8, 16 or 32)
   int32_t rows_per_tile;  // R: rows per warp task (<= 32)
   int32_t task0;          // index of the bin's first task
+  int32_t per_lane;       // most entries a lane reads in one task (ceil(Lc / G))
 };
 
-// Rows [0, cta_rows) are long (more than kCtaRowMin entries) and are handled one row per CTA;
-// the bins cover the rest, one tile of rows per warp.
+// Rows [0, long_rows) of the permuted order have more than kLongRowMin entries; each is split
+// into chunks of kChunkNnz entries, one warp task per chunk (tasks [0, nchunks)).  chunk[q] =
+// (row, first chunk of that row, number of chunks of the row, 0); part[q] holds the chunk's
+// partial dot product and arrivals[row] counts finished chunks (the last one combines the
+// partials in chunk order and rewinds the counter).  The bins cover the remaining rows, one
+// tile of up to 32 rows per warp task (tasks [nchunks, nchunks + ntasks)).
 struct BinTable {
   int32_t nbins;
   int32_t ntasks;
-  int32_t cta_rows;
+  int32_t long_rows;
+  int32_t nchunks;
+  const int4* chunk;
+  double* part;
+  unsigned int* arrivals;
+  double* contrib;  // long row r's kNumSums epilogue contributions (added by the last block)
   Bin bin[kMaxBins];
 };
 
@@ -43,6 +53,7 @@ enum : int32_t { kOptimal = 1, kIterLimit = 2, kNumerical = 3, kInternalError = 
 // each iteration kernel (and read by all threads at kernel entry).
 struct Ctl {
   double eta, omega, tau, sigma, inv_sigma;
+  double w_over_eta, inv_eta_w;  // omega/eta and 1/(eta*omega): the weights of the P-norm
   double ha, hb, he;  // z <- ha*zhat + hb*z + he*z0 (reflected Halpern weights)
   int32_t restart;    // decision taken at iteration t (applied by K2(t) and K1(t+1))
   int32_t done;
@@ -109,18 +120,19 @@ __device__ __forceinline__ double ld_gather(const double* p, uint64_t pol) {
   return v;
 }
 
-// Partial dot product of one lane: entries b+first, b+first+stride, ... < e, loaded kIlp at a
+// Partial dot product of one lane: entries b+first, b+first+stride, ... < e, loaded ILP at a
 // time (all loads of a batch issued before any is used) and accumulated in entry order.
-__device__ __forceinline__ double strided_dot(const int32_t* __restrict__ ci,
-                                              const double* __restrict__ val,
-                                              const double* __restrict__ xg, int first, int e,
-                                              int stride, const LoadPolicy& pol) {
+template <int ILP>
+__device__ __forceinline__ double strided_dot_n(const int32_t* __restrict__ ci,
+                                                const double* __restrict__ val,
+                                                const double* __restrict__ xg, int first, int e,
+                                                int stride, const LoadPolicy& pol) {
   double acc = 0.0;
-  for (int k0 = first; k0 < e; k0 += kIlp * stride) {
-    double v[kIlp];
-    int c[kIlp];
+  for (int k0 = first; k0 < e; k0 += ILP * stride) {
+    double v[ILP];
+    int c[ILP];
 #pragma unroll
-    for (int u = 0; u < kIlp; ++u) {
+    for (int u = 0; u < ILP; ++u) {
       const int k = k0 + u * stride;
       if (k < e) {
         v[u] = ld_stream(val + k, pol.stream);
@@ -130,14 +142,27 @@ __device__ __forceinline__ double strided_dot(const int32_t* __restrict__ ci,
         c[u] = -1;
       }
     }
-    double xv[kIlp];
+    double xv[ILP];
 #pragma unroll
-    for (int u = 0; u < kIlp; ++u) xv[u] = c[u] >= 0 ? ld_gather(xg + c[u], pol.keep) : 0.0;
+    for (int u = 0; u < ILP; ++u) xv[u] = c[u] >= 0 ? ld_gather(xg + c[u], pol.keep) : 0.0;
 #pragma unroll
-    for (int u = 0; u < kIlp; ++u)
+    for (int u = 0; u < ILP; ++u)
       if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
   }
   return acc;
+}
+
+// The same with the batch sized to `per_lane`, the most entries any lane of the warp has
+// (uniform across the warp): short rows then issue no FP64 fma for absent entries, which on
+// this GPU's FP64 unit would cost as much as real ones.
+__device__ __forceinline__ double strided_dot(const int32_t* __restrict__ ci,
+                                              const double* __restrict__ val,
+                                              const double* __restrict__ xg, int first, int e,
+                                              int stride, int per_lane, const LoadPolicy& pol) {
+  if (per_lane <= 1) return strided_dot_n<1>(ci, val, xg, first, e, stride, pol);
+  if (per_lane <= 2) return strided_dot_n<2>(ci, val, xg, first, e, stride, pol);
+  if (per_lane <= 4) return strided_dot_n<4>(ci, val, xg, first, e, stride, pol);
+  return strided_dot_n<kIlp>(ci, val, xg, first, e, stride, pol);
 }
 
 // Dot products of the rows [row0, row0 + nrows) (nrows <= 32) of a CSR matrix with xg.
@@ -148,7 +173,7 @@ __device__ __forceinline__ double tile_spmv(const int32_t* __restrict__ rp,
                                             const int32_t* __restrict__ ci,
                                             const double* __restrict__ val,
                                             const double* __restrict__ xg, int row0, int nrows,
-                                            int G, int lane, const LoadPolicy& pol) {
+                                            int G, int per_lane, int lane, const LoadPolicy& pol) {
   const int rpp = 32 / G;  // rows per pass
   const int passes = (nrows + rpp - 1) / rpp;
   const int g = lane / G, sub = lane - g * G;
@@ -163,7 +188,7 @@ __device__ __forceinline__ double tile_spmv(const int32_t* __restrict__ rp,
     const int q = p * rpp + g;  // row of this lane's group in this pass
     const int b = __shfl_sync(kFull, my_b, q & 31);
     const int e = __shfl_sync(kFull, my_e, q & 31);
-    double acc = q < nrows ? strided_dot(ci, val, xg, b + sub, e, G, pol) : 0.0;
+    double acc = q < nrows ? strided_dot(ci, val, xg, b + sub, e, G, per_lane, pol) : 0.0;
     for (int off = G >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
     const double v = __shfl_sync(kFull, acc, (lane % rpp) * G);
     if (lane / rpp == p) mine = v;
@@ -171,106 +196,116 @@ __device__ __forceinline__ double tile_spmv(const int32_t* __restrict__ rp,
   return mine;
 }
 
-// Dot product of one long row with the whole block (all threads must call it): each thread
-// takes every kThreads-th entry; the block's values are summed by a shared-memory halving tree
-// down to one warp, then a warp butterfly (fixed order; about 12 warp-wide FP64 adds instead of
-// one butterfly per warp).  The result is valid in thread 0.
-__device__ __forceinline__ double cta_row_dot(const int32_t* __restrict__ rp,
-                                              const int32_t* __restrict__ ci,
-                                              const double* __restrict__ val,
-                                              const double* __restrict__ xg, int row,
-                                              const LoadPolicy& pol) {
-  __shared__ double part[kThreads];
-  const int tid = threadIdx.x;
-  const int b = rp[row], e = rp[row + 1];
-  part[tid] = strided_dot(ci, val, xg, b + tid, e, kThreads, pol);
-  __syncthreads();
-#pragma unroll
-  for (int w = kThreads / 2; w >= 32; w >>= 1) {
-    if (tid < w) part[tid] += part[tid + w];
-    __syncthreads();
-  }
-  double v = 0.0;
-  if (tid < 32) v = warp_sum(part[tid]);
-  __syncthreads();
-  return v;
-}
-
-// Visits every row of a binned CSR matrix once with its dot product against xg:
-// epi(row, value) runs in thread 0 for the long rows (one per CTA, grid-strided) and in
-// lane L < nrows of the owning warp for the binned rows.  Which block and lane handle a row
-// depends only on the grid size, so all sums over rows are deterministic.
+// Visits every row of a binned CSR matrix once with its dot product against xg and calls
+// epi(row, value, acc) in exactly one lane: lane L < nrows of the warp that owns a tile (acc =
+// that thread's running sums `s`), or lane 0 of the warp that finishes a long row's last chunk
+// (acc = a zeroed array then stored in bins.contrib for the last block to add in row order).
+// Every sum therefore has a fixed order that depends only on the grid size: results are
+// bit-reproducible run to run.
 template <class Epi>
 __device__ __forceinline__ void for_each_row(const BinTable& bins, const int32_t* __restrict__ rp,
                                              const int32_t* __restrict__ ci,
                                              const double* __restrict__ val,
                                              const double* __restrict__ xg, const LoadPolicy& pol,
-                                             Epi&& epi) {
-  for (int r = blockIdx.x; r < bins.cta_rows; r += gridDim.x) {
-    const double v = cta_row_dot(rp, ci, val, xg, r, pol);
-    if (threadIdx.x == 0) epi(r, v);
-  }
+                                             double (&s)[kNumSums], Epi&& epi) {
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * kWarps;
-  for (int task = blockIdx.x * kWarps + (threadIdx.x >> 5); task < bins.ntasks; task += nwarps) {
-    const Bin B = bins.bin[find_bin(bins, task)];
-    const int row0 = B.row0 + (task - B.task0) * B.rows_per_tile;
+  const int total = bins.nchunks + bins.ntasks;
+  for (int task = blockIdx.x * kWarps + (threadIdx.x >> 5); task < total; task += nwarps) {
+    if (task < bins.nchunks) {
+      const int4 ch = bins.chunk[task];
+      const int b = rp[ch.x] + (task - ch.y) * kChunkNnz;
+      const int e = min(rp[ch.x + 1], b + kChunkNnz);
+      const double v = warp_sum(strided_dot(ci, val, xg, b + lane, e, 32, kChunkNnz / 32, pol));
+      if (lane == 0) {
+        bins.part[task] = v;
+        __threadfence();
+        if (atomicAdd(bins.arrivals + ch.x, 1u) == (unsigned)ch.z - 1u) {
+          __threadfence();
+          double tot = 0.0;
+          for (int q = 0; q < ch.z; ++q) tot += __ldcg(bins.part + ch.y + q);
+          bins.arrivals[ch.x] = 0u;
+          double c[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+          epi(ch.x, tot, c);
+#pragma unroll
+          for (int q = 0; q < kNumSums; ++q) bins.contrib[ch.x * kNumSums + q] = c[q];
+        }
+      }
+      continue;
+    }
+    const Bin B = bins.bin[find_bin(bins, task - bins.nchunks)];
+    const int row0 = B.row0 + (task - bins.nchunks - B.task0) * B.rows_per_tile;
     const int nrows = min(B.rows_per_tile, B.row1 - row0);
-    const double v = tile_spmv(rp, ci, val, xg, row0, nrows, B.lanes, lane, pol);
-    if (lane < nrows) epi(row0 + lane, v);
+    const int lc = B.per_lane;
+    const double v = tile_spmv(rp, ci, val, xg, row0, nrows, B.lanes, lc, lane, pol);
+    if (lane < nrows) epi(row0 + lane, v, s);
   }
 }
 
-// Sums kNumSums per-thread values over the block (shared-memory halving tree down to one
-// warp, then a warp butterfly, all in a fixed order), writes them to partials[blockIdx.x][*],
-// and returns true in every thread of the block that finished last (all partials are then
-// visible).  The whole block must call it; `counter` is reset by the caller's last block.
-__device__ __forceinline__ bool block_sums_last(double (&s)[kNumSums], double* partials,
-                                                unsigned int* counter) {
+// Sums the first nsums of each thread's v[] over the block in a fixed order (shared-memory
+// halving tree down to one warp, then a warp butterfly); the totals end in thread 0's v[].
+// The whole block must call it.
+__device__ __forceinline__ void block_reduce(double (&v)[kNumSums], int nsums) {
   __shared__ double red[kNumSums][kThreads];
-  __shared__ bool is_last;
   const int tid = threadIdx.x;
 #pragma unroll
-  for (int q = 0; q < kNumSums; ++q) red[q][tid] = s[q];
+  for (int q = 0; q < kNumSums; ++q) red[q][tid] = v[q];
   __syncthreads();
 #pragma unroll
   for (int w = kThreads / 2; w >= 32; w >>= 1) {
     if (tid < w) {
 #pragma unroll
-      for (int q = 0; q < kNumSums; ++q) red[q][tid] += red[q][tid + w];
+      for (int q = 0; q < kNumSums; ++q)
+        if (q < nsums) red[q][tid] += red[q][tid + w];
     }
     __syncthreads();
   }
   if (tid < 32) {
-    double v[kNumSums];
 #pragma unroll
-    for (int q = 0; q < kNumSums; ++q) v[q] = warp_sum(red[q][tid]);
-    if (tid == 0) {
+    for (int q = 0; q < kNumSums; ++q) v[q] = q < nsums ? warp_sum(red[q][tid]) : 0.0;
+  }
+  __syncthreads();
+}
+
+// Sums the block's per-thread values (block_reduce), writes them to partials[blockIdx.x][*],
+// and returns true in every thread of the block that finished last (all partials are then
+// visible).  The whole block must call it; `counter` is reset by the caller's last block.
+__device__ __forceinline__ bool block_sums_last(double (&s)[kNumSums], int nsums, double* partials,
+                                                unsigned int* counter) {
+  __shared__ bool is_last;
+  block_reduce(s, nsums);
+  if (threadIdx.x == 0) {
 #pragma unroll
-      for (int q = 0; q < kNumSums; ++q) partials[blockIdx.x * kNumSums + q] = v[q];
-      __threadfence();
-      const unsigned prev = atomicAdd(counter, 1u);
-      is_last = (prev == gridDim.x - 1);
-    }
+    for (int q = 0; q < kNumSums; ++q) partials[blockIdx.x * kNumSums + q] = s[q];
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    is_last = (prev == gridDim.x - 1);
   }
   __syncthreads();
   if (is_last) __threadfence();
   return is_last;
 }
 
-// In the last block's first warp: totals of the partials of all blocks, in a fixed order.
-__device__ __forceinline__ void total_partials(const double* partials, int nblocks,
-                                               double (&tot)[kNumSums]) {
-  const int lane = threadIdx.x & 31;
+// In the last block (all threads): totals over the blocks' partials and, if bins is given, the
+// long rows' epilogue contributions.  Thread t adds blocks t, t + kThreads, ... and long rows
+// t, t + kThreads, ..., then block_reduce; the totals end in thread 0's tot[].
+__device__ __forceinline__ void block_totals(const double* partials, int nblocks, int nsums,
+                                             const BinTable* bins, double (&tot)[kNumSums]) {
 #pragma unroll
   for (int q = 0; q < kNumSums; ++q) tot[q] = 0.0;
-#pragma unroll 4
-  for (int b = lane; b < nblocks; b += 32) {
+  for (int b = threadIdx.x; b < nblocks; b += kThreads) {
 #pragma unroll
-    for (int q = 0; q < kNumSums; ++q) tot[q] += __ldcg(partials + b * kNumSums + q);
+    for (int q = 0; q < kNumSums; ++q)
+      if (q < nsums) tot[q] += __ldcg(partials + b * kNumSums + q);
   }
+  if (bins) {
+    for (int r = threadIdx.x; r < bins->long_rows; r += kThreads) {
 #pragma unroll
-  for (int q = 0; q < kNumSums; ++q) tot[q] = warp_sum(tot[q]);
+      for (int q = 0; q < kNumSums; ++q)
+        if (q < nsums) tot[q] += __ldcg(bins->contrib + r * kNumSums + q);
+    }
+  }
+  block_reduce(tot, nsums);
 }
 
 }  // namespace pdhg

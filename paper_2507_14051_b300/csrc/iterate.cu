@@ -58,7 +58,7 @@ __device__ __forceinline__ double pid_update(Ctl* ctl, double omega, double dxn,
   return exp(lw);
 }
 
-__global__ void __launch_bounds__(kThreads) k1_rows(RowArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k1_rows(RowArgs a) {
   Ctl* ctl = a.ctl;
   if (ctl->done) return;
   const int64_t t = ctl->t;
@@ -68,9 +68,8 @@ __global__ void __launch_bounds__(kThreads) k1_rows(RowArgs a) {
   const double ha = ctl->ha, hb = ctl->hb, he = ctl->he;
   const double sigma = ctl->sigma, inv_sigma = ctl->inv_sigma;
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  const int lane = threadIdx.x & 31;
   const LoadPolicy pol = make_policy();
-  for_each_row(a.bins, a.rp, a.ci, a.val, xh, pol, [&](int i, double v) {
+  for_each_row(a.bins, a.rp, a.ci, a.val, xh, pol, s, [&](int i, double v, double (&acc)[kNumSums]) {
     double yi, axi, y0i;
     if (mode == 0) {
       y0i = a.y0[i];
@@ -92,14 +91,14 @@ __global__ void __launch_bounds__(kThreads) k1_rows(RowArgs a) {
     const double sv = fma(-yi, inv_sigma, w);
     const double yn = sigma * (clampd(sv, lo, hi) - sv);
     const double dy = yi - yn;
-    s[0] = fma(dy, dy, s[0]);
-    s[1] = fma(dy, axi - v, s[1]);
+    acc[0] = fma(dy, dy, acc[0]);
+    acc[1] = fma(dy, axi - v, acc[1]);
     const double d0 = yn - y0i;
-    s[2] = fma(d0, d0, s[2]);
+    acc[2] = fma(d0, d0, acc[2]);
     if (check) {
       const double pr = (v - clampd(v, lo, hi)) * a.inv_dr[i];
-      s[3] = fma(pr, pr, s[3]);
-      s[4] += (yn > 0.0 ? lo * yn : 0.0) + (yn < 0.0 ? hi * yn : 0.0);
+      acc[3] = fma(pr, pr, acc[3]);
+      acc[4] += (yn > 0.0 ? lo * yn : 0.0) + (yn < 0.0 ? hi * yn : 0.0);
     }
     if (mode != 2) {
       a.y[i] = yi;
@@ -108,15 +107,15 @@ __global__ void __launch_bounds__(kThreads) k1_rows(RowArgs a) {
     a.yh[i] = yn;
     a.axh[i] = v;
   });
-  if (!block_sums_last(s, a.partials, &ctl->count1)) return;
-  if (threadIdx.x >= 32) return;
+  const int nsums = check ? 5 : 3;
+  if (!block_sums_last(s, nsums, a.partials, &ctl->count1)) return;
   double tot[kNumSums];
-  total_partials(a.partials, gridDim.x, tot);
-  if (lane != 0) return;
+  block_totals(a.partials, gridDim.x, nsums, &a.bins, tot);
+  if (threadIdx.x != 0) return;
 
   // ---- scalar control (one thread) ----
   const double eta = ctl->eta, om = ctl->omega;
-  const double r2 = (om / eta) * ctl->sxx + tot[0] / (eta * om) + 2.0 * tot[1];
+  const double r2 = fma(ctl->w_over_eta, ctl->sxx, fma(ctl->inv_eta_w, tot[0], 2.0 * tot[1]));
   const double r = sqrt(r2 > 0.0 ? r2 : 0.0);
   const int64_t k = ctl->k;
   if (k == 0) ctl->r0 = r;
@@ -148,6 +147,8 @@ __global__ void __launch_bounds__(kThreads) k1_rows(RowArgs a) {
     ctl->tau = eta / omn;
     ctl->sigma = eta * omn;
     ctl->inv_sigma = 1.0 / (eta * omn);
+    ctl->w_over_eta = omn / eta;
+    ctl->inv_eta_w = 1.0 / (eta * omn);
     ctl->k = 0;
     ctl->restarts += 1;
     if (tr) a.trace[4 * t + 2] = 1.0;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) k1_rows(RowArgs a) {
   ctl->restart = rs;
 }
 
-__global__ void __launch_bounds__(kThreads) k2_cols(ColArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k2_cols(ColArgs a) {
   Ctl* ctl = a.ctl;
   if (ctl->done) return;
   const int64_t t = ctl->t;
@@ -173,9 +174,8 @@ __global__ void __launch_bounds__(kThreads) k2_cols(ColArgs a) {
   const int restart = ctl->restart;
   const double ha = ctl->ha, hb = ctl->hb, he = ctl->he, tau = ctl->tau;
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  const int lane = threadIdx.x & 31;
   const LoadPolicy pol = make_policy();
-  for_each_row(a.bins, a.rp, a.ci, a.val, a.yh, pol, [&](int j, double u) {
+  for_each_row(a.bins, a.rp, a.ci, a.val, a.yh, pol, s, [&](int j, double u, double (&acc)[kNumSums]) {
     const double xc = xc_buf[j];
     double xj, atyj, x0j;
     if (restart) {
@@ -192,27 +192,27 @@ __global__ void __launch_bounds__(kThreads) k2_cols(ColArgs a) {
     const double cj = a.c[j], lo = a.lv[j], hi = a.uv[j];
     const double xn = clampd(fma(-tau, cj - atyj, xj), lo, hi);
     const double dx = xj - xn;
-    s[0] = fma(dx, dx, s[0]);
+    acc[0] = fma(dx, dx, acc[0]);
     const double d0 = xn - x0j;
-    s[1] = fma(d0, d0, s[1]);
+    acc[1] = fma(d0, d0, acc[1]);
     if (check) {
-      s[2] = fma(cj, xc, s[2]);
+      acc[2] = fma(cj, xc, acc[2]);
       const double rc = cj - u;
       const bool fl = isfinite(lo), fu = isfinite(hi);
       const double rr = (fl && fu) ? rc : (fl ? fmax(rc, 0.0) : (fu ? fmin(rc, 0.0) : 0.0));
       const double dd = (rc - rr) * a.inv_dc[j];
-      s[3] = fma(dd, dd, s[3]);
-      s[4] += (rr > 0.0 ? lo * rr : 0.0) + (rr < 0.0 ? hi * rr : 0.0);
+      acc[3] = fma(dd, dd, acc[3]);
+      acc[4] += (rr > 0.0 ? lo * rr : 0.0) + (rr < 0.0 ? hi * rr : 0.0);
     }
     a.x[j] = xj;
     a.aty[j] = atyj;
     xn_buf[j] = xn;
   });
-  if (!block_sums_last(s, a.partials, &ctl->count2)) return;
-  if (threadIdx.x >= 32) return;
+  const int nsums = check ? 5 : 2;
+  if (!block_sums_last(s, nsums, a.partials, &ctl->count2)) return;
   double tot[kNumSums];
-  total_partials(a.partials, gridDim.x, tot);
-  if (lane != 0) return;
+  block_totals(a.partials, gridDim.x, nsums, &a.bins, tot);
+  if (threadIdx.x != 0) return;
 
   ctl->sxx = tot[0];
   ctl->sx0 = tot[1];
@@ -275,11 +275,10 @@ __global__ void __launch_bounds__(kThreads) k_init_cols(int32_t n, const double*
     aty0[j] = 0.0;
     s[0] = fma(xn, xn, s[0]);
   }
-  if (!block_sums_last(s, partials, &ctl->count0)) return;
-  if (threadIdx.x >= 32) return;
+  if (!block_sums_last(s, 1, partials, &ctl->count0)) return;
   double tot[kNumSums];
-  total_partials(partials, gridDim.x, tot);
-  if ((threadIdx.x & 31) != 0) return;
+  block_totals(partials, gridDim.x, 1, nullptr, tot);
+  if (threadIdx.x != 0) return;
   ctl->sxx = tot[0];
   ctl->sx0 = tot[0];
   ctl->count0 = 0;
@@ -326,7 +325,8 @@ __global__ void __launch_bounds__(kThreads) k_spmv(const int32_t* __restrict__ r
                                                    const double* __restrict__ x,
                                                    double* __restrict__ y, BinTable bins) {
   const LoadPolicy pol = make_policy();
-  for_each_row(bins, rp, ci, val, x, pol, [&](int i, double v) { y[i] = v; });
+  double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for_each_row(bins, rp, ci, val, x, pol, s, [&](int i, double v, double (&)[kNumSums]) { y[i] = v; });
 }
 
 }  // namespace pdhg

@@ -107,11 +107,10 @@ __global__ void __launch_bounds__(kThreads) k_pw_start(int32_t n, const int32_t*
     u[j] = v;
     s[0] = fma(v, v, s[0]);
   }
-  if (!block_sums_last(s, partials, &pw->count_b)) return;
-  if (threadIdx.x >= 32) return;
+  if (!block_sums_last(s, 1, partials, &pw->count_b)) return;
   double tot[kNumSums];
-  total_partials(partials, gridDim.x, tot);
-  if ((threadIdx.x & 31) != 0) return;
+  block_totals(partials, gridDim.x, 1, nullptr, tot);
+  if (threadIdx.x != 0) return;
   pw->s = tot[0] > 0.0 ? 1.0 / sqrt(tot[0]) : 0.0;
   pw->count_b = 0;
 }
@@ -126,15 +125,14 @@ __global__ void __launch_bounds__(kThreads) k_pw_rows(const int32_t* __restrict_
   const double sc = pw->s;
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const LoadPolicy pol = make_policy();
-  for_each_row(bins, rp, ci, val, u, pol, [&](int i, double v) {
+  for_each_row(bins, rp, ci, val, u, pol, s, [&](int i, double v, double (&acc)[kNumSums]) {
     v *= sc;
     w[i] = v;
-    s[0] = fma(v, v, s[0]);
+    acc[0] = fma(v, v, acc[0]);
   });
-  if (!block_sums_last(s, partials, &pw->count_a)) return;
-  if (threadIdx.x >= 32) return;
+  if (!block_sums_last(s, 1, partials, &pw->count_a)) return;
   double tot[kNumSums];
-  total_partials(partials, gridDim.x, tot);
+  block_totals(partials, gridDim.x, 1, &bins, tot);
   if (threadIdx.x != 0) return;
   pw->lambda = tot[0];
   pw->count_a = 0;
@@ -149,14 +147,13 @@ __global__ void __launch_bounds__(kThreads) k_pw_cols(const int32_t* __restrict_
                                                       PwCtl* pw, double* partials) {
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const LoadPolicy pol = make_policy();
-  for_each_row(bins, rp, ci, val, w, pol, [&](int j, double v) {
+  for_each_row(bins, rp, ci, val, w, pol, s, [&](int j, double v, double (&acc)[kNumSums]) {
     u[j] = v;
-    s[0] = fma(v, v, s[0]);
+    acc[0] = fma(v, v, acc[0]);
   });
-  if (!block_sums_last(s, partials, &pw->count_b)) return;
-  if (threadIdx.x >= 32) return;
+  if (!block_sums_last(s, 1, partials, &pw->count_b)) return;
   double tot[kNumSums];
-  total_partials(partials, gridDim.x, tot);
+  block_totals(partials, gridDim.x, 1, &bins, tot);
   if (threadIdx.x != 0) return;
   pw->s = tot[0] > 0.0 ? 1.0 / sqrt(tot[0]) : 0.0;
   pw->count_b = 0;

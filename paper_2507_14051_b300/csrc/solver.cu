@@ -141,31 +141,42 @@ lp_status check_params(const lp_params& p) {
   return LP_OK;
 }
 
-// Schedule over rows already sorted by decreasing length class: the leading rows longer than
-// kCtaRowMin go one per CTA; each remaining class becomes a bin with G lanes per row (about
-// lane_target entries per lane and pass) and R rows per warp task (about kTileNnz entries).
-BinTable make_bins(const std::vector<int32_t>& rp, int lane_target) {
+// Schedule over rows already sorted by decreasing length class.  The leading rows longer than
+// kLongRowMin become chunk tasks of kChunkNnz entries.  Each remaining length class becomes a
+// bin whose warp task is a tile of R = min(32, 32 * lane_target / Lc) rows (Lc the class's
+// longest length) read in a single pass with G = 32 / R lanes per row, i.e. at most
+// lane_target entries per lane.
+BinTable make_bins(const std::vector<int32_t>& rp, int lane_target, std::vector<int4>& chunks) {
   BinTable bt{};
   const int32_t rows = (int32_t)rp.size() - 1;
   int32_t r = 0;
-  while (r < rows && rp[r + 1] - rp[r] > kCtaRowMin) ++r;
-  bt.cta_rows = r;
+  chunks.clear();
+  while (r < rows && rp[r + 1] - rp[r] > kLongRowMin) {
+    const int32_t nch = (rp[r + 1] - rp[r] + kChunkNnz - 1) / kChunkNnz;
+    const int32_t first = (int32_t)chunks.size();
+    for (int32_t q = 0; q < nch; ++q) chunks.push_back(make_int4(r, first, nch, 0));
+    ++r;
+  }
+  bt.long_rows = r;
+  bt.nchunks = (int32_t)chunks.size();
   int32_t task = 0;
   while (r < rows) {
     const int cls = length_class(rp[r + 1] - rp[r]);
     int32_t e = r + 1;
     while (e < rows && length_class(rp[e + 1] - rp[e]) == cls) ++e;
     const int64_t lc = int64_t(1) << cls;
-    int G = 1;
-    while (G < 32 && int64_t(G) * 2 * lane_target <= lc) G *= 2;
-    int64_t rr = kTileNnz / lc;
-    const int R = (int)(rr < 1 ? 1 : (rr > 32 ? 32 : rr));
+    int64_t rr = (int64_t)32 * lane_target / lc;
+    int R = (int)(rr < 1 ? 1 : (rr > 32 ? 32 : rr));
+    int Rp = 1;
+    while (Rp * 2 <= R) Rp *= 2;  // a power of two, so that G = 32 / R is one too
+    R = Rp;
     Bin& b = bt.bin[bt.nbins++];
     b.row0 = r;
     b.row1 = e;
-    b.lanes = G;
+    b.lanes = 32 / R;
     b.rows_per_tile = R;
     b.task0 = task;
+    b.per_lane = (int32_t)((lc + b.lanes - 1) / b.lanes);
     task += (e - r + R - 1) / R;
     r = e;
   }
@@ -364,18 +375,17 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
       ciT[pos] = i;
       valT[pos] = valA[q];
     }
-  h->binsA = make_bins(rpA, h->prm.lane_target);
-  h->binsT = make_bins(rpT, h->prm.lane_target);
+  std::vector<int4> chunksA, chunksT;
+  h->binsA = make_bins(rpA, h->prm.lane_target, chunksA);
+  h->binsT = make_bins(rpT, h->prm.lane_target, chunksT);
 
   int occA = 0, occT = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k1_rows, kThreads, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occT, k2_cols, kThreads, 0));
   if (occA < 1) occA = 1;
   if (occT < 1) occT = 1;
-  h->gridA = grid_for_tasks((int64_t)h->binsA.ntasks + (int64_t)h->binsA.cta_rows * kWarps, h->num_sms,
-                            occA * h->num_sms);
-  h->gridT = grid_for_tasks((int64_t)h->binsT.ntasks + (int64_t)h->binsT.cta_rows * kWarps, h->num_sms,
-                            occT * h->num_sms);
+  h->gridA = grid_for_tasks((int64_t)h->binsA.ntasks + h->binsA.nchunks, h->num_sms, occA * h->num_sms);
+  h->gridT = grid_for_tasks((int64_t)h->binsT.ntasks + h->binsT.nchunks, h->num_sms, occT * h->num_sms);
   h->gridV = grid_for(n > m ? n : m, kThreads, 4 * h->num_sms);
   h->max_grid = h->gridA > h->gridT ? h->gridA : h->gridT;
   if (h->gridV > h->max_grid) h->max_grid = h->gridV;
@@ -397,6 +407,22 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   CK(cudaMemset(h->pw, 0, sizeof(PwCtl)));
   h->trace_cap = h->prm.trace_cap;
   if (h->trace_cap > 0) CK(h->alloc(&h->trace, (size_t)h->trace_cap * 4));
+  for (auto [bt, ch] : {std::make_pair(&h->binsA, &chunksA), std::make_pair(&h->binsT, &chunksT)}) {
+    int4* d_chunk = nullptr;
+    double* d_part = nullptr;
+    double* d_contrib = nullptr;
+    unsigned* d_arr = nullptr;
+    CK(h->alloc(&d_chunk, ch->size()));
+    CK(h->alloc(&d_part, ch->size()));
+    CK(h->alloc(&d_contrib, (size_t)bt->long_rows * kNumSums));
+    CK(h->alloc(&d_arr, (size_t)bt->long_rows));
+    if (!ch->empty()) CK(cudaMemcpy(d_chunk, ch->data(), sizeof(int4) * ch->size(), cudaMemcpyHostToDevice));
+    CK(cudaMemset(d_arr, 0, sizeof(unsigned) * (bt->long_rows > 0 ? bt->long_rows : 1)));
+    bt->chunk = d_chunk;
+    bt->part = d_part;
+    bt->arrivals = d_arr;
+    bt->contrib = d_contrib;
+  }
 
   CK(cudaMemcpy(h->rpA, rpA.data(), sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->rpT, rpT.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
@@ -482,7 +508,7 @@ lp_status lp_default_params(lp_params* p) {
   p->pc_alpha = 1.0;
   p->trace_cap = 0;
   p->unroll = 8;
-  p->lane_target = 4;
+  p->lane_target = 8;
   return LP_OK;
 }
 
@@ -581,6 +607,8 @@ lp_status enqueue_start(lp_solver* h, double tol, int64_t max_iter, cudaStream_t
   init.tau = h->eta / h->prm.omega0;
   init.sigma = h->eta * h->prm.omega0;
   init.inv_sigma = 1.0 / (h->eta * h->prm.omega0);
+  init.w_over_eta = h->prm.omega0 / h->eta;
+  init.inv_eta_w = 1.0 / (h->eta * h->prm.omega0);
   init.restart_enabled = h->prm.restart_enabled;
   init.pid_enabled = h->prm.pid_enabled;
   init.max_iter = max_iter;
