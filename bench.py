@@ -37,7 +37,8 @@ sys.path.insert(0, ROOT)
 METRIC = "time to 1e-8 rel KKT, PDHG iter/s, SpMV+update HBM GB/s vs peak"
 FP64_NOMINAL_GOPS = 625.0  # 1.25 TFLOP/s FP64 per GPU (nominal) / 2 flops per DFMA
 FP64_MEASURED_GOPS = 474.0  # DFMA/DADD/DMUL issue rate measured by a register-only loop on a B300
-KERNEL_SOURCES = ("paper_2507_14051_b300/csrc/iterate.cu", "paper_2507_14051_b300/csrc/device.cuh")
+KERNEL_SOURCES = ("paper_2507_14051_b300/csrc/iterate.cu", "paper_2507_14051_b300/csrc/device.cuh",
+                  "paper_2507_14051_b300/csrc/kernels.cuh")
 
 
 def parse():
@@ -97,17 +98,18 @@ def source_digest() -> str:
 
 
 def measured_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernels."""
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel sources (digest) and on this workload; None otherwise."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             data = json.load(f)
     except (OSError, ValueError):
         return None
-    ent = data.get(kernel, {})
-    if ent.get("source_digest") != source_digest() or ent.get("workload") != workload:
+    if data.get("source_digest") != source_digest():
         return None
-    return ent.get("dram_bytes_per_launch")
+    ent = data.get(kernel, {}).get(workload)
+    return None if ent is None else ent.get("dram_bytes_per_launch")
 
 
 def load_peaks():
@@ -253,6 +255,7 @@ def run_ours(args):
         solver.solve(args.tol, args.max_iter, sp)
         lpx.lp_get(solver.h)
     torch.cuda.synchronize()
+    persistent = bool(lpx.lp_get_info(solver.h)[7])
 
     if world > 1:
         dist.barrier()
@@ -274,7 +277,8 @@ def run_ours(args):
         statuses.append(st)
         kkts.append(kkt.tolist())
         total_iters += it
-        launches += 3 + math.ceil(it / unroll) * (2 * unroll + 1)
+        bodies = math.ceil(it / unroll)
+        launches += 3 + (bodies if persistent else bodies * (2 * unroll + 1))
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -287,7 +291,13 @@ def run_ours(args):
     kt = lpx.lp_time_kernels(solver.h, args.kernel_iters, sp)
     work = kernel_work(lp)
     hbm_peak, peak_src = load_peaks()
-    per = {"k1_rows": kt[0], "k2_cols": kt[1]}
+    if kt[1] == 0.0:  # the cooperative loop kernel runs kt[2] iterations per launch
+        per_iter = int(kt[2])
+        work = {"k_loop": (per_iter * (work["k1_rows"][0] + work["k2_cols"][0]),
+                           per_iter * (work["k1_rows"][1] + work["k2_cols"][1]))}
+        per = {"k_loop": kt[0]}
+    else:
+        per = {"k1_rows": kt[0], "k2_cols": kt[1]}
     dom = max(per, key=per.get)
     bytes_, ops = work[dom]
     ms = per[dom]
@@ -303,12 +313,13 @@ def run_ours(args):
                 "traffic": traffic, "kernel": dom}
     roof.update({"peak_source": f"HBM {peak_src} copy {hbm_peak} GB/s; FP64 nominal {FP64_NOMINAL_GOPS} Gop/s "
                                 f"(measured issue rate {FP64_MEASURED_GOPS})",
-                 "kernels": {k: {"ms": per[k], "alg_bytes": work[k][0], "fp64_ops": work[k][1],
+                 "kernels": {k: {"ms_per_launch": per[k], "iters_per_launch": int(kt[2]),
+                                 "alg_bytes_per_launch": work[k][0], "fp64_ops_per_launch": work[k][1],
                                  "GB/s": work[k][0] / (per[k] * 1e-3) / 1e9,
                                  "frac_hbm": work[k][0] / (per[k] * 1e-3) / 1e9 / hbm_peak,
                                  "frac_fp64": work[k][1] / (per[k] * 1e-3) / 1e9 / FP64_NOMINAL_GOPS}
                              for k in per},
-                 "timing": f"mean of {int(kt[2])} launches each, CUDA events on the solve stream"})
+                 "timing": f"mean of {int(kt[3])} launches, CUDA events on the solve stream"})
 
     # end to end through the C ABI with host buffers: create (H2D inside) + solve + get (D2H)
     arrs = [np.ascontiguousarray(lp.row_ptr, np.int64), np.ascontiguousarray(lp.col_idx, np.int32),
@@ -361,6 +372,7 @@ def run_ours(args):
             "status_per_step": statuses, "rel_kkt_last": kkts[-1], "iters_per_step": total_iters / args.steps,
             "time_to_tol_s": (setup_ms / 1e3 + elapsed_s / args.steps) if solved else None,
             "setup_ms": setup_ms, "eta": float(info[0]), "restarts_last": int(info[2]),
+            "driver": "cooperative loop kernel" if persistent else "one kernel per phase",
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,

@@ -84,12 +84,16 @@ typedef struct {
   int64_t trace_cap;       /* > 0: record (r_t, omega_t, restart_t, k_t) for t < trace_cap */
   int32_t unroll;          /* iterations per body of the device-side loop (1..64) */
   int32_t lane_target;     /* SpMV schedule: at most this many nonzeros per lane and task (1..64) */
+  int32_t persistent;      /* 1: one cooperative kernel runs `unroll` iterations per launch with
+                              grid-wide barriers between phases; 0: one kernel per phase;
+                              -1: the first when every block of both phases fits on the GPU at
+                              once (latency-bound sizes), else the second */
 } lp_params;
 
 /* Fills p with the defaults: gamma 1, betas 0.2 / 0.8 / 0.36, K_P 0.5, K_I 0.001, K_D 0,
  * eta 0 (power iteration), omega0 1, check_every 64, restarts and PID on, power_tol 1e-7,
  * power_max_iter 10000, seed 0, Ruiz 10 + Pock-Chambolle alpha 1, no trace, unroll 8,
- * lane_target 8.  Returns LP_ERR_INVALID_ARG if p is NULL. */
+ * lane_target 8, persistent -1.  Returns LP_ERR_INVALID_ARG if p is NULL. */
 LP_API lp_status lp_default_params(lp_params* p);
 
 typedef struct lp_solver* lp_handle;
@@ -152,9 +156,10 @@ LP_API lp_status lp_get(lp_handle h, double* x, double* y, int32_t* solve_status
 
 /* Extra scalars of the last solve (host doubles): out[0] eta, out[1] final omega,
  * out[2] restarts, out[3] ||A~||_2 from the power iteration (0 if eta was given),
- * out[4] power-iteration steps, out[5] primal objective c^T x, out[6] dual objective.
+ * out[4] power-iteration steps, out[5] primal objective c^T x, out[6] dual objective,
+ * out[7] 1 if the cooperative loop kernel runs the solve, 0 if one kernel per phase does.
  * Waits like lp_get.  Errors: LP_ERR_INVALID_ARG, LP_ERR_NOT_SOLVED, LP_ERR_CUDA. */
-LP_API lp_status lp_get_info(lp_handle h, double* out7);
+LP_API lp_status lp_get_info(lp_handle h, double* out8);
 
 /* Copies up to cap rows of the per-iteration trace (r_t, omega_t, restart_t, k_t) into the
  * host array trace[4*cap]; *rows receives the number written.  Needs trace_cap > 0. */
@@ -167,12 +172,14 @@ LP_API void lp_destroy(lp_handle h);
 LP_API const char* lp_last_error(void);
 
 /*
- * Kernel timing for roofline reports: runs `iters` iterations of the same solve that lp_solve
- * would (tolerance 0, from the all-zero start) but launches the two iteration kernels one by
- * one on `stream` with CUDA events around each launch instead of through the graph.
- * ms_out[0] / ms_out[1]: mean duration of the row kernel (A x, dual step, restart control) and
- * of the column kernel (A^T y, primal step, KKT test); ms_out[2]: iterations timed.
- * Synchronous.  Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
+ * Kernel timing for roofline reports: runs at least `iters` iterations of the same solve that
+ * lp_solve would (tolerance 0, from the all-zero start), launching the iteration kernels one
+ * by one on `stream` with CUDA events around each launch instead of through the graph.
+ *   persistent = 0: ms_out[0] / ms_out[1] mean duration of the row kernel (A x, dual step,
+ *     restart control) and of the column kernel (A^T y, primal step, KKT test), ms_out[2] = 1;
+ *   persistent = 1: ms_out[0] mean duration of one launch of the loop kernel, ms_out[1] = 0,
+ *     ms_out[2] = iterations per launch (unroll).
+ * ms_out[3] = launches timed.  Synchronous.  Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
  */
 LP_API lp_status lp_time_kernels(lp_handle h, int64_t iters, void* stream, double* ms_out);
 

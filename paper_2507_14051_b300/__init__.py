@@ -62,6 +62,7 @@ class lp_params(C.Structure):
         ("trace_cap", C.c_int64),
         ("unroll", C.c_int32),
         ("lane_target", C.c_int32),
+        ("persistent", C.c_int32),
     ]
 
 
@@ -178,7 +179,7 @@ def lp_get(h, x=None, y=None):
 
 
 def lp_get_info(h) -> np.ndarray:
-    out = np.zeros(7)
+    out = np.zeros(8)
     _check(load().lp_get_info(h, out.ctypes.data_as(C.POINTER(C.c_double))), "lp_get_info")
     return out
 
@@ -197,8 +198,9 @@ def lp_destroy(h) -> None:
 
 
 def lp_time_kernels(h, iters: int, stream: int | None = None) -> np.ndarray:
-    """[mean ms of the row kernel, mean ms of the column kernel, iterations timed]."""
-    out = np.zeros(3)
+    """[ms per launch of the row (or loop) kernel, ms per launch of the column kernel (0 for
+    the loop kernel), iterations per launch, launches timed]."""
+    out = np.zeros(4)
     _check(load().lp_time_kernels(h, int(iters), stream, out.ctypes.data_as(C.POINTER(C.c_double))),
            "lp_time_kernels")
     return out
@@ -263,7 +265,7 @@ class Solver:
         info = lp_get_info(self.h)
         return dict(x=x, y=y, status=st, kkt=kkt, iters=it, eta=info[0], omega=info[1],
                     restarts=int(info[2]), norm_A=info[3], power_iters=int(info[4]),
-                    pobj=info[5], dobj=info[6])
+                    pobj=info[5], dobj=info[6], persistent=bool(info[7]))
 
     def trace(self):
         return lp_get_trace(self.h, int(self.params.trace_cap))

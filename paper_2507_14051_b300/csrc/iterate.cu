@@ -1,9 +1,9 @@
 // Iteration kernels of restarted reflected-Halpern PDHG (cuPDLPx, arXiv 2507.14051).
 //
-// One iteration t is two streaming kernels, each fused with its epilogue and closed by the
-// block that finishes last (a deterministic fixed-order reduction plus the scalar control):
+// One iteration t has two streaming phases, each fused with its epilogue and followed by a
+// deterministic fixed-order reduction and the scalar control:
 //
-//   K1 (rows of A, gathers xhat_t):
+//   row phase (rows of A, gathers xhat_t):
 //     deferred Halpern update of the y side decided at t-1 (Section 3, reflected Halpern):
 //       y  <- ha*yhat + hb*y + he*y0,  Ax <- ha*Axhat + hb*Ax + he*Ax0   (or <- yhat, Axhat
 //       at a restart, which also resets the anchors);
@@ -12,243 +12,387 @@
 //       s = A xbar - y/sigma;
 //     sums |y - yhat|^2, (y - yhat)^T (Ax - Axhat), |yhat - y0|^2 and, on check iterations,
 //       the primal residual and the y part of the dual objective (Section 4);
-//     last block: fixed-point residual r_t = ||z - T z||_P (Section 2.2 P, Section 3),
-//       restart test (Section 3, three conditions), PID update of omega (Section 3).
-//   K2 (rows of A^T, gathers yhat_t):
-//     u = A^T yhat_t; x side of the Halpern update (decided by K1 of this iteration), the
-//       maintained A^T y likewise; next primal step (eq. pdhg first line)
+//     control: fixed-point residual r_t = ||z - T z||_P (Section 2.2 P, Section 3), restart
+//       test (Section 3, three conditions), PID update of omega (Section 3).
+//   column phase (rows of A^T, gathers yhat_t):
+//     u = A^T yhat_t; x side of the Halpern update (decided by the row phase of this
+//       iteration), the maintained A^T y likewise; next primal step (eq. pdhg first line)
 //       xhat_{t+1} = proj_X(x - tau (c - A^T y));
 //     sums |x - xhat_{t+1}|^2, |xhat_{t+1} - x0|^2 and, on check iterations, c^T xhat_t, the
 //       dual residual and the r part of the dual objective (Section 4);
-//     last block: relative KKT test (Section 4) -> done / status.
+//     control: relative KKT test (Section 4) -> done / status.
+//
+// Two drivers run these phases with the same device functions:
+//   * k_loop: one cooperative (persistent) kernel that runs up to `iters` iterations, with a
+//     grid-wide barrier after each phase; every block then reads all block partials in the same
+//     order and computes the same control decision itself (its copy of the scalar state lives
+//     in shared memory; block 0 writes it back).  No last-block serialisation, no launches
+//     between phases.
+//   * k1_rows / k2_cols: one kernel per phase; the block that finishes last reduces the
+//     partials and runs the control on the global scalar state.
 //
 // A x and A^T y of the current iterate are maintained by the same affine updates as x and y
 // (exact in exact arithmetic; refreshed from true products at every restart), so one SpMV
 // per side per iteration suffices.
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pdhg {
 
-__device__ __forceinline__ bool is_check(const Ctl* ctl, int64_t t) {
-  return ((t + 1) % ctl->check_every) == 0 || (t + 1 == ctl->max_iter);
+__device__ __forceinline__ bool is_check(const Ctl& c, int64_t t) {
+  return ((t + 1) % c.check_every) == 0 || (t + 1 == c.max_iter);
 }
 
 // Restart test, Section 3: (1) r <= b_s r0; (2) r <= b_n r0 and r > r_prev; (3) k >= b_a T.
-__device__ __forceinline__ int restart_test(const Ctl* ctl, int64_t k, int64_t t, double r) {
+__device__ __forceinline__ int restart_test(const Ctl& c, int64_t k, int64_t t, double r) {
   if (k < 1) return 0;
-  if (r <= ctl->beta_s * ctl->r0) return 1;
-  if (r <= ctl->beta_n * ctl->r0 && r > ctl->r_prev) return 1;
-  if ((double)k >= ctl->beta_a * (double)(t + 1)) return 1;
+  if (r <= c.beta_s * c.r0) return 1;
+  if (r <= c.beta_n * c.r0 && r > c.r_prev) return 1;
+  if ((double)k >= c.beta_a * (double)(t + 1)) return 1;
   return 0;
 }
 
 // PID primal weight update, Section 3: e = log(sqrt(w)|dx| / (|dy|/sqrt(w))),
 // log w <- log w - (K_P e + K_I sum e + K_D (e - e_prev)); skipped when a norm is 0 or not
 // finite; log w kept in [-23, 23].
-__device__ __forceinline__ double pid_update(Ctl* ctl, double omega, double dxn, double dyn) {
+__device__ __forceinline__ double pid_update(Ctl& c, double omega, double dxn, double dyn) {
   if (!(dxn > 0.0) || !(dyn > 0.0) || !isfinite(dxn) || !isfinite(dyn)) return omega;
   const double sw = sqrt(omega);
   const double e = log((sw * dxn) / (dyn / sw));
-  ctl->pid_integral += e;
-  const double de = ctl->pid_has_prev ? e - ctl->pid_eprev : 0.0;
-  double lw = log(omega) - (ctl->kp * e + ctl->ki * ctl->pid_integral + ctl->kd * de);
+  c.pid_integral += e;
+  const double de = c.pid_has_prev ? e - c.pid_eprev : 0.0;
+  double lw = log(omega) - (c.kp * e + c.ki * c.pid_integral + c.kd * de);
   lw = fmin(fmax(lw, -23.0), 23.0);
-  ctl->pid_eprev = e;
-  ctl->pid_has_prev = 1;
+  c.pid_eprev = e;
+  c.pid_has_prev = 1;
   return exp(lw);
 }
+
+// ------------------------------------------------------------------ row phase
+
+struct RowStep {
+  int mode;  // 0 Halpern combine, 1 restart, 2 first iteration (state is zero)
+  int check;
+  double ha, hb, he, sigma, inv_sigma;
+};
+
+__device__ __forceinline__ RowStep row_step(const Ctl& c) {
+  RowStep st;
+  st.mode = (c.t == 0) ? 2 : c.restart;
+  st.check = is_check(c, c.t) ? 1 : 0;
+  st.ha = c.ha;
+  st.hb = c.hb;
+  st.he = c.he;
+  st.sigma = c.sigma;
+  st.inv_sigma = c.inv_sigma;
+  return st;
+}
+
+__device__ __forceinline__ void row_epilogue(const RowArgs& a, const RowStep& st, int i, double v,
+                                             double (&acc)[kNumSums]) {
+  double yi, axi, y0i;
+  if (st.mode == 0) {
+    y0i = a.y0[i];
+    yi = fma(st.ha, a.yh[i], fma(st.hb, a.y[i], st.he * y0i));
+    axi = fma(st.ha, a.axh[i], fma(st.hb, a.ax[i], st.he * a.ax0[i]));
+  } else if (st.mode == 1) {
+    yi = a.yh[i];
+    axi = a.axh[i];
+    y0i = yi;
+    a.y0[i] = yi;
+    a.ax0[i] = axi;
+  } else {
+    yi = 0.0;
+    axi = 0.0;
+    y0i = 0.0;
+  }
+  const double lo = a.lc[i], hi = a.uc[i];
+  const double w = fma(2.0, v, -axi);  // A(2 xhat - x)
+  const double sv = fma(-yi, st.inv_sigma, w);
+  const double yn = st.sigma * (clampd(sv, lo, hi) - sv);
+  const double dy = yi - yn;
+  acc[0] = fma(dy, dy, acc[0]);
+  acc[1] = fma(dy, axi - v, acc[1]);
+  const double d0 = yn - y0i;
+  acc[2] = fma(d0, d0, acc[2]);
+  if (st.check) {
+    const double pr = (v - clampd(v, lo, hi)) * a.inv_dr[i];
+    acc[3] = fma(pr, pr, acc[3]);
+    acc[4] += (yn > 0.0 ? lo * yn : 0.0) + (yn < 0.0 ? hi * yn : 0.0);
+  }
+  if (st.mode != 2) {
+    a.y[i] = yi;
+    a.ax[i] = axi;
+  }
+  a.yh[i] = yn;
+  a.axh[i] = v;
+}
+
+// Scalar control after the row phase of iteration c.t, on totals tot[0..2] (and tot[3..4] on
+// check iterations).  Writes the trace row if `trace` is given.
+__device__ __forceinline__ void row_control(Ctl& c, const double (&tot)[kNumSums], bool check,
+                                            double* trace) {
+  const int64_t t = c.t;
+  const double eta = c.eta, om = c.omega;
+  const double r2 = fma(c.w_over_eta, c.sxx, fma(c.inv_eta_w, tot[0], 2.0 * tot[1]));
+  const double r = sqrt(r2 > 0.0 ? r2 : 0.0);
+  const int64_t k = c.k;
+  if (k == 0) c.r0 = r;
+  if (check) {
+    c.pres2 = tot[3];
+    c.dobj_y = tot[4];
+  }
+  c.omega_used = om;
+  c.restarts_used = c.restarts;
+  const bool tr = trace != nullptr && t < c.trace_cap;
+  if (tr) {
+    trace[4 * t + 0] = r;
+    trace[4 * t + 1] = om;
+    trace[4 * t + 2] = 0.0;
+    trace[4 * t + 3] = (double)k;
+  }
+  if (!isfinite(r2)) {
+    c.status = kNumerical;
+    c.iters = t + 1;
+    c.done = 1;
+    return;
+  }
+  const int rs = c.restart_enabled && (t + 1 < c.max_iter) ? restart_test(c, k, t, r) : 0;
+  if (rs) {
+    double omn = om;
+    if (c.pid_enabled) omn = pid_update(c, om, sqrt(c.sx0), sqrt(tot[2]));
+    c.omega = omn;
+    c.tau = eta / omn;
+    c.sigma = eta * omn;
+    c.inv_sigma = 1.0 / (eta * omn);
+    c.w_over_eta = omn / eta;
+    c.inv_eta_w = 1.0 / (eta * omn);
+    c.k = 0;
+    c.restarts += 1;
+    if (tr) trace[4 * t + 2] = 1.0;
+  } else {
+    const double kk = (double)k;
+    const double aw = (kk + 1.0) / (kk + 2.0);
+    c.ha = aw * (1.0 + c.gamma);
+    c.hb = -aw * c.gamma;
+    c.he = 1.0 / (kk + 2.0);
+    c.r_prev = r;
+    c.k = k + 1;
+  }
+  c.restart = rs;
+}
+
+// --------------------------------------------------------------- column phase
+
+struct ColStep {
+  int restart;
+  int check;
+  double ha, hb, he, tau;
+  const double* xc;  // xhat_t
+  double* xn;        // xhat_{t+1}
+};
+
+__device__ __forceinline__ ColStep col_step(const Ctl& c, const ColArgs& a) {
+  ColStep st;
+  st.restart = c.restart;
+  st.check = is_check(c, c.t) ? 1 : 0;
+  st.ha = c.ha;
+  st.hb = c.hb;
+  st.he = c.he;
+  st.tau = c.tau;
+  st.xc = (c.t & 1) ? a.xh1 : a.xh0;
+  st.xn = (c.t & 1) ? a.xh0 : a.xh1;
+  return st;
+}
+
+__device__ __forceinline__ void col_epilogue(const ColArgs& a, const ColStep& st, int j, double u,
+                                             double (&acc)[kNumSums]) {
+  const double xc = st.xc[j];
+  double xj, atyj, x0j;
+  if (st.restart) {
+    xj = xc;
+    atyj = u;
+    x0j = xc;
+    a.x0[j] = xc;
+    a.aty0[j] = u;
+  } else {
+    x0j = a.x0[j];
+    xj = fma(st.ha, xc, fma(st.hb, a.x[j], st.he * x0j));
+    atyj = fma(st.ha, u, fma(st.hb, a.aty[j], st.he * a.aty0[j]));
+  }
+  const double cj = a.c[j], lo = a.lv[j], hi = a.uv[j];
+  const double xn = clampd(fma(-st.tau, cj - atyj, xj), lo, hi);
+  const double dx = xj - xn;
+  acc[0] = fma(dx, dx, acc[0]);
+  const double d0 = xn - x0j;
+  acc[1] = fma(d0, d0, acc[1]);
+  if (st.check) {
+    acc[2] = fma(cj, xc, acc[2]);
+    const double rc = cj - u;
+    const bool fl = isfinite(lo), fu = isfinite(hi);
+    const double rr = (fl && fu) ? rc : (fl ? fmax(rc, 0.0) : (fu ? fmin(rc, 0.0) : 0.0));
+    const double dd = (rc - rr) * a.inv_dc[j];
+    acc[3] = fma(dd, dd, acc[3]);
+    acc[4] += (rr > 0.0 ? lo * rr : 0.0) + (rr < 0.0 ? hi * rr : 0.0);
+  }
+  a.x[j] = xj;
+  a.aty[j] = atyj;
+  st.xn[j] = xn;
+}
+
+// Scalar control after the column phase: carries the x-side sums to the next residual, runs
+// the relative KKT test on check iterations (Section 4), and advances t.
+__device__ __forceinline__ void col_control(Ctl& c, const double (&tot)[kNumSums], bool check) {
+  const int64_t t = c.t;
+  c.sxx = tot[0];
+  c.sx0 = tot[1];
+  if (check) {
+    const double pobj = tot[2], dobj = c.dobj_y + tot[4];
+    const double pres = sqrt(c.pres2), dres = sqrt(tot[3]);
+    const double rg = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+    const double rp = pres / (1.0 + c.lu_norm);
+    const double rd = dres / (1.0 + c.c_norm);
+    double mx = rg;
+    if (!(rp <= mx)) mx = rp;
+    if (!(rd <= mx)) mx = rd;
+    c.kkt[0] = rg;
+    c.kkt[1] = rp;
+    c.kkt[2] = rd;
+    c.kkt[3] = mx;
+    c.kkt[4] = pobj;
+    c.kkt[5] = dobj;
+    c.kkt[6] = pres;
+    c.kkt[7] = dres;
+    if (rg <= c.tol && rp <= c.tol && rd <= c.tol) {
+      c.status = kOptimal;
+      c.iters = t + 1;
+      c.done = 1;
+      return;
+    }
+  }
+  if (t + 1 >= c.max_iter) {
+    c.status = kIterLimit;
+    c.iters = t + 1;
+    c.done = 1;
+    return;
+  }
+  c.t = t + 1;
+}
+
+// ----------------------------------------------------------- one kernel per phase
 
 __global__ void __launch_bounds__(kThreads, 3) k1_rows(RowArgs a) {
   Ctl* ctl = a.ctl;
   if (ctl->done) return;
-  const int64_t t = ctl->t;
-  const bool check = is_check(ctl, t);
-  const double* __restrict__ xh = (t & 1) ? a.xh1 : a.xh0;
-  const int mode = (t == 0) ? 2 : ctl->restart;  // 0 combine, 1 restart, 2 first iteration
-  const double ha = ctl->ha, hb = ctl->hb, he = ctl->he;
-  const double sigma = ctl->sigma, inv_sigma = ctl->inv_sigma;
+  const RowStep st = row_step(*ctl);
+  const double* __restrict__ xh = (ctl->t & 1) ? a.xh1 : a.xh0;
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const LoadPolicy pol = make_policy();
-  for_each_row(a.bins, a.rp, a.ci, a.val, xh, pol, s, [&](int i, double v, double (&acc)[kNumSums]) {
-    double yi, axi, y0i;
-    if (mode == 0) {
-      y0i = a.y0[i];
-      yi = fma(ha, a.yh[i], fma(hb, a.y[i], he * y0i));
-      axi = fma(ha, a.axh[i], fma(hb, a.ax[i], he * a.ax0[i]));
-    } else if (mode == 1) {
-      yi = a.yh[i];
-      axi = a.axh[i];
-      y0i = yi;
-      a.y0[i] = yi;
-      a.ax0[i] = axi;
-    } else {
-      yi = 0.0;
-      axi = 0.0;
-      y0i = 0.0;
-    }
-    const double lo = a.lc[i], hi = a.uc[i];
-    const double w = fma(2.0, v, -axi);  // A(2 xhat - x)
-    const double sv = fma(-yi, inv_sigma, w);
-    const double yn = sigma * (clampd(sv, lo, hi) - sv);
-    const double dy = yi - yn;
-    acc[0] = fma(dy, dy, acc[0]);
-    acc[1] = fma(dy, axi - v, acc[1]);
-    const double d0 = yn - y0i;
-    acc[2] = fma(d0, d0, acc[2]);
-    if (check) {
-      const double pr = (v - clampd(v, lo, hi)) * a.inv_dr[i];
-      acc[3] = fma(pr, pr, acc[3]);
-      acc[4] += (yn > 0.0 ? lo * yn : 0.0) + (yn < 0.0 ? hi * yn : 0.0);
-    }
-    if (mode != 2) {
-      a.y[i] = yi;
-      a.ax[i] = axi;
-    }
-    a.yh[i] = yn;
-    a.axh[i] = v;
-  });
-  const int nsums = check ? 5 : 3;
+  for_each_row(a.bins, a.rp, a.ci, a.val, xh, pol, s,
+               [&](int i, double v, double (&acc)[kNumSums]) { row_epilogue(a, st, i, v, acc); });
+  const int nsums = st.check ? 5 : 3;
   if (!block_sums_last(s, nsums, a.partials, &ctl->count1)) return;
   double tot[kNumSums];
   block_totals(a.partials, gridDim.x, nsums, &a.bins, tot);
   if (threadIdx.x != 0) return;
-
-  // ---- scalar control (one thread) ----
-  const double eta = ctl->eta, om = ctl->omega;
-  const double r2 = fma(ctl->w_over_eta, ctl->sxx, fma(ctl->inv_eta_w, tot[0], 2.0 * tot[1]));
-  const double r = sqrt(r2 > 0.0 ? r2 : 0.0);
-  const int64_t k = ctl->k;
-  if (k == 0) ctl->r0 = r;
-  if (check) {
-    ctl->pres2 = tot[3];
-    ctl->dobj_y = tot[4];
-  }
-  ctl->omega_used = om;
-  ctl->restarts_used = ctl->restarts;
-  const bool tr = a.trace != nullptr && t < ctl->trace_cap;
-  if (tr) {
-    a.trace[4 * t + 0] = r;
-    a.trace[4 * t + 1] = om;
-    a.trace[4 * t + 2] = 0.0;
-    a.trace[4 * t + 3] = (double)k;
-  }
   ctl->count1 = 0;
-  if (!isfinite(r2)) {
-    ctl->status = kNumerical;
-    ctl->iters = t + 1;
-    ctl->done = 1;
-    return;
-  }
-  const int rs = ctl->restart_enabled && (t + 1 < ctl->max_iter) ? restart_test(ctl, k, t, r) : 0;
-  if (rs) {
-    double omn = om;
-    if (ctl->pid_enabled) omn = pid_update(ctl, om, sqrt(ctl->sx0), sqrt(tot[2]));
-    ctl->omega = omn;
-    ctl->tau = eta / omn;
-    ctl->sigma = eta * omn;
-    ctl->inv_sigma = 1.0 / (eta * omn);
-    ctl->w_over_eta = omn / eta;
-    ctl->inv_eta_w = 1.0 / (eta * omn);
-    ctl->k = 0;
-    ctl->restarts += 1;
-    if (tr) a.trace[4 * t + 2] = 1.0;
-  } else {
-    const double kk = (double)k;
-    const double aw = (kk + 1.0) / (kk + 2.0);
-    ctl->ha = aw * (1.0 + ctl->gamma);
-    ctl->hb = -aw * ctl->gamma;
-    ctl->he = 1.0 / (kk + 2.0);
-    ctl->r_prev = r;
-    ctl->k = k + 1;
-  }
-  ctl->restart = rs;
+  row_control(*ctl, tot, st.check, a.trace);
 }
 
 __global__ void __launch_bounds__(kThreads, 3) k2_cols(ColArgs a) {
   Ctl* ctl = a.ctl;
   if (ctl->done) return;
-  const int64_t t = ctl->t;
-  const bool check = is_check(ctl, t);
-  const double* __restrict__ xc_buf = (t & 1) ? a.xh1 : a.xh0;
-  double* __restrict__ xn_buf = (t & 1) ? a.xh0 : a.xh1;
-  const int restart = ctl->restart;
-  const double ha = ctl->ha, hb = ctl->hb, he = ctl->he, tau = ctl->tau;
+  const ColStep st = col_step(*ctl, a);
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const LoadPolicy pol = make_policy();
-  for_each_row(a.bins, a.rp, a.ci, a.val, a.yh, pol, s, [&](int j, double u, double (&acc)[kNumSums]) {
-    const double xc = xc_buf[j];
-    double xj, atyj, x0j;
-    if (restart) {
-      xj = xc;
-      atyj = u;
-      x0j = xc;
-      a.x0[j] = xc;
-      a.aty0[j] = u;
-    } else {
-      x0j = a.x0[j];
-      xj = fma(ha, xc, fma(hb, a.x[j], he * x0j));
-      atyj = fma(ha, u, fma(hb, a.aty[j], he * a.aty0[j]));
-    }
-    const double cj = a.c[j], lo = a.lv[j], hi = a.uv[j];
-    const double xn = clampd(fma(-tau, cj - atyj, xj), lo, hi);
-    const double dx = xj - xn;
-    acc[0] = fma(dx, dx, acc[0]);
-    const double d0 = xn - x0j;
-    acc[1] = fma(d0, d0, acc[1]);
-    if (check) {
-      acc[2] = fma(cj, xc, acc[2]);
-      const double rc = cj - u;
-      const bool fl = isfinite(lo), fu = isfinite(hi);
-      const double rr = (fl && fu) ? rc : (fl ? fmax(rc, 0.0) : (fu ? fmin(rc, 0.0) : 0.0));
-      const double dd = (rc - rr) * a.inv_dc[j];
-      acc[3] = fma(dd, dd, acc[3]);
-      acc[4] += (rr > 0.0 ? lo * rr : 0.0) + (rr < 0.0 ? hi * rr : 0.0);
-    }
-    a.x[j] = xj;
-    a.aty[j] = atyj;
-    xn_buf[j] = xn;
-  });
-  const int nsums = check ? 5 : 2;
+  for_each_row(a.bins, a.rp, a.ci, a.val, a.yh, pol, s,
+               [&](int j, double u, double (&acc)[kNumSums]) { col_epilogue(a, st, j, u, acc); });
+  const int nsums = st.check ? 5 : 2;
   if (!block_sums_last(s, nsums, a.partials, &ctl->count2)) return;
   double tot[kNumSums];
   block_totals(a.partials, gridDim.x, nsums, &a.bins, tot);
   if (threadIdx.x != 0) return;
-
-  ctl->sxx = tot[0];
-  ctl->sx0 = tot[1];
   ctl->count2 = 0;
-  if (check) {
-    const double pobj = tot[2], dobj = ctl->dobj_y + tot[4];
-    const double pres = sqrt(ctl->pres2), dres = sqrt(tot[3]);
-    const double rg = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
-    const double rp = pres / (1.0 + ctl->lu_norm);
-    const double rd = dres / (1.0 + ctl->c_norm);
-    double mx = rg;
-    if (!(rp <= mx)) mx = rp;
-    if (!(rd <= mx)) mx = rd;
-    ctl->kkt[0] = rg;
-    ctl->kkt[1] = rp;
-    ctl->kkt[2] = rd;
-    ctl->kkt[3] = mx;
-    ctl->kkt[4] = pobj;
-    ctl->kkt[5] = dobj;
-    ctl->kkt[6] = pres;
-    ctl->kkt[7] = dres;
-    if (rg <= ctl->tol && rp <= ctl->tol && rd <= ctl->tol) {
-      ctl->status = kOptimal;
-      ctl->iters = t + 1;
-      ctl->done = 1;
-      return;
-    }
-  }
-  if (t + 1 >= ctl->max_iter) {
-    ctl->status = kIterLimit;
-    ctl->iters = t + 1;
-    ctl->done = 1;
-    return;
-  }
-  ctl->t = t + 1;
+  col_control(*ctl, tot, st.check);
 }
+
+// ------------------------------------------------------------ persistent loop
+
+// Sums each thread's values over the block and stores them as this block's partials.
+__device__ __forceinline__ void store_block_partials(double (&s)[kNumSums], int nsums, double* part) {
+  block_reduce(s, nsums);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < kNumSums; ++q) part[blockIdx.x * kNumSums + q] = s[q];
+  }
+}
+
+// Runs up to `iters` iterations (fewer if the solve finishes) with a grid-wide barrier after
+// each phase.  Must be launched cooperatively with every block resident.  Each block keeps an
+// identical copy of the scalar state in shared memory: all blocks read the same partials in the
+// same order and run the same control code, so their decisions agree bit for bit and every
+// block leaves the loop at the same barrier.  Block 0 writes the state back, writes the trace,
+// and (if use_cond) sets the device-side loop condition of the enclosing graph.
+__global__ void __launch_bounds__(kThreads, 3) k_loop(RowArgs ra, ColArgs ca, double* part_rows,
+                                                      double* part_cols, int32_t iters,
+                                                      cudaGraphConditionalHandle cond,
+                                                      int32_t use_cond) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ Ctl sc;
+  __shared__ RowStep rst;
+  __shared__ ColStep cst;
+  if (threadIdx.x == 0) sc = *ra.ctl;
+  __syncthreads();
+  const LoadPolicy pol = make_policy();
+  double* trace = blockIdx.x == 0 ? ra.trace : nullptr;
+  for (int32_t it = 0; it < iters && !sc.done; ++it) {
+    // ---- row phase
+    if (threadIdx.x == 0) rst = row_step(sc);
+    __syncthreads();
+    const RowStep st = rst;
+    const double* __restrict__ xh = (sc.t & 1) ? ra.xh1 : ra.xh0;
+    double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for_each_row(ra.bins, ra.rp, ra.ci, ra.val, xh, pol, s,
+                 [&](int i, double v, double (&acc)[kNumSums]) { row_epilogue(ra, st, i, v, acc); });
+    const int nr = st.check ? 5 : 3;
+    store_block_partials(s, nr, part_rows);
+    grid.sync();
+    double tot[kNumSums];
+    block_totals(part_rows, gridDim.x, nr, &ra.bins, tot);
+    if (threadIdx.x == 0) row_control(sc, tot, st.check, trace);
+    __syncthreads();
+    if (sc.done) break;
+    // ---- column phase
+    if (threadIdx.x == 0) cst = col_step(sc, ca);
+    __syncthreads();
+    const ColStep cs = cst;
+    double s2[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for_each_row(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, s2,
+                 [&](int j, double u, double (&acc)[kNumSums]) { col_epilogue(ca, cs, j, u, acc); });
+    const int nc = cs.check ? 5 : 2;
+    store_block_partials(s2, nc, part_cols);
+    grid.sync();
+    double tot2[kNumSums];
+    block_totals(part_cols, gridDim.x, nc, &ca.bins, tot2);
+    if (threadIdx.x == 0) col_control(sc, tot2, cs.check);
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc.bodies += 1;
+    if (!sc.done && sc.bodies > sc.max_iter / (iters > 0 ? iters : 1) + 2) {
+      sc.status = kInternalError;  // the loop outran max_iter: stop rather than spin
+      sc.iters = sc.t + 1;
+      sc.done = 1;
+    }
+    *ra.ctl = sc;
+    if (use_cond) cudaGraphSetConditional(cond, sc.done ? 0u : 1u);
+  }
+}
+
+// ----------------------------------------------------------------- start / misc
 
 // Installs the scalar state of a new solve (built on the host, passed by value so that
 // back-to-back solves on one stream cannot race on a host staging buffer).
@@ -296,10 +440,10 @@ __global__ void k_init_rows(int32_t m, double* y, double* y0, double* yh, double
   }
 }
 
-// Sets the device-side loop condition: keep iterating while the solve is not done.  Guard:
-// each body performs at most `unroll` iterations, so more than max_iter/unroll + 2 bodies
-// means the control logic failed to finish the solve; stop with an internal-error status
-// instead of looping.
+// Sets the device-side loop condition of the split-kernel graph: keep iterating while the solve
+// is not done.  Guard: each body performs at most `unroll` iterations, so more than
+// max_iter/unroll + 2 bodies means the control logic failed to finish the solve; stop with an
+// internal-error status instead of looping.
 __global__ void k_set_cond(cudaGraphConditionalHandle h, Ctl* ctl, int32_t unroll) {
   ctl->bodies += 1;
   if (!ctl->done && ctl->bodies > ctl->max_iter / unroll + 2) {

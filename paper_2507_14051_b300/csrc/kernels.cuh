@@ -36,11 +36,14 @@ struct ColArgs {
 struct PwCtl {
   double lambda, s;
   unsigned int count_a, count_b;
+  int32_t step;  // index of the current step inside a batch (lambda is also stored in hist[step])
 };
 
 // iterate.cu
 __global__ void k1_rows(RowArgs a);
 __global__ void k2_cols(ColArgs a);
+__global__ void k_loop(RowArgs ra, ColArgs ca, double* part_rows, double* part_cols, int32_t iters,
+                       cudaGraphConditionalHandle cond, int32_t use_cond);
 __global__ void k_init_ctl(Ctl* dst, Ctl src);
 __global__ void k_init_cols(int32_t n, const double* c, const double* lv, const double* uv,
                             double* xh0, double* x, double* x0, double* aty, double* aty0,
@@ -65,7 +68,8 @@ __global__ void k_scale_rows(int32_t m, const double* dr, double* lc, double* uc
 __global__ void k_pw_start(int32_t n, const int32_t* col_perm, uint64_t seed, double* u, PwCtl* pw,
                            double* partials);
 __global__ void k_pw_rows(const int32_t* rp, const int32_t* ci, const double* val, const double* u,
-                          double* w, BinTable bins, PwCtl* pw, double* partials);
+                          double* w, BinTable bins, PwCtl* pw, double* partials, double* hist,
+                          int32_t step);
 __global__ void k_pw_cols(const int32_t* rp, const int32_t* ci, const double* val, const double* w,
                           double* u, BinTable bins, PwCtl* pw, double* partials);
 

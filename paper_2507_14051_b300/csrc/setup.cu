@@ -115,13 +115,15 @@ __global__ void __launch_bounds__(kThreads) k_pw_start(int32_t n, const int32_t*
   pw->count_b = 0;
 }
 
-// w = s * (A u); lambda = |w|^2.
+// w = s * (A u); lambda = |w|^2, also recorded as hist[step] so that the host can apply the
+// stopping rule to a batch of steps after one synchronisation.
 __global__ void __launch_bounds__(kThreads) k_pw_rows(const int32_t* __restrict__ rp,
                                                       const int32_t* __restrict__ ci,
                                                       const double* __restrict__ val,
                                                       const double* __restrict__ u,
                                                       double* __restrict__ w, BinTable bins,
-                                                      PwCtl* pw, double* partials) {
+                                                      PwCtl* pw, double* partials, double* hist,
+                                                      int32_t step) {
   const double sc = pw->s;
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const LoadPolicy pol = make_policy();
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_pw_rows(const int32_t* __restrict_
   block_totals(partials, gridDim.x, 1, &bins, tot);
   if (threadIdx.x != 0) return;
   pw->lambda = tot[0];
+  hist[step] = tot[0];
   pw->count_a = 0;
 }
 

@@ -49,6 +49,8 @@ int grid_for_tasks(int64_t warp_tasks, int num_sms, int max_blocks) {
   return (int)g;
 }
 
+constexpr int kPwBatch = 16;  // power-iteration steps per host synchronisation
+
 int grid_for(int64_t work, int per_block, int cap) {
   int64_t g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -76,7 +78,9 @@ struct lp_solver {
   lp_params prm{};
   std::vector<int32_t> row_perm, col_perm;  // permuted index -> original index
   BinTable binsA{}, binsT{};
-  int gridA = 1, gridT = 1, gridV = 1, max_grid = 1;
+  int gridA = 1, gridT = 1, gridV = 1, gridL = 1, max_grid = 1;
+  bool loop_active = false;  // the graph body is the cooperative loop kernel
+  bool loop_fits = false;    // both phases' grids fit on the device at once
   // device storage
   int32_t *rpA = nullptr, *ciA = nullptr, *rpT = nullptr, *ciT = nullptr;
   double *valA = nullptr, *valT = nullptr;
@@ -87,6 +91,7 @@ struct lp_solver {
   double *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
   double* out_buf = nullptr;
   double* partials = nullptr;
+  double* partials2 = nullptr;  // column-phase partials of the loop kernel
   double* trace = nullptr;
   int64_t trace_cap = 0;
   Ctl* ctl = nullptr;
@@ -138,6 +143,7 @@ lp_status check_params(const lp_params& p) {
   if (p.trace_cap < 0) return fail(LP_ERR_INVALID_ARG, "trace_cap must be >= 0");
   if (p.unroll < 1 || p.unroll > 64) return fail(LP_ERR_INVALID_ARG, "unroll must be in [1, 64]");
   if (p.lane_target < 1 || p.lane_target > 64) return fail(LP_ERR_INVALID_ARG, "lane_target must be in [1, 64]");
+  if (p.persistent < -1 || p.persistent > 1) return fail(LP_ERR_INVALID_ARG, "persistent must be -1, 0 or 1");
   return LP_OK;
 }
 
@@ -238,44 +244,82 @@ void fill_args(const lp_solver* h, RowArgs& ra, ColArgs& ca) {
   ca.ctl = h->ctl; ca.partials = h->partials; ca.bins = h->binsT;
 }
 
-lp_status build_graph(lp_solver* h) {
-  if (h->exec) {
-    cudaGraphExecDestroy(h->exec);
-    h->exec = nullptr;
-  }
-  if (h->graph) {
-    cudaGraphDestroy(h->graph);
-    h->graph = nullptr;
-  }
-  RowArgs ra{};
-  ColArgs ca{};
-  fill_args(h, ra, ca);
-  CK(cudaGraphCreate(&h->graph, 0));
-  cudaGraphConditionalHandle cond;
-  CK(cudaGraphConditionalHandleCreate(&cond, h->graph, 1, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams cp{};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = cond;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t node;
-  CK(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &cp));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  cudaStream_t s = h->setup_stream;
-  CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  for (int u = 0; u < h->prm.unroll; ++u) {
-    k1_rows<<<h->gridA, kThreads, 0, s>>>(ra);
-    k2_cols<<<h->gridT, kThreads, 0, s>>>(ca);
-  }
-  k_set_cond<<<1, 1, 0, s>>>(cond, h->ctl, h->prm.unroll);
-  cudaGraph_t captured = nullptr;
-  cudaError_t e = cudaStreamEndCapture(s, &captured);
-  if (e != cudaSuccess) return fail(LP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  CK(cudaGraphInstantiate(&h->exec, h->graph, 0));
-  h->graph_unroll = h->prm.unroll;
-  return LP_OK;
+cudaError_t launch_loop(const lp_solver* h, const RowArgs& ra, const ColArgs& ca, int32_t iters,
+                        cudaGraphConditionalHandle cond, int32_t use_cond, cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)h->gridL);
+  cfg.blockDim = dim3((unsigned)kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_loop, ra, ca, h->partials, h->partials2, iters, cond, use_cond);
 }
 
+// Captures the solve loop: a graph whose conditional while node runs the body until the solve
+// is done.  Body: one cooperative launch of the loop kernel (`unroll` iterations; it sets the
+// loop condition itself) or, for persistent = 0 or if the driver refuses a cooperative kernel
+// in the body, `unroll` pairs of the phase kernels plus the kernel that sets the condition.
+lp_status build_graph(lp_solver* h) {
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (h->exec) {
+      cudaGraphExecDestroy(h->exec);
+      h->exec = nullptr;
+    }
+    if (h->graph) {
+      cudaGraphDestroy(h->graph);
+      h->graph = nullptr;
+    }
+    const bool want = h->prm.persistent == 1 || (h->prm.persistent == -1 && h->loop_fits);
+    const bool loop = want && attempt == 0;
+    RowArgs ra{};
+    ColArgs ca{};
+    fill_args(h, ra, ca);
+    CK(cudaGraphCreate(&h->graph, 0));
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, h->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t s = h->setup_stream;
+    CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    if (loop) {
+      le = launch_loop(h, ra, ca, h->prm.unroll, cond, 1, s);
+    } else {
+      for (int u = 0; u < h->prm.unroll; ++u) {
+        k1_rows<<<h->gridA, kThreads, 0, s>>>(ra);
+        k2_cols<<<h->gridT, kThreads, 0, s>>>(ca);
+      }
+      k_set_cond<<<1, 1, 0, s>>>(cond, h->ctl, h->prm.unroll);
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &captured);
+    if (e == cudaSuccess && le == cudaSuccess) e = cudaGraphInstantiate(&h->exec, h->graph, 0);
+    else if (e == cudaSuccess) e = le;
+    if (e == cudaSuccess) {
+      h->loop_active = loop;
+      h->graph_unroll = h->prm.unroll;
+      return LP_OK;
+    }
+    cudaGetLastError();  // clear the sticky-free launch error before retrying without the loop kernel
+    if (!loop) return fail(LP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  return fail(LP_ERR_CUDA, "graph capture failed");
+}
+
+// Power iteration (Section 3, "Stepsize") on the device.  Steps run in batches of kPwBatch
+// without host synchronisation; each step records its lambda, and the host then applies the
+// stopping rule step by step, so the estimate is the one of the first step that meets it (the
+// extra steps of the batch only refine the iterate, which is not used afterwards).
 lp_status run_power_iteration(lp_solver* h) {
   cudaStream_t s = h->setup_stream;
   h->pw_iters = 0;
@@ -285,23 +329,33 @@ lp_status run_power_iteration(lp_solver* h) {
   }
   double* u = h->x;  // scratch: the iterate buffers are free until the first solve
   double* w = h->y;
+  double* hist = h->out_buf;  // kPwBatch lambdas
   k_pw_start<<<h->gridV, kThreads, 0, s>>>(h->n, h->d_col_perm, h->prm.power_seed, u, h->pw, h->partials);
   CK(cudaGetLastError());
   double lam = 0.0, prev = 0.0;
-  int64_t it;
-  for (it = 1; it <= h->prm.power_max_iter; ++it) {
-    k_pw_rows<<<h->gridA, kThreads, 0, s>>>(h->rpA, h->ciA, h->valA, u, w, h->binsA, h->pw, h->partials);
-    CK(cudaMemcpyAsync(h->pinned, &h->pw->lambda, sizeof(double), cudaMemcpyDeviceToHost, s));
+  int64_t it = 0;
+  bool stop = false;
+  double got[kPwBatch];
+  while (!stop && it < h->prm.power_max_iter) {
+    const int64_t left = h->prm.power_max_iter - it;
+    const int batch = left < kPwBatch ? (int)left : kPwBatch;
+    for (int q = 0; q < batch; ++q) {
+      k_pw_rows<<<h->gridA, kThreads, 0, s>>>(h->rpA, h->ciA, h->valA, u, w, h->binsA, h->pw, h->partials,
+                                               hist, q);
+      k_pw_cols<<<h->gridT, kThreads, 0, s>>>(h->rpT, h->ciT, h->valT, w, u, h->binsT, h->pw, h->partials);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(got, hist, sizeof(double) * batch, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    lam = h->pinned[0];
-    if (lam == 0.0) break;
-    k_pw_cols<<<h->gridT, kThreads, 0, s>>>(h->rpT, h->ciT, h->valT, w, u, h->binsT, h->pw, h->partials);
-    if (it > 1 && std::fabs(lam - prev) <= h->prm.power_tol * lam) break;
-    prev = lam;
+    for (int q = 0; q < batch && !stop; ++q) {
+      ++it;
+      lam = got[q];
+      if (lam == 0.0) stop = true;
+      else if (it > 1 && std::fabs(lam - prev) <= h->prm.power_tol * lam) stop = true;
+      else prev = lam;
+    }
   }
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(s));
-  h->pw_iters = it > h->prm.power_max_iter ? h->prm.power_max_iter : it;
+  h->pw_iters = it;
   h->norm_A = std::sqrt(lam);
   return LP_OK;
 }
@@ -386,9 +440,16 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   if (occT < 1) occT = 1;
   h->gridA = grid_for_tasks((int64_t)h->binsA.ntasks + h->binsA.nchunks, h->num_sms, occA * h->num_sms);
   h->gridT = grid_for_tasks((int64_t)h->binsT.ntasks + h->binsT.nchunks, h->num_sms, occT * h->num_sms);
+  int occL = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occL, k_loop, kThreads, 0));
+  if (occL < 1) occL = 1;
+  h->gridL = h->gridA > h->gridT ? h->gridA : h->gridT;
+  h->loop_fits = h->gridL <= occL * h->num_sms;
+  if (h->gridL > occL * h->num_sms) h->gridL = occL * h->num_sms;  // all blocks co-resident
   h->gridV = grid_for(n > m ? n : m, kThreads, 4 * h->num_sms);
   h->max_grid = h->gridA > h->gridT ? h->gridA : h->gridT;
   if (h->gridV > h->max_grid) h->max_grid = h->gridV;
+  if (h->gridL > h->max_grid) h->max_grid = h->gridL;
 
   // ---- device buffers ----
   CK(h->alloc(&h->rpA, m + 1)); CK(h->alloc(&h->ciA, nnz)); CK(h->alloc(&h->valA, nnz));
@@ -399,8 +460,13 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
     CK(h->alloc(p, n));
   for (double** p : {&h->lc, &h->uc, &h->inv_dr, &h->dr, &h->y, &h->y0, &h->yh, &h->ax, &h->ax0, &h->axh})
     CK(h->alloc(p, m));
-  CK(h->alloc(&h->out_buf, (size_t)(n > m ? n : m) + 1));
+  {
+    size_t ob = (size_t)(n > m ? n : m) + 1;
+    if (ob < (size_t)kPwBatch) ob = kPwBatch;  // also holds a batch of power-iteration lambdas
+    CK(h->alloc(&h->out_buf, ob));
+  }
   CK(h->alloc(&h->partials, (size_t)h->max_grid * kNumSums));
+  CK(h->alloc(&h->partials2, (size_t)h->max_grid * kNumSums));
   CK(h->alloc(&h->ctl, 1));
   CK(h->alloc(&h->pw, 1));
   CK(cudaMemset(h->ctl, 0, sizeof(Ctl)));
@@ -509,6 +575,7 @@ lp_status lp_default_params(lp_params* p) {
   p->trace_cap = 0;
   p->unroll = 8;
   p->lane_target = 8;
+  p->persistent = -1;
   return LP_OK;
 }
 
@@ -591,7 +658,7 @@ lp_status lp_set_params(lp_handle h, const lp_params* p) {
     if (h->trace_cap > 0) CK(h->alloc(&h->trace, (size_t)h->trace_cap * 4));
     return build_graph(h);
   }
-  if (h->prm.unroll != h->graph_unroll) return build_graph(h);
+  if (h->prm.unroll != h->graph_unroll || p->persistent != old.persistent) return build_graph(h);
   return LP_OK;
 }
 
@@ -683,9 +750,10 @@ lp_status lp_get(lp_handle h, double* x, double* y, int32_t* solve_status, doubl
   return LP_OK;
 }
 
-lp_status lp_get_info(lp_handle h, double* out7) {
+lp_status lp_get_info(lp_handle h, double* out8) {
   g_err.clear();
-  if (!h || !out7) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  if (!h || !out8) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  double* out7 = out8;
   if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "lp_get_info before lp_solve");
   CK(cudaSetDevice(h->device));
   CK(cudaStreamSynchronize(h->last_stream));
@@ -698,6 +766,7 @@ lp_status lp_get_info(lp_handle h, double* out7) {
   out7[4] = (double)h->pw_iters;
   out7[5] = ctl.kkt[4];
   out7[6] = ctl.kkt[5];
+  out8[7] = h->loop_active ? 1.0 : 0.0;
   return LP_OK;
 }
 
@@ -731,34 +800,48 @@ lp_status lp_time_kernels(lp_handle h, int64_t iters, void* stream, double* ms_o
   if (!h || !ms_out || iters < 1) return fail(LP_ERR_INVALID_ARG, "bad argument");
   CK(cudaSetDevice(h->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  lp_status st = enqueue_start(h, 0.0, iters, s);
+  const bool loop = h->loop_active;
+  const int32_t per = loop ? h->prm.unroll : 1;
+  const int64_t launches = (iters + per - 1) / per;
+  lp_status st = enqueue_start(h, 0.0, launches * per, s);
   if (st != LP_OK) return st;
   RowArgs ra{};
   ColArgs ca{};
   fill_args(h, ra, ca);
-  std::vector<cudaEvent_t> ev(2 * iters + 1);
+  const int64_t nev = loop ? launches + 1 : 2 * launches + 1;
+  std::vector<cudaEvent_t> ev(nev);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   CK(cudaEventRecord(ev[0], s));
-  for (int64_t t = 0; t < iters; ++t) {
-    k1_rows<<<h->gridA, kThreads, 0, s>>>(ra);
-    CK(cudaEventRecord(ev[2 * t + 1], s));
-    k2_cols<<<h->gridT, kThreads, 0, s>>>(ca);
-    CK(cudaEventRecord(ev[2 * t + 2], s));
+  for (int64_t q = 0; q < launches; ++q) {
+    if (loop) {
+      CK(launch_loop(h, ra, ca, per, cudaGraphConditionalHandle{}, 0, s));
+      CK(cudaEventRecord(ev[q + 1], s));
+    } else {
+      k1_rows<<<h->gridA, kThreads, 0, s>>>(ra);
+      CK(cudaEventRecord(ev[2 * q + 1], s));
+      k2_cols<<<h->gridT, kThreads, 0, s>>>(ca);
+      CK(cudaEventRecord(ev[2 * q + 2], s));
+    }
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   double a = 0.0, b = 0.0;
-  for (int64_t t = 0; t < iters; ++t) {
+  for (int64_t q = 0; q < launches; ++q) {
     float m1 = 0.f, m2 = 0.f;
-    CK(cudaEventElapsedTime(&m1, ev[2 * t], ev[2 * t + 1]));
-    CK(cudaEventElapsedTime(&m2, ev[2 * t + 1], ev[2 * t + 2]));
+    if (loop) {
+      CK(cudaEventElapsedTime(&m1, ev[q], ev[q + 1]));
+    } else {
+      CK(cudaEventElapsedTime(&m1, ev[2 * q], ev[2 * q + 1]));
+      CK(cudaEventElapsedTime(&m2, ev[2 * q + 1], ev[2 * q + 2]));
+    }
     a += m1;
     b += m2;
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  ms_out[0] = a / (double)iters;
-  ms_out[1] = b / (double)iters;
-  ms_out[2] = (double)iters;
+  ms_out[0] = a / (double)launches;
+  ms_out[1] = b / (double)launches;
+  ms_out[2] = (double)per;
+  ms_out[3] = (double)launches;
   h->solved = true;
   h->last_stream = s;
   return LP_OK;

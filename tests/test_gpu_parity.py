@@ -175,7 +175,9 @@ def test_small_lp_iterates(cuda_device, seed, iters):
 @pytest.mark.parametrize("variant", [dict(gamma=0.0), dict(gamma=0.5), dict(restart_enabled=0),
                                      dict(pid_enabled=0), dict(ruiz_iters=0, pc_enabled=0),
                                      dict(k_p=0.3, k_i=0.05, k_d=0.2), dict(check_every=1),
-                                     dict(check_every=7, unroll=3), dict(lane_target=1), dict(lane_target=16)])
+                                     dict(check_every=7, unroll=3), dict(lane_target=1), dict(lane_target=16),
+                                     dict(persistent=0), dict(persistent=0, check_every=5, unroll=2),
+                                     dict(persistent=1, unroll=5)])
 def test_variants_iterates(cuda_device, variant):
     compare_fixed(gen.free_and_boxed_mix(3, 300, 450), 400, **variant)
 
@@ -239,13 +241,27 @@ def test_single_iteration_and_degenerate_shapes(cuda_device):
     compare_fixed(gen.ragged_rows(9, 64, 5000), 150)
 
 
-def test_deterministic_and_reusable(cuda_device):
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_deterministic_and_reusable(cuda_device, persistent):
     lp = gen.miplib_like(4, 3000, 6000, 2000)
-    with lpx.Solver(lp) as s:
+    with lpx.Solver(lp, persistent=persistent) as s:
         a = s.solve(0.0, 500).result()
         b = s.solve(0.0, 500).result()
+    assert a["persistent"] == bool(persistent)
     assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["y"], b["y"])
     assert a["iters"] == b["iters"] == 500
+
+
+def test_both_drivers_agree(cuda_device):
+    """The cooperative loop kernel and the one-kernel-per-phase driver run the same device
+    functions; only the grid size (hence the order of the block sums) differs."""
+    lp = gen.miplib_like(5, 3000, 6000, 2000)
+    eta = oracle_eta(lp)
+    a = gpu_solve(lp, 0.0, 300, eta=eta, persistent=1)
+    b = gpu_solve(lp, 0.0, 300, eta=eta, persistent=0)
+    assert a["persistent"] and not b["persistent"]
+    assert_iterates_close(a["x"], b["x"])
+    assert_iterates_close(a["y"], b["y"])
 
 
 def test_device_inputs_equal_host_inputs(cuda_device):
