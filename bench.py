@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--workload", default="miplib", choices=["miplib", "mcf", "small"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--max-iter", type=int, default=100000)
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+                    help="0 FP64; 1 FP32 phase then FP64 refinement; 2 FP32 only")
+    ap.add_argument("--switch-tol", type=float, default=1e-5)
     ap.add_argument("--kernel-iters", type=int, default=300)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
@@ -245,7 +248,7 @@ def run_ours(args):
     sp = stream.cuda_stream
 
     t0 = time.perf_counter()
-    solver = lpx.Solver(lp)
+    solver = lpx.Solver(lp, precision=args.precision, switch_tol=args.switch_tol)
     setup_ms = 1e3 * (time.perf_counter() - t0)
     prm = solver.params
     unroll = int(prm.unroll)
@@ -277,8 +280,14 @@ def run_ours(args):
         statuses.append(st)
         kkts.append(kkt.tolist())
         total_iters += it
-        bodies = math.ceil(it / unroll)
-        launches += 3 + (bodies if persistent else bodies * (2 * unroll + 1))
+        it32 = int(lpx.lp_get_info(solver.h)[8])
+        for phase_iters in ((it - it32, it32) if args.precision == 1 else (it,)):
+            bodies = max(1, math.ceil(phase_iters / unroll))
+            launches += 3 + (bodies if persistent else bodies * (2 * unroll + 1))
+        if args.precision == 1:
+            launches += 5  # hand-over: control, vectors, two SpMVs, first primal step
+        elif args.precision == 2:
+            launches += 1  # FP32 point to the FP64 output buffers
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -334,7 +343,7 @@ def run_ours(args):
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = lpx.lp_create(lp.m, lp.n, lp.nnz, *pinned, where=lpx.LP_HOST)
+        h = lpx.lp_create(lp.m, lp.n, lp.nnz, *pinned, where=lpx.LP_HOST, params=solver.params)
         lpx.lp_solve(h, args.tol, args.max_iter, sp)
         st, kkt, it = lpx.lp_get(h, xo, yo)
         e2e_s += time.perf_counter() - t0
@@ -364,7 +373,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_s * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f64", 1: "f32+f64", 2: "f32"}[args.precision], "data": "synthetic",
             "config": {"workload": wl, "instances": f"one per GPU, seed = rank", "tol": args.tol,
                        "max_iter": args.max_iter, "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"independent instances x{world}",
@@ -372,6 +382,7 @@ def run_ours(args):
             "status_per_step": statuses, "rel_kkt_last": kkts[-1], "iters_per_step": total_iters / args.steps,
             "time_to_tol_s": (setup_ms / 1e3 + elapsed_s / args.steps) if solved else None,
             "setup_ms": setup_ms, "eta": float(info[0]), "restarts_last": int(info[2]),
+            "iters_fp32_last": int(info[8]),
             "driver": "cooperative loop kernel" if persistent else "one kernel per phase",
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": h2d,

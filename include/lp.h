@@ -51,6 +51,7 @@ enum {
   LP_SOLVE_ITER_LIMIT = 2, /* max_iter iterations done without meeting tol */
   LP_SOLVE_NUMERICAL = 3,  /* the fixed-point residual became NaN or infinite */
   LP_SOLVE_INFEASIBLE = 4, /* reserved: the paper gives no infeasibility test; never returned */
+  LP_SOLVE_STALLED = 5,    /* precision 2 only: the FP32 solve stopped improving (fp32_patience) */
   LP_SOLVE_INTERNAL_ERROR = 6 /* the device loop outran max_iter (a library fault); not expected */
 };
 
@@ -88,12 +89,25 @@ typedef struct {
                               grid-wide barriers between phases; 0: one kernel per phase;
                               -1: the first when every block of both phases fits on the GPU at
                               once (latency-bound sizes), else the second */
+  int32_t precision;       /* 0: FP64 throughout.  1: mixed -- matrix and iterates in FP32 with
+                              FP32 SpMV accumulation (reductions, restart test, PID and KKT test in
+                              FP64) until the relative KKT error is <= max(tol, switch_tol) or
+                              max_iter iterations, then an FP64 refinement phase anchored at the
+                              FP32 point, up to max_iter further iterations.  2: FP32 phase only.
+                              Fixed at lp_create. */
+  double switch_tol;       /* precision 1: KKT level at which the FP32 phase hands over */
+  int32_t fp32_patience;   /* FP32 phase: at a check iteration whose relative KKT error is no new
+                              best for the fp32_patience-th time in a row, or is above 100 times
+                              the best, the phase stops (precision 1: hands over to FP64 with
+                              omega and the PID state of the best check; precision 2: ends with
+                              LP_SOLVE_STALLED).  0 disables the guard. */
 } lp_params;
 
 /* Fills p with the defaults: gamma 1, betas 0.2 / 0.8 / 0.36, K_P 0.5, K_I 0.001, K_D 0,
  * eta 0 (power iteration), omega0 1, check_every 64, restarts and PID on, power_tol 1e-7,
  * power_max_iter 10000, seed 0, Ruiz 10 + Pock-Chambolle alpha 1, no trace, unroll 8,
- * lane_target 8, persistent -1.  Returns LP_ERR_INVALID_ARG if p is NULL. */
+ * lane_target 8, persistent -1, precision 0, switch_tol 1e-5, fp32_patience 32.  Returns
+ * LP_ERR_INVALID_ARG if p is NULL. */
 LP_API lp_status lp_default_params(lp_params* p);
 
 typedef struct lp_solver* lp_handle;
@@ -157,9 +171,10 @@ LP_API lp_status lp_get(lp_handle h, double* x, double* y, int32_t* solve_status
 /* Extra scalars of the last solve (host doubles): out[0] eta, out[1] final omega,
  * out[2] restarts, out[3] ||A~||_2 from the power iteration (0 if eta was given),
  * out[4] power-iteration steps, out[5] primal objective c^T x, out[6] dual objective,
- * out[7] 1 if the cooperative loop kernel runs the solve, 0 if one kernel per phase does.
+ * out[7] 1 if the cooperative loop kernel runs the solve, 0 if one kernel per phase does,
+ * out[8] iterations done in FP32 (precision 1 or 2; 0 for FP64).
  * Waits like lp_get.  Errors: LP_ERR_INVALID_ARG, LP_ERR_NOT_SOLVED, LP_ERR_CUDA. */
-LP_API lp_status lp_get_info(lp_handle h, double* out8);
+LP_API lp_status lp_get_info(lp_handle h, double* out9);
 
 /* Copies up to cap rows of the per-iteration trace (r_t, omega_t, restart_t, k_t) into the
  * host array trace[4*cap]; *rows receives the number written.  Needs trace_cap > 0. */

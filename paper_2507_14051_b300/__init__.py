@@ -30,7 +30,7 @@ LP_ERR_OUT_OF_MEMORY = -4
 LP_ERR_NOT_SOLVED = -5
 LP_ERR_TOO_LARGE = -6
 LP_SOLVE_OPTIMAL, LP_SOLVE_ITER_LIMIT, LP_SOLVE_NUMERICAL, LP_SOLVE_INFEASIBLE = 1, 2, 3, 4
-LP_SOLVE_INTERNAL_ERROR = 6
+LP_SOLVE_STALLED, LP_SOLVE_INTERNAL_ERROR = 5, 6
 LP_HOST, LP_DEVICE = 0, 1
 
 EXPORTED = ("lp_default_params", "lp_create", "lp_set_params", "lp_solve", "lp_get",
@@ -63,6 +63,9 @@ class lp_params(C.Structure):
         ("unroll", C.c_int32),
         ("lane_target", C.c_int32),
         ("persistent", C.c_int32),
+        ("precision", C.c_int32),
+        ("switch_tol", C.c_double),
+        ("fp32_patience", C.c_int32),
     ]
 
 
@@ -179,7 +182,7 @@ def lp_get(h, x=None, y=None):
 
 
 def lp_get_info(h) -> np.ndarray:
-    out = np.zeros(8)
+    out = np.zeros(9)
     _check(load().lp_get_info(h, out.ctypes.data_as(C.POINTER(C.c_double))), "lp_get_info")
     return out
 
@@ -265,7 +268,7 @@ class Solver:
         info = lp_get_info(self.h)
         return dict(x=x, y=y, status=st, kkt=kkt, iters=it, eta=info[0], omega=info[1],
                     restarts=int(info[2]), norm_A=info[3], power_iters=int(info[4]),
-                    pobj=info[5], dobj=info[6], persistent=bool(info[7]))
+                    pobj=info[5], dobj=info[6], persistent=bool(info[7]), iters_fp32=int(info[8]))
 
     def trace(self):
         return lp_get_trace(self.h, int(self.params.trace_cap))

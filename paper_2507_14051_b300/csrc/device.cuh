@@ -47,7 +47,7 @@ struct BinTable {
   Bin bin[kMaxBins];
 };
 
-enum : int32_t { kOptimal = 1, kIterLimit = 2, kNumerical = 3, kInternalError = 6 };
+enum : int32_t { kOptimal = 1, kIterLimit = 2, kNumerical = 3, kStalled = 5, kInternalError = 6 };
 
 // Scalar state of one solve; lives in device memory and is only touched by the last block of
 // each iteration kernel (and read by all threads at kernel entry).
@@ -68,6 +68,14 @@ struct Ctl {
   double sxx, sx0;       // |x - xhat|^2 and |xhat - x0|^2 for the coming iteration (from K2)
   double pres2, dobj_y;  // check-iteration sums from K1, finished by K2
   double omega_used;     // omega of the last iteration performed
+  int64_t iters32;       // mixed precision: iterations of the FP32 phase
+  // FP32 phase stall guard: best relative KKT error seen at a check iteration, checks since,
+  // and omega / PID state at that check (restored for the FP64 phase after a stall)
+  // and omega / PID state at that check (restored for the FP64 phase after a stall); the
+  // check iterations store zhat in slot cand_slot of a two-slot buffer, best_slot holds the best
+  int32_t patience, since_best, cand_slot, best_slot;
+  double best_kkt, omega_best, integral_best, eprev_best;
+  double kkt_best[8];
   int64_t restarts_used; // restarts before the last iteration's decision
   double kkt[8];         // rel_gap, rel_pres, rel_dres, rel_kkt, pobj, dobj, pres, dres
   double lu_norm, c_norm;
@@ -78,8 +86,12 @@ struct Ctl {
 __device__ __forceinline__ double clampd(double v, double lo, double hi) {
   return fmin(fmax(v, lo), hi);
 }
+__device__ __forceinline__ float clampd(float v, float lo, float hi) {
+  return fminf(fmaxf(v, lo), hi);
+}
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class V>
+__device__ __forceinline__ V warp_sum(V v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
   return v;
@@ -113,23 +125,32 @@ __device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol) {
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
+__device__ __forceinline__ float ld_stream(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
 // Gathered vector entries: L2 evict-last.
 __device__ __forceinline__ double ld_gather(const double* p, uint64_t pol) {
   double v;
   asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
   return v;
 }
+__device__ __forceinline__ float ld_gather(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
 
 // Partial dot product of one lane: entries b+first, b+first+stride, ... < e, loaded ILP at a
 // time (all loads of a batch issued before any is used) and accumulated in entry order.
-template <int ILP>
-__device__ __forceinline__ double strided_dot_n(const int32_t* __restrict__ ci,
-                                                const double* __restrict__ val,
-                                                const double* __restrict__ xg, int first, int e,
-                                                int stride, const LoadPolicy& pol) {
-  double acc = 0.0;
+template <int ILP, class V>
+__device__ __forceinline__ V strided_dot_n(const int32_t* __restrict__ ci, const V* __restrict__ val,
+                                           const V* __restrict__ xg, int first, int e, int stride,
+                                           const LoadPolicy& pol) {
+  V acc = V(0);
   for (int k0 = first; k0 < e; k0 += ILP * stride) {
-    double v[ILP];
+    V v[ILP];
     int c[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
@@ -138,13 +159,13 @@ __device__ __forceinline__ double strided_dot_n(const int32_t* __restrict__ ci,
         v[u] = ld_stream(val + k, pol.stream);
         c[u] = ld_stream(ci + k, pol.stream);
       } else {
-        v[u] = 0.0;
+        v[u] = V(0);
         c[u] = -1;
       }
     }
-    double xv[ILP];
+    V xv[ILP];
 #pragma unroll
-    for (int u = 0; u < ILP; ++u) xv[u] = c[u] >= 0 ? ld_gather(xg + c[u], pol.keep) : 0.0;
+    for (int u = 0; u < ILP; ++u) xv[u] = c[u] >= 0 ? ld_gather(xg + c[u], pol.keep) : V(0);
 #pragma unroll
     for (int u = 0; u < ILP; ++u)
       if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
@@ -155,10 +176,10 @@ __device__ __forceinline__ double strided_dot_n(const int32_t* __restrict__ ci,
 // The same with the batch sized to `per_lane`, the most entries any lane of the warp has
 // (uniform across the warp): short rows then issue no FP64 fma for absent entries, which on
 // this GPU's FP64 unit would cost as much as real ones.
-__device__ __forceinline__ double strided_dot(const int32_t* __restrict__ ci,
-                                              const double* __restrict__ val,
-                                              const double* __restrict__ xg, int first, int e,
-                                              int stride, int per_lane, const LoadPolicy& pol) {
+template <class V>
+__device__ __forceinline__ V strided_dot(const int32_t* __restrict__ ci, const V* __restrict__ val,
+                                         const V* __restrict__ xg, int first, int e, int stride,
+                                         int per_lane, const LoadPolicy& pol) {
   if (per_lane <= 1) return strided_dot_n<1>(ci, val, xg, first, e, stride, pol);
   if (per_lane <= 2) return strided_dot_n<2>(ci, val, xg, first, e, stride, pol);
   if (per_lane <= 4) return strided_dot_n<4>(ci, val, xg, first, e, stride, pol);
@@ -169,11 +190,10 @@ __device__ __forceinline__ double strided_dot(const int32_t* __restrict__ ci,
 // G lanes per row, 32/G rows per pass; lane L returns the value of row L (garbage for
 // L >= nrows).  Summation: each lane accumulates its strided entries in order, then a
 // fixed xor butterfly over the G lanes (deterministic).
-__device__ __forceinline__ double tile_spmv(const int32_t* __restrict__ rp,
-                                            const int32_t* __restrict__ ci,
-                                            const double* __restrict__ val,
-                                            const double* __restrict__ xg, int row0, int nrows,
-                                            int G, int per_lane, int lane, const LoadPolicy& pol) {
+template <class V>
+__device__ __forceinline__ V tile_spmv(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                       const V* __restrict__ val, const V* __restrict__ xg, int row0,
+                                       int nrows, int G, int per_lane, int lane, const LoadPolicy& pol) {
   const int rpp = 32 / G;  // rows per pass
   const int passes = (nrows + rpp - 1) / rpp;
   const int g = lane / G, sub = lane - g * G;
@@ -183,14 +203,14 @@ __device__ __forceinline__ double tile_spmv(const int32_t* __restrict__ rp,
     my_b = rp[row0 + lane];
     my_e = rp[row0 + lane + 1];
   }
-  double mine = 0.0;
+  V mine = V(0);
   for (int p = 0; p < passes; ++p) {
     const int q = p * rpp + g;  // row of this lane's group in this pass
     const int b = __shfl_sync(kFull, my_b, q & 31);
     const int e = __shfl_sync(kFull, my_e, q & 31);
-    double acc = q < nrows ? strided_dot(ci, val, xg, b + sub, e, G, per_lane, pol) : 0.0;
+    V acc = q < nrows ? strided_dot(ci, val, xg, b + sub, e, G, per_lane, pol) : V(0);
     for (int off = G >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-    const double v = __shfl_sync(kFull, acc, (lane % rpp) * G);
+    const V v = __shfl_sync(kFull, acc, (lane % rpp) * G);
     if (lane / rpp == p) mine = v;
   }
   return mine;
@@ -202,11 +222,10 @@ __device__ __forceinline__ double tile_spmv(const int32_t* __restrict__ rp,
 // (acc = a zeroed array then stored in bins.contrib for the last block to add in row order).
 // Every sum therefore has a fixed order that depends only on the grid size: results are
 // bit-reproducible run to run.
-template <class Epi>
+template <class V, class Epi>
 __device__ __forceinline__ void for_each_row(const BinTable& bins, const int32_t* __restrict__ rp,
-                                             const int32_t* __restrict__ ci,
-                                             const double* __restrict__ val,
-                                             const double* __restrict__ xg, const LoadPolicy& pol,
+                                             const int32_t* __restrict__ ci, const V* __restrict__ val,
+                                             const V* __restrict__ xg, const LoadPolicy& pol,
                                              double (&s)[kNumSums], Epi&& epi) {
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * kWarps;
@@ -216,9 +235,9 @@ __device__ __forceinline__ void for_each_row(const BinTable& bins, const int32_t
       const int4 ch = bins.chunk[task];
       const int b = rp[ch.x] + (task - ch.y) * kChunkNnz;
       const int e = min(rp[ch.x + 1], b + kChunkNnz);
-      const double v = warp_sum(strided_dot(ci, val, xg, b + lane, e, 32, kChunkNnz / 32, pol));
+      const V v = warp_sum(strided_dot(ci, val, xg, b + lane, e, 32, kChunkNnz / 32, pol));
       if (lane == 0) {
-        bins.part[task] = v;
+        bins.part[task] = (double)v;
         __threadfence();
         if (atomicAdd(bins.arrivals + ch.x, 1u) == (unsigned)ch.z - 1u) {
           __threadfence();
@@ -226,7 +245,7 @@ __device__ __forceinline__ void for_each_row(const BinTable& bins, const int32_t
           for (int q = 0; q < ch.z; ++q) tot += __ldcg(bins.part + ch.y + q);
           bins.arrivals[ch.x] = 0u;
           double c[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-          epi(ch.x, tot, c);
+          epi(ch.x, (V)tot, c);
 #pragma unroll
           for (int q = 0; q < kNumSums; ++q) bins.contrib[ch.x * kNumSums + q] = c[q];
         }
@@ -237,7 +256,7 @@ __device__ __forceinline__ void for_each_row(const BinTable& bins, const int32_t
     const int row0 = B.row0 + (task - bins.nchunks - B.task0) * B.rows_per_tile;
     const int nrows = min(B.rows_per_tile, B.row1 - row0);
     const int lc = B.per_lane;
-    const double v = tile_spmv(rp, ci, val, xg, row0, nrows, B.lanes, lc, lane, pol);
+    const V v = tile_spmv(rp, ci, val, xg, row0, nrows, B.lanes, lc, lane, pol);
     if (lane < nrows) epi(row0 + lane, v, s);
   }
 }

@@ -71,11 +71,24 @@ __device__ __forceinline__ double pid_update(Ctl& c, double omega, double dxn, d
   return exp(lw);
 }
 
+// FP64 accumulation of a product / value computed in the phase's value type: for FP64 the
+// product is fused into the accumulator, for FP32 the product is rounded to FP32 and added in
+// FP64 (the reductions stay FP64 in both precisions).
+__device__ __forceinline__ void acc_fma(double& a, double p, double q) { a = fma(p, q, a); }
+__device__ __forceinline__ void acc_fma(double& a, float p, float q) { a += (double)(p * q); }
+__device__ __forceinline__ double fmav(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmav(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double maxv(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float maxv(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double minv(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float minv(float a, float b) { return fminf(a, b); }
+
 // ------------------------------------------------------------------ row phase
 
 struct RowStep {
   int mode;  // 0 Halpern combine, 1 restart, 2 first iteration (state is zero)
   int check;
+  int cand;  // stall-guard slot written at this check iteration
   double ha, hb, he, sigma, inv_sigma;
 };
 
@@ -83,6 +96,7 @@ __device__ __forceinline__ RowStep row_step(const Ctl& c) {
   RowStep st;
   st.mode = (c.t == 0) ? 2 : c.restart;
   st.check = is_check(c, c.t) ? 1 : 0;
+  st.cand = c.cand_slot;
   st.ha = c.ha;
   st.hb = c.hb;
   st.he = c.he;
@@ -91,13 +105,16 @@ __device__ __forceinline__ RowStep row_step(const Ctl& c) {
   return st;
 }
 
-__device__ __forceinline__ void row_epilogue(const RowArgs& a, const RowStep& st, int i, double v,
+template <class V>
+__device__ __forceinline__ void row_epilogue(const RowArgsT<V>& a, const RowStep& st, int i, V v,
                                              double (&acc)[kNumSums]) {
-  double yi, axi, y0i;
+  const V ha = (V)st.ha, hb = (V)st.hb, he = (V)st.he;
+  const V sigma = (V)st.sigma, inv_sigma = (V)st.inv_sigma;
+  V yi, axi, y0i;
   if (st.mode == 0) {
     y0i = a.y0[i];
-    yi = fma(st.ha, a.yh[i], fma(st.hb, a.y[i], st.he * y0i));
-    axi = fma(st.ha, a.axh[i], fma(st.hb, a.ax[i], st.he * a.ax0[i]));
+    yi = fmav(ha, a.yh[i], fmav(hb, a.y[i], he * y0i));
+    axi = fmav(ha, a.axh[i], fmav(hb, a.ax[i], he * a.ax0[i]));
   } else if (st.mode == 1) {
     yi = a.yh[i];
     axi = a.axh[i];
@@ -105,23 +122,24 @@ __device__ __forceinline__ void row_epilogue(const RowArgs& a, const RowStep& st
     a.y0[i] = yi;
     a.ax0[i] = axi;
   } else {
-    yi = 0.0;
-    axi = 0.0;
-    y0i = 0.0;
+    yi = V(0);
+    axi = V(0);
+    y0i = V(0);
   }
-  const double lo = a.lc[i], hi = a.uc[i];
-  const double w = fma(2.0, v, -axi);  // A(2 xhat - x)
-  const double sv = fma(-yi, st.inv_sigma, w);
-  const double yn = st.sigma * (clampd(sv, lo, hi) - sv);
-  const double dy = yi - yn;
-  acc[0] = fma(dy, dy, acc[0]);
-  acc[1] = fma(dy, axi - v, acc[1]);
-  const double d0 = yn - y0i;
-  acc[2] = fma(d0, d0, acc[2]);
+  const V lo = a.lc[i], hi = a.uc[i];
+  const V w = fmav(V(2), v, -axi);  // A(2 xhat - x)
+  const V sv = fmav(-yi, inv_sigma, w);
+  const V yn = sigma * (clampd(sv, lo, hi) - sv);
+  const V dy = yi - yn;
+  acc_fma(acc[0], dy, dy);
+  acc_fma(acc[1], dy, axi - v);
+  const V d0 = yn - y0i;
+  acc_fma(acc[2], d0, d0);
   if (st.check) {
-    const double pr = (v - clampd(v, lo, hi)) * a.inv_dr[i];
-    acc[3] = fma(pr, pr, acc[3]);
-    acc[4] += (yn > 0.0 ? lo * yn : 0.0) + (yn < 0.0 ? hi * yn : 0.0);
+    const V pr = (v - clampd(v, lo, hi)) * a.inv_dr[i];
+    acc_fma(acc[3], pr, pr);
+    acc[4] += (double)((yn > V(0) ? lo * yn : V(0)) + (yn < V(0) ? hi * yn : V(0)));
+    if (a.yb0) (st.cand ? a.yb1 : a.yb0)[i] = yn;
   }
   if (st.mode != 2) {
     a.y[i] = yi;
@@ -187,18 +205,22 @@ __device__ __forceinline__ void row_control(Ctl& c, const double (&tot)[kNumSums
 
 // --------------------------------------------------------------- column phase
 
-struct ColStep {
+template <class V>
+struct ColStepT {
   int restart;
   int check;
+  int cand;
   double ha, hb, he, tau;
-  const double* xc;  // xhat_t
-  double* xn;        // xhat_{t+1}
+  const V* xc;  // xhat_t
+  V* xn;        // xhat_{t+1}
 };
 
-__device__ __forceinline__ ColStep col_step(const Ctl& c, const ColArgs& a) {
-  ColStep st;
+template <class V>
+__device__ __forceinline__ ColStepT<V> col_step(const Ctl& c, const ColArgsT<V>& a) {
+  ColStepT<V> st;
   st.restart = c.restart;
   st.check = is_check(c, c.t) ? 1 : 0;
+  st.cand = c.cand_slot;
   st.ha = c.ha;
   st.hb = c.hb;
   st.he = c.he;
@@ -208,10 +230,12 @@ __device__ __forceinline__ ColStep col_step(const Ctl& c, const ColArgs& a) {
   return st;
 }
 
-__device__ __forceinline__ void col_epilogue(const ColArgs& a, const ColStep& st, int j, double u,
+template <class V>
+__device__ __forceinline__ void col_epilogue(const ColArgsT<V>& a, const ColStepT<V>& st, int j, V u,
                                              double (&acc)[kNumSums]) {
-  const double xc = st.xc[j];
-  double xj, atyj, x0j;
+  const V ha = (V)st.ha, hb = (V)st.hb, he = (V)st.he, tau = (V)st.tau;
+  const V xc = st.xc[j];
+  V xj, atyj, x0j;
   if (st.restart) {
     xj = xc;
     atyj = u;
@@ -220,23 +244,24 @@ __device__ __forceinline__ void col_epilogue(const ColArgs& a, const ColStep& st
     a.aty0[j] = u;
   } else {
     x0j = a.x0[j];
-    xj = fma(st.ha, xc, fma(st.hb, a.x[j], st.he * x0j));
-    atyj = fma(st.ha, u, fma(st.hb, a.aty[j], st.he * a.aty0[j]));
+    xj = fmav(ha, xc, fmav(hb, a.x[j], he * x0j));
+    atyj = fmav(ha, u, fmav(hb, a.aty[j], he * a.aty0[j]));
   }
-  const double cj = a.c[j], lo = a.lv[j], hi = a.uv[j];
-  const double xn = clampd(fma(-st.tau, cj - atyj, xj), lo, hi);
-  const double dx = xj - xn;
-  acc[0] = fma(dx, dx, acc[0]);
-  const double d0 = xn - x0j;
-  acc[1] = fma(d0, d0, acc[1]);
+  const V cj = a.c[j], lo = a.lv[j], hi = a.uv[j];
+  const V xn = clampd(fmav(-tau, cj - atyj, xj), lo, hi);
+  const V dx = xj - xn;
+  acc_fma(acc[0], dx, dx);
+  const V d0 = xn - x0j;
+  acc_fma(acc[1], d0, d0);
   if (st.check) {
-    acc[2] = fma(cj, xc, acc[2]);
-    const double rc = cj - u;
+    acc_fma(acc[2], cj, xc);
+    const V rc = cj - u;
     const bool fl = isfinite(lo), fu = isfinite(hi);
-    const double rr = (fl && fu) ? rc : (fl ? fmax(rc, 0.0) : (fu ? fmin(rc, 0.0) : 0.0));
-    const double dd = (rc - rr) * a.inv_dc[j];
-    acc[3] = fma(dd, dd, acc[3]);
-    acc[4] += (rr > 0.0 ? lo * rr : 0.0) + (rr < 0.0 ? hi * rr : 0.0);
+    const V rr = (fl && fu) ? rc : (fl ? maxv(rc, V(0)) : (fu ? minv(rc, V(0)) : V(0)));
+    const V dd = (rc - rr) * a.inv_dc[j];
+    acc_fma(acc[3], dd, dd);
+    acc[4] += (double)((rr > V(0) ? lo * rr : V(0)) + (rr < V(0) ? hi * rr : V(0)));
+    if (a.xb0) (st.cand ? a.xb1 : a.xb0)[j] = xc;
   }
   a.x[j] = xj;
   a.aty[j] = atyj;
@@ -272,6 +297,23 @@ __device__ __forceinline__ void col_control(Ctl& c, const double (&tot)[kNumSums
       c.done = 1;
       return;
     }
+    if (c.patience > 0) {  // FP32 phase: stop once its rounding floor stalls or reverses progress
+      if (mx < c.best_kkt) {
+        c.best_kkt = mx;
+        c.since_best = 0;
+        c.omega_best = c.omega;
+        c.integral_best = c.pid_integral;
+        c.eprev_best = c.pid_eprev;
+        for (int q = 0; q < 8; ++q) c.kkt_best[q] = c.kkt[q];
+        c.best_slot = c.cand_slot;  // zhat_t of this check is in that slot; write the other next
+        c.cand_slot ^= 1;
+      } else if (++c.since_best >= c.patience || !(mx <= 100.0 * c.best_kkt)) {
+        c.status = kStalled;
+        c.iters = t + 1;
+        c.done = 1;
+        return;
+      }
+    }
   }
   if (t + 1 >= c.max_iter) {
     c.status = kIterLimit;
@@ -284,15 +326,16 @@ __device__ __forceinline__ void col_control(Ctl& c, const double (&tot)[kNumSums
 
 // ----------------------------------------------------------- one kernel per phase
 
-__global__ void __launch_bounds__(kThreads, 3) k1_rows(RowArgs a) {
+template <class V>
+__global__ void __launch_bounds__(kThreads, 3) k1_rows(RowArgsT<V> a) {
   Ctl* ctl = a.ctl;
   if (ctl->done) return;
   const RowStep st = row_step(*ctl);
-  const double* __restrict__ xh = (ctl->t & 1) ? a.xh1 : a.xh0;
+  const V* __restrict__ xh = (ctl->t & 1) ? a.xh1 : a.xh0;
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const LoadPolicy pol = make_policy();
   for_each_row(a.bins, a.rp, a.ci, a.val, xh, pol, s,
-               [&](int i, double v, double (&acc)[kNumSums]) { row_epilogue(a, st, i, v, acc); });
+               [&](int i, V v, double (&acc)[kNumSums]) { row_epilogue(a, st, i, v, acc); });
   const int nsums = st.check ? 5 : 3;
   if (!block_sums_last(s, nsums, a.partials, &ctl->count1)) return;
   double tot[kNumSums];
@@ -302,14 +345,15 @@ __global__ void __launch_bounds__(kThreads, 3) k1_rows(RowArgs a) {
   row_control(*ctl, tot, st.check, a.trace);
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k2_cols(ColArgs a) {
+template <class V>
+__global__ void __launch_bounds__(kThreads, 3) k2_cols(ColArgsT<V> a) {
   Ctl* ctl = a.ctl;
   if (ctl->done) return;
-  const ColStep st = col_step(*ctl, a);
+  const ColStepT<V> st = col_step(*ctl, a);
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const LoadPolicy pol = make_policy();
   for_each_row(a.bins, a.rp, a.ci, a.val, a.yh, pol, s,
-               [&](int j, double u, double (&acc)[kNumSums]) { col_epilogue(a, st, j, u, acc); });
+               [&](int j, V u, double (&acc)[kNumSums]) { col_epilogue(a, st, j, u, acc); });
   const int nsums = st.check ? 5 : 2;
   if (!block_sums_last(s, nsums, a.partials, &ctl->count2)) return;
   double tot[kNumSums];
@@ -336,14 +380,15 @@ __device__ __forceinline__ void store_block_partials(double (&s)[kNumSums], int 
 // same order and run the same control code, so their decisions agree bit for bit and every
 // block leaves the loop at the same barrier.  Block 0 writes the state back, writes the trace,
 // and (if use_cond) sets the device-side loop condition of the enclosing graph.
-__global__ void __launch_bounds__(kThreads, 3) k_loop(RowArgs ra, ColArgs ca, double* part_rows,
+template <class V>
+__global__ void __launch_bounds__(kThreads, 3) k_loop(RowArgsT<V> ra, ColArgsT<V> ca, double* part_rows,
                                                       double* part_cols, int32_t iters,
                                                       cudaGraphConditionalHandle cond,
                                                       int32_t use_cond) {
   cg::grid_group grid = cg::this_grid();
   __shared__ Ctl sc;
   __shared__ RowStep rst;
-  __shared__ ColStep cst;
+  __shared__ ColStepT<V> cst;
   if (threadIdx.x == 0) sc = *ra.ctl;
   __syncthreads();
   const LoadPolicy pol = make_policy();
@@ -353,10 +398,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_loop(RowArgs ra, ColArgs ca, do
     if (threadIdx.x == 0) rst = row_step(sc);
     __syncthreads();
     const RowStep st = rst;
-    const double* __restrict__ xh = (sc.t & 1) ? ra.xh1 : ra.xh0;
+    const V* __restrict__ xh = (sc.t & 1) ? ra.xh1 : ra.xh0;
     double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for_each_row(ra.bins, ra.rp, ra.ci, ra.val, xh, pol, s,
-                 [&](int i, double v, double (&acc)[kNumSums]) { row_epilogue(ra, st, i, v, acc); });
+                 [&](int i, V v, double (&acc)[kNumSums]) { row_epilogue(ra, st, i, v, acc); });
     const int nr = st.check ? 5 : 3;
     store_block_partials(s, nr, part_rows);
     grid.sync();
@@ -368,10 +413,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_loop(RowArgs ra, ColArgs ca, do
     // ---- column phase
     if (threadIdx.x == 0) cst = col_step(sc, ca);
     __syncthreads();
-    const ColStep cs = cst;
+    const ColStepT<V> cs = cst;
     double s2[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for_each_row(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, s2,
-                 [&](int j, double u, double (&acc)[kNumSums]) { col_epilogue(ca, cs, j, u, acc); });
+                 [&](int j, V u, double (&acc)[kNumSums]) { col_epilogue(ca, cs, j, u, acc); });
     const int nc = cs.check ? 5 : 2;
     store_block_partials(s2, nc, part_cols);
     grid.sync();
@@ -402,22 +447,22 @@ __global__ void k_init_ctl(Ctl* dst, Ctl src) {
 
 // First primal step from z = 0: xhat_0 = proj_X(-tau c); zeroes the iterate, the anchors and
 // the maintained products; sums |0 - xhat_0|^2 and |xhat_0 - 0|^2 for r_0.
-__global__ void __launch_bounds__(kThreads) k_init_cols(int32_t n, const double* __restrict__ c,
-                                                        const double* __restrict__ lv,
-                                                        const double* __restrict__ uv,
-                                                        double* xh0, double* x, double* x0,
-                                                        double* aty, double* aty0, Ctl* ctl,
+template <class V>
+__global__ void __launch_bounds__(kThreads) k_init_cols(int32_t n, const V* __restrict__ c,
+                                                        const V* __restrict__ lv,
+                                                        const V* __restrict__ uv, V* xh0, V* x,
+                                                        V* x0, V* aty, V* aty0, Ctl* ctl,
                                                         double* partials) {
-  const double tau = ctl->tau;
+  const V tau = (V)ctl->tau;
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const double xn = clampd(-tau * c[j], lv[j], uv[j]);
+    const V xn = clampd(-tau * c[j], lv[j], uv[j]);
     xh0[j] = xn;
-    x[j] = 0.0;
-    x0[j] = 0.0;
-    aty[j] = 0.0;
-    aty0[j] = 0.0;
-    s[0] = fma(xn, xn, s[0]);
+    x[j] = V(0);
+    x0[j] = V(0);
+    aty[j] = V(0);
+    aty0[j] = V(0);
+    acc_fma(s[0], xn, xn);
   }
   if (!block_sums_last(s, 1, partials, &ctl->count0)) return;
   double tot[kNumSums];
@@ -428,16 +473,125 @@ __global__ void __launch_bounds__(kThreads) k_init_cols(int32_t n, const double*
   ctl->count0 = 0;
 }
 
-__global__ void k_init_rows(int32_t m, double* y, double* y0, double* yh, double* ax, double* ax0,
-                            double* axh) {
+template <class V>
+__global__ void k_init_rows(int32_t m, V* y, V* y0, V* yh, V* ax, V* ax0, V* axh) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    y[i] = 0.0;
-    y0[i] = 0.0;
-    yh[i] = 0.0;
-    ax[i] = 0.0;
-    ax0[i] = 0.0;
-    axh[i] = 0.0;
+    y[i] = V(0);
+    y0[i] = V(0);
+    yh[i] = V(0);
+    ax[i] = V(0);
+    ax0[i] = V(0);
+    axh[i] = V(0);
   }
+}
+
+// ------------------------------------------------------------- mixed precision
+
+__global__ void k_to_float(int64_t len, const double* __restrict__ src, float* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+// dst[i] = dst2[i] = (double)src[i] (dst2 may be null).
+__global__ void k_to_double(int64_t len, const float* __restrict__ src, double* __restrict__ dst,
+                            double* __restrict__ dst2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)src[i];
+    dst[i] = v;
+    if (dst2) dst2[i] = v;
+  }
+}
+
+// Hand-over from the FP32 phase to the FP64 refinement phase (a new epoch anchored at the FP32
+// point): the FP64 phase continues the iteration count, omega and the PID state, starts with
+// k = 0 and the restart flag set (so its first row step takes y = yhat, Ax = A xhat as iterate
+// and anchor), gets the final tolerance and max_iter_fp64 further iterations.  After a stall
+// of the FP32 phase, omega and the PID state go back to their values at its best check (past
+// that point the FP32 rounding, not the iterate, drove the PID).  A NUMERICAL end of the FP32
+// phase is kept and ends the solve.
+__global__ void k_switch_ctl(Ctl* ctl, double tol, int64_t max_iter_fp64) {
+  const int64_t it32 = ctl->iters;
+  ctl->iters32 = it32;
+  if (ctl->status == kNumerical) return;
+  if (ctl->status == kStalled && ctl->best_kkt < INFINITY) {
+    const double om = ctl->omega_best, eta = ctl->eta;
+    ctl->omega = om;
+    ctl->tau = eta / om;
+    ctl->sigma = eta * om;
+    ctl->inv_sigma = 1.0 / (eta * om);
+    ctl->w_over_eta = om / eta;
+    ctl->inv_eta_w = 1.0 / (eta * om);
+    ctl->pid_integral = ctl->integral_best;
+    ctl->pid_eprev = ctl->eprev_best;
+  }
+  ctl->patience = 0;
+  ctl->t = it32;
+  ctl->k = 0;
+  ctl->restart = 1;
+  ctl->done = 0;
+  ctl->status = 0;
+  ctl->tol = tol;
+  ctl->max_iter = it32 + max_iter_fp64;
+  ctl->bodies = 0;
+}
+
+// Copies the FP32 phase's returned point to FP64: zhat_T of its last iteration T = iters - 1
+// (xhat in the ping-pong buffer of T's parity), or after a stall the best check's zhat from the
+// stall guard's slot buffers.  Destination: x and x0 (refinement start) or, for an FP32-only
+// solve (or an FP32 phase that ended NUMERICAL, which ends the solve), the FP64 xhat buffer of
+// T's parity and yhat.  An FP32-only solve that stalled also reports the best check's KKT values.
+// Runs on the FP32 phase's final state, before k_switch_ctl.
+__global__ void k_switch_vectors(int32_t n, int32_t m, Ctl* ctl, const float* __restrict__ xh0f,
+                                 const float* __restrict__ xh1f, const float* __restrict__ yhf,
+                                 const float* __restrict__ xb0, const float* __restrict__ xb1,
+                                 const float* __restrict__ yb0, const float* __restrict__ yb1,
+                                 double* x, double* x0, double* yh, double* xh0, double* xh1,
+                                 int32_t fp32_only) {
+  if (ctl->status == kNumerical) fp32_only = 1;
+  const int64_t last = ctl->iters - 1;
+  const bool best = ctl->status == kStalled && ctl->best_slot >= 0 && xb0 != nullptr;
+  const float* xs = best ? (ctl->best_slot ? xb1 : xb0) : ((last & 1) ? xh1f : xh0f);
+  const float* ys = best ? (ctl->best_slot ? yb1 : yb0) : yhf;
+  double* xo = fp32_only ? ((last & 1) ? xh1 : xh0) : x;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)xs[j];
+    xo[j] = v;
+    if (!fp32_only) x0[j] = v;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    yh[i] = (double)ys[i];
+  if (best && fp32_only && blockIdx.x == 0 && threadIdx.x == 0)
+    for (int q = 0; q < 8; ++q) ctl->kkt[q] = ctl->kkt_best[q];
+}
+
+// FP64 refinement start: xhat = proj_X(x - tau (c - A^T y)) for the given x and A^T y (both
+// FP64 already), aty0 = aty, and the sums |x - xhat|^2 = |xhat - x0|^2 (x0 = x).
+__global__ void __launch_bounds__(kThreads) k_warm_cols(int32_t n, const double* __restrict__ c,
+                                                        const double* __restrict__ lv,
+                                                        const double* __restrict__ uv, double* xh0,
+                                                        double* xh1, const double* __restrict__ x,
+                                                        const double* __restrict__ aty,
+                                                        double* __restrict__ aty0, Ctl* ctl,
+                                                        double* partials) {
+  if (ctl->done) return;  // the FP32 phase ended the solve (NUMERICAL)
+  const double tau = ctl->tau;
+  double* xh = (ctl->t & 1) ? xh1 : xh0;
+  double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const double xj = x[j];
+    const double xn = clampd(fma(-tau, c[j] - aty[j], xj), lv[j], uv[j]);
+    xh[j] = xn;
+    aty0[j] = aty[j];
+    const double d = xj - xn;
+    s[0] = fma(d, d, s[0]);
+  }
+  if (!block_sums_last(s, 1, partials, &ctl->count0)) return;
+  double tot[kNumSums];
+  block_totals(partials, gridDim.x, 1, nullptr, tot);
+  if (threadIdx.x != 0) return;
+  ctl->sxx = tot[0];
+  ctl->sx0 = tot[0];
+  ctl->count0 = 0;
 }
 
 // Sets the device-side loop condition of the split-kernel graph: keep iterating while the solve
@@ -472,5 +626,19 @@ __global__ void __launch_bounds__(kThreads) k_spmv(const int32_t* __restrict__ r
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for_each_row(bins, rp, ci, val, x, pol, s, [&](int i, double v, double (&)[kNumSums]) { y[i] = v; });
 }
+
+// explicit instantiations for both precisions
+template <class V>
+IterKernels<V> iter_kernels() {
+  IterKernels<V> k;
+  k.rows = k1_rows<V>;
+  k.cols = k2_cols<V>;
+  k.loop = k_loop<V>;
+  k.init_cols = k_init_cols<V>;
+  k.init_rows = k_init_rows<V>;
+  return k;
+}
+template IterKernels<double> iter_kernels<double>();
+template IterKernels<float> iter_kernels<float>();
 
 }  // namespace pdhg

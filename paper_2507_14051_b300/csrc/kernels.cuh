@@ -6,32 +6,42 @@
 
 namespace pdhg {
 
-struct RowArgs {
+// Argument blocks of the two phases, for value type V (double: FP64 path; float: the FP32
+// phase of the mixed-precision solve).  The scalar state, the reductions and the control are
+// FP64 in both.
+template <class V>
+struct RowArgsT {
   const int32_t* rp;
   const int32_t* ci;
-  const double* val;
-  const double* xh0;  // xhat ping-pong: xhat_t is xh[t & 1]
-  const double* xh1;
-  double *y, *y0, *yh, *ax, *ax0, *axh;
-  const double *lc, *uc, *inv_dr;
+  const V* val;
+  const V* xh0;  // xhat ping-pong: xhat_t is xh[t & 1]
+  const V* xh1;
+  V *y, *y0, *yh, *ax, *ax0, *axh;
+  const V *lc, *uc, *inv_dr;
+  V *yb0, *yb1;  // FP32 stall guard: yhat at check iterations, two slots (null: guard off)
   Ctl* ctl;
   double* partials;
   double* trace;
   BinTable bins;
 };
 
-struct ColArgs {
+template <class V>
+struct ColArgsT {
   const int32_t* rp;
   const int32_t* ci;
-  const double* val;
-  const double* yh;
-  double *xh0, *xh1;
-  double *x, *x0, *aty, *aty0;
-  const double *c, *lv, *uv, *inv_dc;
+  const V* val;
+  const V* yh;
+  V *xh0, *xh1;
+  V *x, *x0, *aty, *aty0;
+  const V *c, *lv, *uv, *inv_dc;
+  V *xb0, *xb1;  // FP32 stall guard: xhat at check iterations, two slots (null: guard off)
   Ctl* ctl;
   double* partials;
   BinTable bins;
 };
+
+using RowArgs = RowArgsT<double>;
+using ColArgs = ColArgsT<double>;
 
 struct PwCtl {
   double lambda, s;
@@ -39,22 +49,38 @@ struct PwCtl {
   int32_t step;  // index of the current step inside a batch (lambda is also stored in hist[step])
 };
 
-// iterate.cu
-__global__ void k1_rows(RowArgs a);
-__global__ void k2_cols(ColArgs a);
-__global__ void k_loop(RowArgs ra, ColArgs ca, double* part_rows, double* part_cols, int32_t iters,
-                       cudaGraphConditionalHandle cond, int32_t use_cond);
+// iterate.cu.  The phase kernels are templates over the value type V of the matrix and the
+// iterates (double; float for the first phase of a mixed-precision solve).  A __global__
+// template is launched only from the file that instantiates it (elsewhere its launch stub has no
+// registered device code), so other files launch them through these pointers.
+template <class V>
+struct IterKernels {
+  void (*rows)(RowArgsT<V>);
+  void (*cols)(ColArgsT<V>);
+  void (*loop)(RowArgsT<V>, ColArgsT<V>, double*, double*, int32_t, cudaGraphConditionalHandle, int32_t);
+  void (*init_cols)(int32_t, const V*, const V*, const V*, V*, V*, V*, V*, V*, Ctl*, double*);
+  void (*init_rows)(int32_t, V*, V*, V*, V*, V*, V*);
+};
+template <class V>
+IterKernels<V> iter_kernels();  // instantiated for double and float in iterate.cu
 __global__ void k_init_ctl(Ctl* dst, Ctl src);
-__global__ void k_init_cols(int32_t n, const double* c, const double* lv, const double* uv,
-                            double* xh0, double* x, double* x0, double* aty, double* aty0,
-                            Ctl* ctl, double* partials);
-__global__ void k_init_rows(int32_t m, double* y, double* y0, double* yh, double* ax,
-                            double* ax0, double* axh);
 __global__ void k_set_cond(cudaGraphConditionalHandle h, Ctl* ctl, int32_t unroll);
 __global__ void k_unpermute_scale(int32_t len, const int32_t* perm, const double* v,
                                   const double* d, double* out);
 __global__ void k_spmv(const int32_t* rp, const int32_t* ci, const double* val, const double* x,
                        double* y, BinTable bins);
+// mixed precision: conversions and the hand-over from the FP32 phase to the FP64 phase
+__global__ void k_to_float(int64_t len, const double* src, float* dst);
+__global__ void k_to_double(int64_t len, const float* src, double* dst, double* dst2);
+__global__ void k_switch_ctl(Ctl* ctl, double tol, int64_t max_iter_fp64);
+__global__ void k_switch_vectors(int32_t n, int32_t m, Ctl* ctl, const float* xh0f,
+                                 const float* xh1f, const float* yhf, const float* xb0,
+                                 const float* xb1, const float* yb0, const float* yb1, double* x,
+                                 double* x0, double* yh, double* xh0, double* xh1,
+                                 int32_t fp32_only);
+__global__ void k_warm_cols(int32_t n, const double* c, const double* lv, const double* uv,
+                            double* xh0, double* xh1, const double* x, const double* aty,
+                            double* aty0, Ctl* ctl, double* partials);
 
 // setup.cu
 __global__ void k_row_factor(int32_t rows, const int32_t* rp, const double* val, int32_t kind,

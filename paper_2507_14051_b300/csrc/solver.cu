@@ -89,6 +89,18 @@ struct lp_solver {
   double *lc = nullptr, *uc = nullptr, *inv_dr = nullptr, *dr = nullptr;
   double *x = nullptr, *x0 = nullptr, *xh0 = nullptr, *xh1 = nullptr, *aty = nullptr, *aty0 = nullptr;
   double *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
+  // FP32 phase of the mixed-precision solve (allocated when precision != 0)
+  struct F32 {
+    float *valA = nullptr, *valT = nullptr;
+    float *c = nullptr, *lv = nullptr, *uv = nullptr, *inv_dc = nullptr;
+    float *x = nullptr, *x0 = nullptr, *xh0 = nullptr, *xh1 = nullptr, *aty = nullptr, *aty0 = nullptr;
+    float *lc = nullptr, *uc = nullptr, *inv_dr = nullptr;
+    float *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
+    float *xb0 = nullptr, *xb1 = nullptr, *yb0 = nullptr, *yb1 = nullptr;  // stall guard's slots
+  } f32;
+  cudaGraph_t graph32 = nullptr;
+  cudaGraphExec_t exec32 = nullptr;
+  bool loop_active32 = false;
   double* out_buf = nullptr;
   double* partials = nullptr;
   double* partials2 = nullptr;  // column-phase partials of the loop kernel
@@ -120,6 +132,8 @@ struct lp_solver {
   ~lp_solver() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    if (exec32) cudaGraphExecDestroy(exec32);
+    if (graph32) cudaGraphDestroy(graph32);
     for (void* p : allocations) cudaFree(p);
     if (pinned) cudaFreeHost(pinned);
     if (setup_stream) cudaStreamDestroy(setup_stream);
@@ -144,6 +158,9 @@ lp_status check_params(const lp_params& p) {
   if (p.unroll < 1 || p.unroll > 64) return fail(LP_ERR_INVALID_ARG, "unroll must be in [1, 64]");
   if (p.lane_target < 1 || p.lane_target > 64) return fail(LP_ERR_INVALID_ARG, "lane_target must be in [1, 64]");
   if (p.persistent < -1 || p.persistent > 1) return fail(LP_ERR_INVALID_ARG, "persistent must be -1, 0 or 1");
+  if (p.precision < 0 || p.precision > 2) return fail(LP_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
+  if (!(p.switch_tol >= 0.0)) return fail(LP_ERR_INVALID_ARG, "switch_tol must be >= 0");
+  if (p.fp32_patience < 0) return fail(LP_ERR_INVALID_ARG, "fp32_patience must be >= 0");
   return LP_OK;
 }
 
@@ -244,7 +261,27 @@ void fill_args(const lp_solver* h, RowArgs& ra, ColArgs& ca) {
   ca.ctl = h->ctl; ca.partials = h->partials; ca.bins = h->binsT;
 }
 
-cudaError_t launch_loop(const lp_solver* h, const RowArgs& ra, const ColArgs& ca, int32_t iters,
+void fill_args(const lp_solver* h, RowArgsT<float>& ra, ColArgsT<float>& ca) {
+  const auto& f = h->f32;
+  ra = RowArgsT<float>{};
+  ra.rp = h->rpA; ra.ci = h->ciA; ra.val = f.valA;
+  ra.xh0 = f.xh0; ra.xh1 = f.xh1;
+  ra.y = f.y; ra.y0 = f.y0; ra.yh = f.yh; ra.ax = f.ax; ra.ax0 = f.ax0; ra.axh = f.axh;
+  ra.lc = f.lc; ra.uc = f.uc; ra.inv_dr = f.inv_dr;
+  ra.yb0 = f.yb0; ra.yb1 = f.yb1;
+  ra.ctl = h->ctl; ra.partials = h->partials; ra.trace = h->trace_cap > 0 ? h->trace : nullptr;
+  ra.bins = h->binsA;
+  ca = ColArgsT<float>{};
+  ca.rp = h->rpT; ca.ci = h->ciT; ca.val = f.valT; ca.yh = f.yh;
+  ca.xh0 = f.xh0; ca.xh1 = f.xh1;
+  ca.x = f.x; ca.x0 = f.x0; ca.aty = f.aty; ca.aty0 = f.aty0;
+  ca.c = f.c; ca.lv = f.lv; ca.uv = f.uv; ca.inv_dc = f.inv_dc;
+  ca.xb0 = f.xb0; ca.xb1 = f.xb1;
+  ca.ctl = h->ctl; ca.partials = h->partials; ca.bins = h->binsT;
+}
+
+template <class V>
+cudaError_t launch_loop(const lp_solver* h, const RowArgsT<V>& ra, const ColArgsT<V>& ca, int32_t iters,
                         cudaGraphConditionalHandle cond, int32_t use_cond, cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)h->gridL);
@@ -256,64 +293,76 @@ cudaError_t launch_loop(const lp_solver* h, const RowArgs& ra, const ColArgs& ca
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_loop, ra, ca, h->partials, h->partials2, iters, cond, use_cond);
+  return cudaLaunchKernelEx(&cfg, iter_kernels<V>().loop, ra, ca, h->partials, h->partials2, iters, cond, use_cond);
 }
 
-// Captures the solve loop: a graph whose conditional while node runs the body until the solve
-// is done.  Body: one cooperative launch of the loop kernel (`unroll` iterations; it sets the
-// loop condition itself) or, for persistent = 0 or if the driver refuses a cooperative kernel
-// in the body, `unroll` pairs of the phase kernels plus the kernel that sets the condition.
-lp_status build_graph(lp_solver* h) {
+// Captures the solve loop of one precision: a graph whose conditional while node runs the body
+// until the solve is done.  Body: one cooperative launch of the loop kernel (`unroll`
+// iterations; it sets the loop condition itself) or, for persistent = 0 or if the driver
+// refuses a cooperative kernel in the body, `unroll` pairs of the phase kernels plus the kernel
+// that sets the condition.
+template <class V>
+lp_status build_graph_for(lp_solver* h, cudaGraph_t* graph, cudaGraphExec_t* exec, bool* loop_active) {
   for (int attempt = 0; attempt < 2; ++attempt) {
-    if (h->exec) {
-      cudaGraphExecDestroy(h->exec);
-      h->exec = nullptr;
+    if (*exec) {
+      cudaGraphExecDestroy(*exec);
+      *exec = nullptr;
     }
-    if (h->graph) {
-      cudaGraphDestroy(h->graph);
-      h->graph = nullptr;
+    if (*graph) {
+      cudaGraphDestroy(*graph);
+      *graph = nullptr;
     }
     const bool want = h->prm.persistent == 1 || (h->prm.persistent == -1 && h->loop_fits);
     const bool loop = want && attempt == 0;
-    RowArgs ra{};
-    ColArgs ca{};
+    RowArgsT<V> ra{};
+    ColArgsT<V> ca{};
     fill_args(h, ra, ca);
-    CK(cudaGraphCreate(&h->graph, 0));
+    CK(cudaGraphCreate(graph, 0));
     cudaGraphConditionalHandle cond;
-    CK(cudaGraphConditionalHandleCreate(&cond, h->graph, 1, cudaGraphCondAssignDefault));
+    CK(cudaGraphConditionalHandleCreate(&cond, *graph, 1, cudaGraphCondAssignDefault));
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = cond;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t node;
-    CK(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &cp));
+    CK(cudaGraphAddNode(&node, *graph, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaStream_t s = h->setup_stream;
     CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
     if (loop) {
-      le = launch_loop(h, ra, ca, h->prm.unroll, cond, 1, s);
+      le = launch_loop<V>(h, ra, ca, h->prm.unroll, cond, 1, s);
     } else {
       for (int u = 0; u < h->prm.unroll; ++u) {
-        k1_rows<<<h->gridA, kThreads, 0, s>>>(ra);
-        k2_cols<<<h->gridT, kThreads, 0, s>>>(ca);
+        iter_kernels<V>().rows<<<h->gridA, kThreads, 0, s>>>(ra);
+        iter_kernels<V>().cols<<<h->gridT, kThreads, 0, s>>>(ca);
       }
       k_set_cond<<<1, 1, 0, s>>>(cond, h->ctl, h->prm.unroll);
     }
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &captured);
-    if (e == cudaSuccess && le == cudaSuccess) e = cudaGraphInstantiate(&h->exec, h->graph, 0);
+    if (e == cudaSuccess && le == cudaSuccess) e = cudaGraphInstantiate(exec, *graph, 0);
     else if (e == cudaSuccess) e = le;
     if (e == cudaSuccess) {
-      h->loop_active = loop;
-      h->graph_unroll = h->prm.unroll;
+      *loop_active = loop;
       return LP_OK;
     }
-    cudaGetLastError();  // clear the sticky-free launch error before retrying without the loop kernel
+    cudaGetLastError();  // clear the launch error before retrying without the loop kernel
     if (!loop) return fail(LP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   }
   return fail(LP_ERR_CUDA, "graph capture failed");
+}
+
+lp_status build_graph(lp_solver* h) {
+  lp_status st = build_graph_for<double>(h, &h->graph, &h->exec, &h->loop_active);
+  if (st != LP_OK) return st;
+  if (h->prm.precision != 0) {
+    st = build_graph_for<float>(h, &h->graph32, &h->exec32, &h->loop_active32);
+    if (st != LP_OK) return st;
+  }
+  h->graph_unroll = h->prm.unroll;
+  return LP_OK;
 }
 
 // Power iteration (Section 3, "Stepsize") on the device.  Steps run in batches of kPwBatch
@@ -434,14 +483,19 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   h->binsT = make_bins(rpT, h->prm.lane_target, chunksT);
 
   int occA = 0, occT = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k1_rows, kThreads, 0));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occT, k2_cols, kThreads, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, iter_kernels<double>().rows, kThreads, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occT, iter_kernels<double>().cols, kThreads, 0));
   if (occA < 1) occA = 1;
   if (occT < 1) occT = 1;
   h->gridA = grid_for_tasks((int64_t)h->binsA.ntasks + h->binsA.nchunks, h->num_sms, occA * h->num_sms);
   h->gridT = grid_for_tasks((int64_t)h->binsT.ntasks + h->binsT.nchunks, h->num_sms, occT * h->num_sms);
   int occL = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occL, k_loop, kThreads, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occL, iter_kernels<double>().loop, kThreads, 0));
+  if (h->prm.precision != 0) {  // one loop grid serves both precisions
+    int occF = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occF, iter_kernels<float>().loop, kThreads, 0));
+    if (occF < occL) occL = occF;
+  }
   if (occL < 1) occL = 1;
   h->gridL = h->gridA > h->gridT ? h->gridA : h->gridT;
   h->loop_fits = h->gridL <= occL * h->num_sms;
@@ -540,6 +594,25 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   if (n > 0) k_scale_cols<<<h->gridV, 256, 0, s>>>(n, h->dc, h->c, h->lv, h->uv, h->inv_dc);
   if (m > 0) k_scale_rows<<<h->gridV, 256, 0, s>>>(m, h->dr, h->lc, h->uc, h->inv_dr);
   CK(cudaGetLastError());
+  if (h->prm.precision != 0) {
+    auto& f = h->f32;
+    CK(h->alloc(&f.valA, nnz)); CK(h->alloc(&f.valT, nnz));
+    for (float** q : {&f.c, &f.lv, &f.uv, &f.inv_dc, &f.x, &f.x0, &f.xh0, &f.xh1, &f.aty, &f.aty0,
+                      &f.xb0, &f.xb1})
+      CK(h->alloc(q, n));
+    for (float** q : {&f.lc, &f.uc, &f.inv_dr, &f.y, &f.y0, &f.yh, &f.ax, &f.ax0, &f.axh, &f.yb0, &f.yb1})
+      CK(h->alloc(q, m));
+    const int g = grid_for(nnz > 0 ? nnz : 1, 256, 8 * h->num_sms);
+    k_to_float<<<g, 256, 0, s>>>(nnz, h->valA, f.valA);
+    k_to_float<<<g, 256, 0, s>>>(nnz, h->valT, f.valT);
+    for (auto pr : {std::make_pair((const double*)h->c, f.c), std::make_pair((const double*)h->lv, f.lv),
+                    std::make_pair((const double*)h->uv, f.uv), std::make_pair((const double*)h->inv_dc, f.inv_dc)})
+      k_to_float<<<h->gridV, 256, 0, s>>>(n, pr.first, pr.second);
+    for (auto pr : {std::make_pair((const double*)h->lc, f.lc), std::make_pair((const double*)h->uc, f.uc),
+                    std::make_pair((const double*)h->inv_dr, f.inv_dr)})
+      k_to_float<<<h->gridV, 256, 0, s>>>(m, pr.first, pr.second);
+    CK(cudaGetLastError());
+  }
   CK(cudaStreamSynchronize(s));
 
   lp_status st = set_eta(h);
@@ -576,6 +649,9 @@ lp_status lp_default_params(lp_params* p) {
   p->unroll = 8;
   p->lane_target = 8;
   p->persistent = -1;
+  p->precision = 0;
+  p->switch_tol = 1e-5;
+  p->fp32_patience = 32;
   return LP_OK;
 }
 
@@ -642,6 +718,7 @@ lp_status lp_set_params(lp_handle h, const lp_params* p) {
   h->prm.pc_enabled = old.pc_enabled;
   h->prm.pc_alpha = old.pc_alpha;
   h->prm.lane_target = old.lane_target;  // the bin tables are built at lp_create
+  h->prm.precision = old.precision;      // the FP32 buffers are made at lp_create
   if (p->power_seed != old.power_seed || p->power_tol != old.power_tol ||
       p->power_max_iter != old.power_max_iter)
     h->power_valid = false;
@@ -666,7 +743,9 @@ lp_status lp_set_params(lp_handle h, const lp_params* p) {
 
 namespace {
 
-// Scalar state, zero iterate and first primal step of a solve, enqueued on s.
+// Scalar state, zero iterate and first primal step of a solve, enqueued on s, for the buffers
+// of precision V (the FP64 set, or the FP32 set of a mixed-precision solve).
+template <class V>
 lp_status enqueue_start(lp_solver* h, double tol, int64_t max_iter, cudaStream_t s) {
   Ctl init{};
   init.eta = h->eta;
@@ -693,10 +772,33 @@ lp_status enqueue_start(lp_solver* h, double tol, int64_t max_iter, cudaStream_t
   init.kp = h->prm.k_p;
   init.ki = h->prm.k_i;
   init.kd = h->prm.k_d;
+  init.patience = (sizeof(V) == sizeof(float)) ? h->prm.fp32_patience : 0;
+  init.best_kkt = INFINITY;
+  init.cand_slot = 0;
+  init.best_slot = -1;
   k_init_ctl<<<1, 1, 0, s>>>(h->ctl, init);
-  k_init_rows<<<h->gridV, 256, 0, s>>>(h->m, h->y, h->y0, h->yh, h->ax, h->ax0, h->axh);
-  k_init_cols<<<h->gridV, kThreads, 0, s>>>(h->n, h->c, h->lv, h->uv, h->xh0, h->x, h->x0, h->aty,
-                                            h->aty0, h->ctl, h->partials);
+  RowArgsT<V> ra;
+  ColArgsT<V> ca;
+  fill_args(h, ra, ca);
+  iter_kernels<V>().init_rows<<<h->gridV, 256, 0, s>>>(h->m, ra.y, ra.y0, ra.yh, ra.ax, ra.ax0, ra.axh);
+  iter_kernels<V>().init_cols<<<h->gridV, kThreads, 0, s>>>(h->n, ca.c, ca.lv, ca.uv, ca.xh0, ca.x, ca.x0, ca.aty, ca.aty0,
+                                               h->ctl, h->partials);
+  CK(cudaGetLastError());
+  return LP_OK;
+}
+
+// Mixed precision, after the FP32 phase: hand the FP32 point over to the FP64 buffers as the
+// anchor of a new epoch (A x and A^T y recomputed in FP64 from it) and continue in FP64.
+lp_status enqueue_switch(lp_solver* h, double tol, int64_t max_iter, cudaStream_t s) {
+  const auto& f = h->f32;
+  const int g = grid_for((int64_t)(h->n > h->m ? h->n : h->m), 256, 4 * h->num_sms);
+  k_switch_vectors<<<g, 256, 0, s>>>(h->n, h->m, h->ctl, f.xh0, f.xh1, f.yh, f.xb0, f.xb1, f.yb0, f.yb1,
+                                     h->x, h->x0, h->yh, h->xh0, h->xh1, 0);
+  k_switch_ctl<<<1, 1, 0, s>>>(h->ctl, tol, max_iter);
+  k_spmv<<<h->gridA, kThreads, 0, s>>>(h->rpA, h->ciA, h->valA, h->x, h->axh, h->binsA);
+  k_spmv<<<h->gridT, kThreads, 0, s>>>(h->rpT, h->ciT, h->valT, h->yh, h->aty, h->binsT);
+  k_warm_cols<<<h->gridV, kThreads, 0, s>>>(h->n, h->c, h->lv, h->uv, h->xh0, h->xh1, h->x, h->aty, h->aty0,
+                                            h->ctl, h->partials);
   CK(cudaGetLastError());
   return LP_OK;
 }
@@ -712,9 +814,29 @@ lp_status lp_solve(lp_handle h, double tol, int64_t max_iter, void* stream) {
   if (max_iter < 1) return fail(LP_ERR_INVALID_ARG, "max_iter must be >= 1");
   CK(cudaSetDevice(h->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  lp_status st = enqueue_start(h, tol, max_iter, s);
-  if (st != LP_OK) return st;
-  CK(cudaGraphLaunch(h->exec, s));
+  lp_status st = LP_OK;
+  if (h->prm.precision == 0) {
+    st = enqueue_start<double>(h, tol, max_iter, s);
+    if (st != LP_OK) return st;
+    CK(cudaGraphLaunch(h->exec, s));
+  } else {
+    // FP32 phase: to max(tol, switch_tol) (mixed) or tol (FP32 only), at most max_iter iterations
+    const double tol32 = h->prm.precision == 1 ? (tol > h->prm.switch_tol ? tol : h->prm.switch_tol) : tol;
+    st = enqueue_start<float>(h, tol32, max_iter, s);
+    if (st != LP_OK) return st;
+    CK(cudaGraphLaunch(h->exec32, s));
+    if (h->prm.precision == 1) {
+      st = enqueue_switch(h, tol, max_iter, s);
+      if (st != LP_OK) return st;
+      CK(cudaGraphLaunch(h->exec, s));
+    } else {
+      const auto& f = h->f32;
+      const int g = grid_for((int64_t)(h->n > h->m ? h->n : h->m), 256, 4 * h->num_sms);
+      k_switch_vectors<<<g, 256, 0, s>>>(h->n, h->m, h->ctl, f.xh0, f.xh1, f.yh, f.xb0, f.xb1, f.yb0,
+                                         f.yb1, h->x, h->x0, h->yh, h->xh0, h->xh1, 1);
+      CK(cudaGetLastError());
+    }
+  }
   h->solved = true;
   h->last_stream = s;
   return LP_OK;
@@ -750,10 +872,11 @@ lp_status lp_get(lp_handle h, double* x, double* y, int32_t* solve_status, doubl
   return LP_OK;
 }
 
-lp_status lp_get_info(lp_handle h, double* out8) {
+lp_status lp_get_info(lp_handle h, double* out9) {
   g_err.clear();
-  if (!h || !out8) return fail(LP_ERR_INVALID_ARG, "NULL argument");
-  double* out7 = out8;
+  if (!h || !out9) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  double* out7 = out9;
+  double* out8 = out9;
   if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "lp_get_info before lp_solve");
   CK(cudaSetDevice(h->device));
   CK(cudaStreamSynchronize(h->last_stream));
@@ -767,6 +890,7 @@ lp_status lp_get_info(lp_handle h, double* out8) {
   out7[5] = ctl.kkt[4];
   out7[6] = ctl.kkt[5];
   out8[7] = h->loop_active ? 1.0 : 0.0;
+  out9[8] = h->prm.precision == 1 ? (double)ctl.iters32 : (h->prm.precision == 2 ? (double)ctl.iters : 0.0);
   return LP_OK;
 }
 
@@ -803,7 +927,7 @@ lp_status lp_time_kernels(lp_handle h, int64_t iters, void* stream, double* ms_o
   const bool loop = h->loop_active;
   const int32_t per = loop ? h->prm.unroll : 1;
   const int64_t launches = (iters + per - 1) / per;
-  lp_status st = enqueue_start(h, 0.0, launches * per, s);
+  lp_status st = enqueue_start<double>(h, 0.0, launches * per, s);
   if (st != LP_OK) return st;
   RowArgs ra{};
   ColArgs ca{};
@@ -814,12 +938,12 @@ lp_status lp_time_kernels(lp_handle h, int64_t iters, void* stream, double* ms_o
   CK(cudaEventRecord(ev[0], s));
   for (int64_t q = 0; q < launches; ++q) {
     if (loop) {
-      CK(launch_loop(h, ra, ca, per, cudaGraphConditionalHandle{}, 0, s));
+      CK(launch_loop<double>(h, ra, ca, per, cudaGraphConditionalHandle{}, 0, s));
       CK(cudaEventRecord(ev[q + 1], s));
     } else {
-      k1_rows<<<h->gridA, kThreads, 0, s>>>(ra);
+      iter_kernels<double>().rows<<<h->gridA, kThreads, 0, s>>>(ra);
       CK(cudaEventRecord(ev[2 * q + 1], s));
-      k2_cols<<<h->gridT, kThreads, 0, s>>>(ca);
+      iter_kernels<double>().cols<<<h->gridT, kThreads, 0, s>>>(ca);
       CK(cudaEventRecord(ev[2 * q + 2], s));
     }
   }
