@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="miplib", choices=["miplib", "mcf", "small"])
+    ap.add_argument("--workload", default="miplib", choices=["miplib", "mcf", "small", "batch"])
+    ap.add_argument("--batch-count", type=int, default=512, help="instances of the batch workload")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--max-iter", type=int, default=100000)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
@@ -81,15 +82,15 @@ def workload_name(name: str, lp) -> str:
 def kernel_work(lp):
     """Algorithmic bytes and FP64 operations of one launch of each iteration kernel.
     Bytes (what the method must move, FP64 values, 32-bit indices):
-      row kernel:    12 nnz (A values + columns) + 8 (m+1) row offsets + 8 n gathered xhat
+      row kernel:    12 nnz (A values + columns) + 4 (m+1) row offsets + 8 n gathered xhat
                      + 56 m (y, y0, l_c, u_c, y read; y, yhat written)
-      column kernel: 12 nnz + 8 (n+1) + 8 m gathered yhat + 56 n (x, x0, c, l_v, u_v read;
+      column kernel: 12 nnz + 4 (n+1) + 8 m gathered yhat + 56 n (x, x0, c, l_v, u_v read;
                      x, xhat written)
     FP64 operations (fma/add/mul issued by the kernel's arithmetic): one fma per nonzero plus
     17 per row (row kernel) or 12 per column (column kernel)."""
     m, n, nnz = lp.m, lp.n, lp.nnz
-    return {"k1_rows": (12 * nnz + 8 * (m + 1) + 8 * n + 56 * m, nnz + 17 * m),
-            "k2_cols": (12 * nnz + 8 * (n + 1) + 8 * m + 56 * n, nnz + 12 * n)}
+    return {"k1_rows": (12 * nnz + 4 * (m + 1) + 8 * n + 56 * m, nnz + 17 * m),
+            "k2_cols": (12 * nnz + 4 * (n + 1) + 8 * m + 56 * n, nnz + 12 * n)}
 
 
 def source_digest() -> str:
@@ -194,6 +195,23 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
+    if args.workload == "batch":
+        from paper_2507_14051_b300 import gen
+        lps = gen.batch_uneven(0, count=args.batch_count)
+        total_it, total_s = 0, 0.0
+        for _ in range(args.steps):
+            r = batch_cpu_baseline(lps, args.tol, 8.0)
+            total_it += r["value"] * 8.0
+            total_s += 8.0
+        value = total_it / total_s
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "instance-iter/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 8000.0,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": f"{args.batch_count} uneven LPs (batch)", "tol": args.tol},
+                "cpu_baseline": dict(r, value=value),
+                "e2e": {"value": value, "unit": "instance-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     lp = make_workload(args.workload, 0)
     wl = workload_name(args.workload, lp)
     probe = 10
@@ -398,10 +416,156 @@ def run_ours(args):
     return 0
 
 
+def batch_work(lps, local_nnz, vb):
+    """Algorithmic bytes of one iteration of the grid loop over the instances it runs (those
+    with more than local_nnz nonzeros), values of vb bytes, 32-bit indices: per instance the
+    row-kernel and column-kernel terms of kernel_work with vb in place of 8."""
+    tot = 0
+    for lp in lps:
+        if lp.nnz <= local_nnz:
+            continue
+        m, n, z = lp.m, lp.n, lp.nnz
+        tot += (vb + 4) * z + 4 * (m + 1) + vb * n + 7 * vb * m
+        tot += (vb + 4) * z + 4 * (n + 1) + vb * m + 7 * vb * n
+    return tot
+
+
+def batch_cpu_baseline(lps, tol, seconds):
+    """The FP64 oracle on instances 0, 1, ... of the batch in order, each solved to tol (at
+    most 20k iterations), until about `seconds` of CPU time: instance-iterations per second."""
+    import oracle
+    it, t_used, k = 0, 0.0, 0
+    while k < len(lps) and t_used < seconds:
+        t0 = time.perf_counter()
+        out = oracle.solve(lps[k], tol=tol, max_iter=20000)
+        t_used += time.perf_counter() - t0
+        it += out["iters"]
+        k += 1
+    return {"value": it / t_used, "unit": "instance-iter/s", "cores": 1, "kind": "oracle",
+            "sample": f"instances 0..{k - 1} of the batch, each solved to {tol:g} from zero (at most "
+                      f"20k iterations), single-threaded FP64 oracle, {t_used:.1f} s"}
+
+
+def run_batch(args):
+    """Batch workload: one lp_batch_solve over every instance = one step."""
+    import torch
+    import paper_2507_14051_b300 as lpx
+    from paper_2507_14051_b300 import gen
+    from paper_2507_14051_b300.dist import reduce_elapsed_and_work
+
+    rank, local, world = _env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    lps = gen.batch_uneven(rank, count=args.batch_count)
+    nnz = sum(lp.nnz for lp in lps)
+    wl = (f"{args.batch_count} uneven LPs, m log-uniform in [100, 20000], n = 2m, 1 % density, N(0,1), "
+          f"box [0,1], planted optima (sum m = {sum(lp.m for lp in lps)}, sum nnz = {nnz})")
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    t0 = time.perf_counter()
+    b = lpx.BatchSolver(lps, precision=args.precision, switch_tol=args.switch_tol)
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    local_nnz = int(b.params.batch_local_nnz)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        b.solve(args.tol, args.max_iter, sp)
+        b.summary()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, total_it, launches, steps_out = 0.0, 0, 0, []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.solve(args.tol, args.max_iter, sp)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        total_ms += ms
+        sm = b.summary()
+        total_it += int(sm["iters"].sum())
+        grid_it = [int(i) for i, lp in zip(sm["iters"], lps) if lp.nnz > local_nnz]
+        stages = 2 if args.precision == 1 else 1
+        launches += stages * (2 + (math.ceil(max(grid_it) / 16) + 1 if grid_it else 0) + 1)
+        launches += 4 if args.precision == 1 else (1 if args.precision == 2 else 0)
+        steps_out.append({"ms": ms, "optimal": int((sm["status"] == 1).sum()),
+                          "iter_limit": int((sm["status"] == 2).sum()),
+                          "iters_max": int(sm["iters"].max()), "iters_median": float(np.median(sm["iters"]))})
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed_s, all_it = reduce_elapsed_and_work(total_ms / 1e3, total_it)
+    value = all_it / elapsed_s
+    # roofline of the grid loop kernel (all grid instances running, 16 iterations per launch)
+    hbm_peak, peak_src = load_peaks()
+    ms64, per = b.time_loop(64, fp64=True, stream=sp)
+    roof = {"bound": "hbm", "kernel": "kb_loop<double>", "unit": "GB/s", "peak": hbm_peak,
+            "traffic": None, "iters_per_launch": per, "ms_per_launch": ms64}
+    roof["achieved"] = batch_work(lps, local_nnz, 8) * per / (ms64 * 1e-3) / 1e9
+    roof["frac"] = roof["achieved"] / hbm_peak
+    if args.precision != 0:
+        ms32, _ = b.time_loop(64, fp64=False, stream=sp)
+        roof["fp32"] = {"kernel": "kb_loop<float>", "ms_per_launch": ms32,
+                        "achieved": batch_work(lps, local_nnz, 4) * per / (ms32 * 1e-3) / 1e9}
+        roof["fp32"]["frac"] = roof["fp32"]["achieved"] / hbm_peak
+    roof["peak_source"] = f"HBM {peak_src} copy {hbm_peak} GB/s"
+    b.close()
+    # end to end through the C ABI from host arrays: create (H2D inside) + solve + summary
+    e2e_s, e2e_it = 0.0, 0
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b2 = lpx.BatchSolver(lps, precision=args.precision, switch_tol=args.switch_tol)
+        b2.solve(args.tol, args.max_iter, sp)
+        sm = b2.summary()
+        xs = [b2.get(k)["x"] for k in range(len(lps))]
+        e2e_s += time.perf_counter() - t0
+        e2e_it += int(sm["iters"].sum())
+        b2.close()
+    e2e_s, e2e_it = reduce_elapsed_and_work(e2e_s, e2e_it)
+    h2d = sum(lp.row_ptr.nbytes + 12 * lp.nnz + 8 * (3 * lp.n + 2 * lp.m) for lp in lps)
+    d2h = sum(8 * (lp.m + lp.n) for lp in lps) + len(lps) * (4 + 32 + 16 + 8)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = batch_cpu_baseline(lps, args.tol, args.cpu_seconds)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "instance-iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f64", 1: "f32+f64", 2: "f32"}[args.precision], "data": "synthetic",
+            "config": {"workload": wl, "tol": args.tol, "max_iter": args.max_iter,
+                       "batch_local_nnz": local_nnz, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"independent batches x{world}"},
+            "time_to_tol_s": elapsed_s / args.steps, "setup_ms": setup_ms, "steps_detail": steps_out,
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_it / e2e_s if e2e_s > 0 else None, "unit": "instance-iter/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+                    "includes": "lp_batch_create from host arrays (validation, transposes, tasks, "
+                                "preconditioning, power iterations, H2D) + lp_batch_solve + results to host"},
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

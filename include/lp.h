@@ -101,13 +101,16 @@ typedef struct {
                               the best, the phase stops (precision 1: hands over to FP64 with
                               omega and the PID state of the best check; precision 2: ends with
                               LP_SOLVE_STALLED).  0 disables the guard. */
+  int64_t batch_local_nnz; /* lp_batch_* only: instances with at most this many nonzeros are
+                              solved by one thread block each (block barriers only) instead of
+                              by the grid-wide loop; 0 puts every instance on the grid loop */
 } lp_params;
 
 /* Fills p with the defaults: gamma 1, betas 0.2 / 0.8 / 0.36, K_P 0.5, K_I 0.001, K_D 0,
  * eta 0 (power iteration), omega0 1, check_every 64, restarts and PID on, power_tol 1e-7,
  * power_max_iter 10000, seed 0, Ruiz 10 + Pock-Chambolle alpha 1, no trace, unroll 8,
- * lane_target 8, persistent -1, precision 0, switch_tol 1e-5, fp32_patience 32.  Returns
- * LP_ERR_INVALID_ARG if p is NULL. */
+ * lane_target 8, persistent -1, precision 0, switch_tol 1e-5, fp32_patience 32,
+ * batch_local_nnz 16384.  Returns LP_ERR_INVALID_ARG if p is NULL. */
 LP_API lp_status lp_default_params(lp_params* p);
 
 typedef struct lp_solver* lp_handle;

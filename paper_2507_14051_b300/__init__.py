@@ -35,7 +35,9 @@ LP_HOST, LP_DEVICE = 0, 1
 
 EXPORTED = ("lp_default_params", "lp_create", "lp_set_params", "lp_solve", "lp_get",
             "lp_get_info", "lp_get_trace", "lp_destroy", "lp_last_error", "lp_time_kernels",
-            "lp_debug_spmv", "lp_debug_layout", "lp_power_norm_noalloc")
+            "lp_debug_spmv", "lp_debug_layout", "lp_power_norm_noalloc",
+            "lp_batch_create", "lp_batch_solve", "lp_batch_get", "lp_batch_get_all",
+            "lp_batch_time_loop", "lp_batch_destroy", "lp_tune_lane_target")
 
 
 class lp_params(C.Structure):
@@ -66,6 +68,7 @@ class lp_params(C.Structure):
         ("precision", C.c_int32),
         ("switch_tol", C.c_double),
         ("fp32_patience", C.c_int32),
+        ("batch_local_nnz", C.c_int64),
     ]
 
 
@@ -114,8 +117,18 @@ def load(path: str | None = None) -> C.CDLL:
         L.lp_debug_layout.argtypes = [vp, i32p, i32p, dp, dp]
         L.lp_power_norm_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, C.c_double,
                                             C.c_int64, C.c_uint64, vp, dp, i64p]
+        pp = C.POINTER(C.c_void_p)
+        L.lp_batch_create.argtypes = [C.c_int32, vp, vp, vp, pp, pp, pp, pp, pp, pp, pp, pp, vp, vp,
+                                      C.POINTER(lp_params), C.POINTER(C.c_void_p)]
+        L.lp_tune_lane_target.argtypes = [C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, C.c_char_p, i32p, dp]
+        L.lp_batch_solve.argtypes = [vp, C.c_double, C.c_int64, vp]
+        L.lp_batch_get.argtypes = [vp, C.c_int32, vp, vp, i32p, dp, i64p]
+        L.lp_batch_get_all.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.lp_batch_time_loop.argtypes = [vp, C.c_int64, C.c_int32, vp, dp]
+        L.lp_batch_destroy.argtypes = [vp]
+        L.lp_batch_destroy.restype = None
         for name in EXPORTED:
-            if name not in ("lp_destroy", "lp_last_error"):
+            if name not in ("lp_destroy", "lp_last_error", "lp_batch_destroy"):
                 getattr(L, name).restype = C.c_int32
         _lib = L
         return L
@@ -289,3 +302,100 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class BatchSolver:
+    """Owns one batch handle (include/lp_batch.h) over a list of LPs (objects as for Solver).
+    ``eta``: None (power iteration per instance, or params' eta) or a sequence of per-instance
+    step sizes."""
+
+    def __init__(self, lps, eta=None, lane_target=None, **params):
+        self.count = len(lps)
+        self.shapes = [(int(lp.m), int(lp.n)) for lp in lps]
+        cols = {"row_ptr": np.int64, "col_idx": np.int32, "val": np.float64, "c": np.float64,
+                "l_c": np.float64, "u_c": np.float64, "l_v": np.float64, "u_v": np.float64}
+        keep = {k: [np.ascontiguousarray(getattr(lp, k), dtype=dt) for lp in lps] for k, dt in cols.items()}
+        ptrs = {k: (C.c_void_p * self.count)(*[a.ctypes.data for a in v]) for k, v in keep.items()}
+        m = np.array([s[0] for s in self.shapes], np.int32)
+        n = np.array([s[1] for s in self.shapes], np.int32)
+        nnz = np.array([int(a[-1]) for a in keep["row_ptr"]], np.int64)
+        eta_arr = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
+        lt_arr = None if lane_target is None else np.ascontiguousarray(lane_target, dtype=np.int32)
+        self.params = lp_default_params(**params)
+        h = C.c_void_p()
+        _check(load().lp_batch_create(self.count, m.ctypes.data, n.ctypes.data, nnz.ctypes.data,
+                                      ptrs["row_ptr"], ptrs["col_idx"], ptrs["val"], ptrs["c"],
+                                      ptrs["l_c"], ptrs["u_c"], ptrs["l_v"], ptrs["u_v"],
+                                      None if eta_arr is None else eta_arr.ctypes.data,
+                                      None if lt_arr is None else lt_arr.ctypes.data,
+                                      C.byref(self.params), C.byref(h)), "lp_batch_create")
+        self.h = h.value
+
+    def solve(self, tol=1e-8, max_iter=100000, stream=None):
+        _check(load().lp_batch_solve(self.h, tol, int(max_iter), stream), "lp_batch_solve")
+        return self
+
+    def get(self, k):
+        m, n = self.shapes[k]
+        x, y = np.zeros(n), np.zeros(m)
+        st = C.c_int32(0)
+        kkt = np.zeros(4)
+        it = C.c_int64(0)
+        _check(load().lp_batch_get(self.h, k, x.ctypes.data, y.ctypes.data, C.byref(st),
+                                   kkt.ctypes.data_as(C.POINTER(C.c_double)), C.byref(it)), "lp_batch_get")
+        return dict(x=x, y=y, status=st.value, kkt=kkt, iters=it.value)
+
+    def summary(self):
+        st = np.zeros(self.count, np.int32)
+        kkt = np.zeros((self.count, 4))
+        it = np.zeros(self.count, np.int64)
+        it32 = np.zeros(self.count, np.int64)
+        eta = np.zeros(self.count)
+        _check(load().lp_batch_get_all(self.h, st.ctypes.data, kkt.ctypes.data, it.ctypes.data,
+                                       it32.ctypes.data, eta.ctypes.data), "lp_batch_get_all")
+        return dict(status=st, kkt=kkt, iters=it, iters_fp32=it32, eta=eta)
+
+    def time_loop(self, iters, fp64=True, stream=None):
+        """(ms per launch of the batch loop kernel, iterations per launch)."""
+        out = np.zeros(2)
+        _check(load().lp_batch_time_loop(self.h, int(iters), 1 if fp64 else 0, stream,
+                                         out.ctypes.data_as(C.POINTER(C.c_double))), "lp_batch_time_loop")
+        return float(out[0]), int(out[1])
+
+    def close(self):
+        if self.h:
+            load().lp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def lp_tune_lane_target(lp, cache_path: str | None = None, timings: bool = False):
+    """Fastest tile schedule (lane_target) for lp's matrix, cached per shape class (see
+    include/lp_batch.h).  Returns best, or (best, ms per candidate [2, 4, 8, 16, 32])."""
+    rp = np.ascontiguousarray(lp.row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(lp.col_idx, dtype=np.int32)
+    v = np.ascontiguousarray(lp.val, dtype=np.float64)
+    best = C.c_int32(0)
+    ms = np.zeros(5)
+    _check(load().lp_tune_lane_target(int(lp.m), int(lp.n), int(rp[-1]), rp.ctypes.data, ci.ctypes.data,
+                                      v.ctypes.data, None if cache_path is None else cache_path.encode(),
+                                      C.byref(best), ms.ctypes.data_as(C.POINTER(C.c_double)) if timings else None),
+           "lp_tune_lane_target")
+    return (best.value, ms) if timings else best.value
+
+
+def tune_batch(lps, cache_path: str | None = None):
+    """Per-instance tile schedules for a batch: one tuning run per shape class (the library
+    caches by class), so a batch of many similar instances costs a few timings."""
+    return [lp_tune_lane_target(lp, cache_path) for lp in lps]

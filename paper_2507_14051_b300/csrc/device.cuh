@@ -142,6 +142,17 @@ __device__ __forceinline__ float ld_gather(const float* p, uint64_t pol) {
   return v;
 }
 
+// splitmix64 (Steele, Lea, Flood 2014; public-domain reference code by S. Vigna): output i
+// of the stream started at `seed`; the start vector entry is uniform on [-1, 1) from the top
+// 53 bits.  Entry j' of the permuted vector is the entry of original column col_perm[j'].
+__device__ __forceinline__ double start_entry(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= (z >> 31);
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
 // Partial dot product of one lane: entries b+first, b+first+stride, ... < e, loaded ILP at a
 // time (all loads of a batch issued before any is used) and accumulated in entry order.
 template <int ILP, class V>

@@ -36,293 +36,11 @@
 // per side per iteration suffices.
 #include <cooperative_groups.h>
 
-#include "kernels.cuh"
+#include "step.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace pdhg {
-
-__device__ __forceinline__ bool is_check(const Ctl& c, int64_t t) {
-  return ((t + 1) % c.check_every) == 0 || (t + 1 == c.max_iter);
-}
-
-// Restart test, Section 3: (1) r <= b_s r0; (2) r <= b_n r0 and r > r_prev; (3) k >= b_a T.
-__device__ __forceinline__ int restart_test(const Ctl& c, int64_t k, int64_t t, double r) {
-  if (k < 1) return 0;
-  if (r <= c.beta_s * c.r0) return 1;
-  if (r <= c.beta_n * c.r0 && r > c.r_prev) return 1;
-  if ((double)k >= c.beta_a * (double)(t + 1)) return 1;
-  return 0;
-}
-
-// PID primal weight update, Section 3: e = log(sqrt(w)|dx| / (|dy|/sqrt(w))),
-// log w <- log w - (K_P e + K_I sum e + K_D (e - e_prev)); skipped when a norm is 0 or not
-// finite; log w kept in [-23, 23].
-__device__ __forceinline__ double pid_update(Ctl& c, double omega, double dxn, double dyn) {
-  if (!(dxn > 0.0) || !(dyn > 0.0) || !isfinite(dxn) || !isfinite(dyn)) return omega;
-  const double sw = sqrt(omega);
-  const double e = log((sw * dxn) / (dyn / sw));
-  c.pid_integral += e;
-  const double de = c.pid_has_prev ? e - c.pid_eprev : 0.0;
-  double lw = log(omega) - (c.kp * e + c.ki * c.pid_integral + c.kd * de);
-  lw = fmin(fmax(lw, -23.0), 23.0);
-  c.pid_eprev = e;
-  c.pid_has_prev = 1;
-  return exp(lw);
-}
-
-// FP64 accumulation of a product / value computed in the phase's value type: for FP64 the
-// product is fused into the accumulator, for FP32 the product is rounded to FP32 and added in
-// FP64 (the reductions stay FP64 in both precisions).
-__device__ __forceinline__ void acc_fma(double& a, double p, double q) { a = fma(p, q, a); }
-__device__ __forceinline__ void acc_fma(double& a, float p, float q) { a += (double)(p * q); }
-__device__ __forceinline__ double fmav(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fmav(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double maxv(double a, double b) { return fmax(a, b); }
-__device__ __forceinline__ float maxv(float a, float b) { return fmaxf(a, b); }
-__device__ __forceinline__ double minv(double a, double b) { return fmin(a, b); }
-__device__ __forceinline__ float minv(float a, float b) { return fminf(a, b); }
-
-// ------------------------------------------------------------------ row phase
-
-struct RowStep {
-  int mode;  // 0 Halpern combine, 1 restart, 2 first iteration (state is zero)
-  int check;
-  int cand;  // stall-guard slot written at this check iteration
-  double ha, hb, he, sigma, inv_sigma;
-};
-
-__device__ __forceinline__ RowStep row_step(const Ctl& c) {
-  RowStep st;
-  st.mode = (c.t == 0) ? 2 : c.restart;
-  st.check = is_check(c, c.t) ? 1 : 0;
-  st.cand = c.cand_slot;
-  st.ha = c.ha;
-  st.hb = c.hb;
-  st.he = c.he;
-  st.sigma = c.sigma;
-  st.inv_sigma = c.inv_sigma;
-  return st;
-}
-
-template <class V>
-__device__ __forceinline__ void row_epilogue(const RowArgsT<V>& a, const RowStep& st, int i, V v,
-                                             double (&acc)[kNumSums]) {
-  const V ha = (V)st.ha, hb = (V)st.hb, he = (V)st.he;
-  const V sigma = (V)st.sigma, inv_sigma = (V)st.inv_sigma;
-  V yi, axi, y0i;
-  if (st.mode == 0) {
-    y0i = a.y0[i];
-    yi = fmav(ha, a.yh[i], fmav(hb, a.y[i], he * y0i));
-    axi = fmav(ha, a.axh[i], fmav(hb, a.ax[i], he * a.ax0[i]));
-  } else if (st.mode == 1) {
-    yi = a.yh[i];
-    axi = a.axh[i];
-    y0i = yi;
-    a.y0[i] = yi;
-    a.ax0[i] = axi;
-  } else {
-    yi = V(0);
-    axi = V(0);
-    y0i = V(0);
-  }
-  const V lo = a.lc[i], hi = a.uc[i];
-  const V w = fmav(V(2), v, -axi);  // A(2 xhat - x)
-  const V sv = fmav(-yi, inv_sigma, w);
-  const V yn = sigma * (clampd(sv, lo, hi) - sv);
-  const V dy = yi - yn;
-  acc_fma(acc[0], dy, dy);
-  acc_fma(acc[1], dy, axi - v);
-  const V d0 = yn - y0i;
-  acc_fma(acc[2], d0, d0);
-  if (st.check) {
-    const V pr = (v - clampd(v, lo, hi)) * a.inv_dr[i];
-    acc_fma(acc[3], pr, pr);
-    acc[4] += (double)((yn > V(0) ? lo * yn : V(0)) + (yn < V(0) ? hi * yn : V(0)));
-    if (a.yb0) (st.cand ? a.yb1 : a.yb0)[i] = yn;
-  }
-  if (st.mode != 2) {
-    a.y[i] = yi;
-    a.ax[i] = axi;
-  }
-  a.yh[i] = yn;
-  a.axh[i] = v;
-}
-
-// Scalar control after the row phase of iteration c.t, on totals tot[0..2] (and tot[3..4] on
-// check iterations).  Writes the trace row if `trace` is given.
-__device__ __forceinline__ void row_control(Ctl& c, const double (&tot)[kNumSums], bool check,
-                                            double* trace) {
-  const int64_t t = c.t;
-  const double eta = c.eta, om = c.omega;
-  const double r2 = fma(c.w_over_eta, c.sxx, fma(c.inv_eta_w, tot[0], 2.0 * tot[1]));
-  const double r = sqrt(r2 > 0.0 ? r2 : 0.0);
-  const int64_t k = c.k;
-  if (k == 0) c.r0 = r;
-  if (check) {
-    c.pres2 = tot[3];
-    c.dobj_y = tot[4];
-  }
-  c.omega_used = om;
-  c.restarts_used = c.restarts;
-  const bool tr = trace != nullptr && t < c.trace_cap;
-  if (tr) {
-    trace[4 * t + 0] = r;
-    trace[4 * t + 1] = om;
-    trace[4 * t + 2] = 0.0;
-    trace[4 * t + 3] = (double)k;
-  }
-  if (!isfinite(r2)) {
-    c.status = kNumerical;
-    c.iters = t + 1;
-    c.done = 1;
-    return;
-  }
-  const int rs = c.restart_enabled && (t + 1 < c.max_iter) ? restart_test(c, k, t, r) : 0;
-  if (rs) {
-    double omn = om;
-    if (c.pid_enabled) omn = pid_update(c, om, sqrt(c.sx0), sqrt(tot[2]));
-    c.omega = omn;
-    c.tau = eta / omn;
-    c.sigma = eta * omn;
-    c.inv_sigma = 1.0 / (eta * omn);
-    c.w_over_eta = omn / eta;
-    c.inv_eta_w = 1.0 / (eta * omn);
-    c.k = 0;
-    c.restarts += 1;
-    if (tr) trace[4 * t + 2] = 1.0;
-  } else {
-    const double kk = (double)k;
-    const double aw = (kk + 1.0) / (kk + 2.0);
-    c.ha = aw * (1.0 + c.gamma);
-    c.hb = -aw * c.gamma;
-    c.he = 1.0 / (kk + 2.0);
-    c.r_prev = r;
-    c.k = k + 1;
-  }
-  c.restart = rs;
-}
-
-// --------------------------------------------------------------- column phase
-
-template <class V>
-struct ColStepT {
-  int restart;
-  int check;
-  int cand;
-  double ha, hb, he, tau;
-  const V* xc;  // xhat_t
-  V* xn;        // xhat_{t+1}
-};
-
-template <class V>
-__device__ __forceinline__ ColStepT<V> col_step(const Ctl& c, const ColArgsT<V>& a) {
-  ColStepT<V> st;
-  st.restart = c.restart;
-  st.check = is_check(c, c.t) ? 1 : 0;
-  st.cand = c.cand_slot;
-  st.ha = c.ha;
-  st.hb = c.hb;
-  st.he = c.he;
-  st.tau = c.tau;
-  st.xc = (c.t & 1) ? a.xh1 : a.xh0;
-  st.xn = (c.t & 1) ? a.xh0 : a.xh1;
-  return st;
-}
-
-template <class V>
-__device__ __forceinline__ void col_epilogue(const ColArgsT<V>& a, const ColStepT<V>& st, int j, V u,
-                                             double (&acc)[kNumSums]) {
-  const V ha = (V)st.ha, hb = (V)st.hb, he = (V)st.he, tau = (V)st.tau;
-  const V xc = st.xc[j];
-  V xj, atyj, x0j;
-  if (st.restart) {
-    xj = xc;
-    atyj = u;
-    x0j = xc;
-    a.x0[j] = xc;
-    a.aty0[j] = u;
-  } else {
-    x0j = a.x0[j];
-    xj = fmav(ha, xc, fmav(hb, a.x[j], he * x0j));
-    atyj = fmav(ha, u, fmav(hb, a.aty[j], he * a.aty0[j]));
-  }
-  const V cj = a.c[j], lo = a.lv[j], hi = a.uv[j];
-  const V xn = clampd(fmav(-tau, cj - atyj, xj), lo, hi);
-  const V dx = xj - xn;
-  acc_fma(acc[0], dx, dx);
-  const V d0 = xn - x0j;
-  acc_fma(acc[1], d0, d0);
-  if (st.check) {
-    acc_fma(acc[2], cj, xc);
-    const V rc = cj - u;
-    const bool fl = isfinite(lo), fu = isfinite(hi);
-    const V rr = (fl && fu) ? rc : (fl ? maxv(rc, V(0)) : (fu ? minv(rc, V(0)) : V(0)));
-    const V dd = (rc - rr) * a.inv_dc[j];
-    acc_fma(acc[3], dd, dd);
-    acc[4] += (double)((rr > V(0) ? lo * rr : V(0)) + (rr < V(0) ? hi * rr : V(0)));
-    if (a.xb0) (st.cand ? a.xb1 : a.xb0)[j] = xc;
-  }
-  a.x[j] = xj;
-  a.aty[j] = atyj;
-  st.xn[j] = xn;
-}
-
-// Scalar control after the column phase: carries the x-side sums to the next residual, runs
-// the relative KKT test on check iterations (Section 4), and advances t.
-__device__ __forceinline__ void col_control(Ctl& c, const double (&tot)[kNumSums], bool check) {
-  const int64_t t = c.t;
-  c.sxx = tot[0];
-  c.sx0 = tot[1];
-  if (check) {
-    const double pobj = tot[2], dobj = c.dobj_y + tot[4];
-    const double pres = sqrt(c.pres2), dres = sqrt(tot[3]);
-    const double rg = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
-    const double rp = pres / (1.0 + c.lu_norm);
-    const double rd = dres / (1.0 + c.c_norm);
-    double mx = rg;
-    if (!(rp <= mx)) mx = rp;
-    if (!(rd <= mx)) mx = rd;
-    c.kkt[0] = rg;
-    c.kkt[1] = rp;
-    c.kkt[2] = rd;
-    c.kkt[3] = mx;
-    c.kkt[4] = pobj;
-    c.kkt[5] = dobj;
-    c.kkt[6] = pres;
-    c.kkt[7] = dres;
-    if (rg <= c.tol && rp <= c.tol && rd <= c.tol) {
-      c.status = kOptimal;
-      c.iters = t + 1;
-      c.done = 1;
-      return;
-    }
-    if (c.patience > 0) {  // FP32 phase: stop once its rounding floor stalls or reverses progress
-      if (mx < c.best_kkt) {
-        c.best_kkt = mx;
-        c.since_best = 0;
-        c.omega_best = c.omega;
-        c.integral_best = c.pid_integral;
-        c.eprev_best = c.pid_eprev;
-        for (int q = 0; q < 8; ++q) c.kkt_best[q] = c.kkt[q];
-        c.best_slot = c.cand_slot;  // zhat_t of this check is in that slot; write the other next
-        c.cand_slot ^= 1;
-      } else if (++c.since_best >= c.patience || !(mx <= 100.0 * c.best_kkt)) {
-        c.status = kStalled;
-        c.iters = t + 1;
-        c.done = 1;
-        return;
-      }
-    }
-  }
-  if (t + 1 >= c.max_iter) {
-    c.status = kIterLimit;
-    c.iters = t + 1;
-    c.done = 1;
-    return;
-  }
-  c.t = t + 1;
-}
 
 // ----------------------------------------------------------- one kernel per phase
 
@@ -502,37 +220,9 @@ __global__ void k_to_double(int64_t len, const float* __restrict__ src, double* 
   }
 }
 
-// Hand-over from the FP32 phase to the FP64 refinement phase (a new epoch anchored at the FP32
-// point): the FP64 phase continues the iteration count, omega and the PID state, starts with
-// k = 0 and the restart flag set (so its first row step takes y = yhat, Ax = A xhat as iterate
-// and anchor), gets the final tolerance and max_iter_fp64 further iterations.  After a stall
-// of the FP32 phase, omega and the PID state go back to their values at its best check (past
-// that point the FP32 rounding, not the iterate, drove the PID).  A NUMERICAL end of the FP32
-// phase is kept and ends the solve.
+// Hand-over kernel of the single-instance solve (switch_ctl in step.cuh).
 __global__ void k_switch_ctl(Ctl* ctl, double tol, int64_t max_iter_fp64) {
-  const int64_t it32 = ctl->iters;
-  ctl->iters32 = it32;
-  if (ctl->status == kNumerical) return;
-  if (ctl->status == kStalled && ctl->best_kkt < INFINITY) {
-    const double om = ctl->omega_best, eta = ctl->eta;
-    ctl->omega = om;
-    ctl->tau = eta / om;
-    ctl->sigma = eta * om;
-    ctl->inv_sigma = 1.0 / (eta * om);
-    ctl->w_over_eta = om / eta;
-    ctl->inv_eta_w = 1.0 / (eta * om);
-    ctl->pid_integral = ctl->integral_best;
-    ctl->pid_eprev = ctl->eprev_best;
-  }
-  ctl->patience = 0;
-  ctl->t = it32;
-  ctl->k = 0;
-  ctl->restart = 1;
-  ctl->done = 0;
-  ctl->status = 0;
-  ctl->tol = tol;
-  ctl->max_iter = it32 + max_iter_fp64;
-  ctl->bodies = 0;
+  switch_ctl(*ctl, tol, max_iter_fp64);
 }
 
 // Copies the FP32 phase's returned point to FP64: zhat_T of its last iteration T = iters - 1

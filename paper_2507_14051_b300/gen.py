@@ -95,9 +95,10 @@ def _matvec(row_ptr, col_idx, val, x):
     """s = A x for the generator's own bookkeeping (planting row bounds)."""
     m = len(row_ptr) - 1
     prod = val * x[col_idx]
-    out = np.add.reduceat(prod, row_ptr[:-1]) if len(prod) else np.zeros(m)
-    out = np.asarray(out, dtype=np.float64)
-    out[row_ptr[:-1] == row_ptr[1:]] = 0.0  # reduceat quirk on empty rows
+    out = np.zeros(m)
+    nonempty = row_ptr[:-1] < row_ptr[1:]
+    if len(prod):  # segments start at the non-empty rows only (reduceat needs starts < len)
+        out[nonempty] = np.add.reduceat(prod, row_ptr[:-1][nonempty])
     return out
 
 
@@ -135,9 +136,6 @@ def known_optimum(rng, m, n, row_ptr, col_idx, val, l_v, u_v, *, frac_at_bound=0
     s = _matvec(row_ptr, col_idx, val, x)
     if row_type is None:
         row_type = rng.integers(0, 4, m)
-    y = np.zeros(m)
-    l_c = np.empty(m)
-    u_c = np.empty(m)
     nz = rng.random(m) < y_nonzero
     sign = np.where(rng.random(m) < 0.5, 1.0, -1.0)
     # sign allowed by the row type: '>=' rows only y >= 0, '<=' rows only y <= 0
@@ -145,31 +143,18 @@ def known_optimum(rng, m, n, row_ptr, col_idx, val, l_v, u_v, *, frac_at_bound=0
     mag = rng.uniform(0.1, 1.0, m)
     slack = rng.uniform(0.5, 2.0, (m, 2))
     which = rng.integers(0, 3, m)  # for the free choice of the inactive side
-    for i in range(m):
-        ty = row_type[i]
-        if nz[i]:
-            y[i] = sign[i] * mag[i]
-        if ty == 0:
-            l_c[i] = u_c[i] = s[i]
-        elif ty == 1:
-            u_c[i] = INF
-            l_c[i] = s[i] if y[i] > 0 else s[i] - slack[i, 0]
-        elif ty == 2:
-            l_c[i] = -INF
-            u_c[i] = s[i] if y[i] < 0 else s[i] + slack[i, 1]
-        else:
-            if y[i] > 0:
-                l_c[i], u_c[i] = s[i], s[i] + slack[i, 1]
-            elif y[i] < 0:
-                l_c[i], u_c[i] = s[i] - slack[i, 0], s[i]
-            else:
-                l_c[i], u_c[i] = s[i] - slack[i, 0], s[i] + slack[i, 1]
-        if ty == 0 or ty == 3:
-            # optional widening to infinity on the side that carries no multiplier
-            if which[i] == 2 and y[i] > 0 and ty == 3:
-                u_c[i] = INF
-            if which[i] == 2 and y[i] < 0 and ty == 3:
-                l_c[i] = -INF
+    y = np.where(nz, sign * mag, 0.0)
+    pos, neg = y > 0, y < 0
+    eq, ge, le, rg = row_type == 0, row_type == 1, row_type == 2, row_type == 3
+    # equality: l = u = s;  '>=': u = inf, l = s where y > 0 else s - slack;  '<=': mirrored;
+    # ranged: the side carrying the multiplier is tight, the other at a slack (both slack if y = 0)
+    l_c = np.where(eq, s, np.where(ge, np.where(pos, s, s - slack[:, 0]),
+                   np.where(le, -INF, np.where(neg | (y == 0), s - slack[:, 0], s))))
+    u_c = np.where(eq, s, np.where(ge, INF, np.where(le, np.where(neg, s, s + slack[:, 1]),
+                   np.where(pos | (y == 0), s + slack[:, 1], s))))
+    # ranged rows: optional widening to infinity on the side that carries no multiplier
+    u_c = np.where(rg & (which == 2) & pos, INF, u_c)
+    l_c = np.where(rg & (which == 2) & neg, -INF, l_c)
     c = _rmatvec(row_ptr, col_idx, val, y, n) + r
     return LP(m, n, row_ptr, col_idx, val, c, l_c, u_c, l_v.copy(), u_v.copy(), x, y, r, name)
 
@@ -301,3 +286,50 @@ def ragged_rows(seed: int, m: int, n: int) -> LP:
     lv = np.zeros(n)
     uv = np.where(rng.random(n) < 0.5, INF, rng.uniform(1.0, 3.0, n))
     return known_optimum(rng, m, n, rp, ci, v, lv, uv, name=f"ragged_{m}x{n}_s{seed}")
+
+
+def bernoulli_csr(rng: np.random.Generator, m: int, n: int, density: float):
+    """Bernoulli(density) sparsity over the m x n grid, N(0,1) values, sampled by geometric gaps
+    between selected positions in row-major order (exact Bernoulli sampling without drawing
+    one uniform per grid cell; columns come out sorted in each row)."""
+    total = m * n
+    if total == 0 or density <= 0.0:
+        return np.zeros(m + 1, np.int64), np.zeros(0, np.int32), np.zeros(0)
+    parts, cur = [], -1
+    while True:
+        k = int(total * density * 1.02) + 64
+        pos = cur + np.cumsum(rng.geometric(density, size=k))
+        parts.append(pos[pos < total])
+        if pos[-1] >= total:
+            break
+        cur = int(pos[-1])
+    pos = np.concatenate(parts)
+    rows = pos // n
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=m), out=row_ptr[1:])
+    col_idx = (pos - rows * n).astype(np.int32)
+    val = rng.standard_normal(len(pos))
+    return row_ptr, col_idx, val
+
+
+def batch_sizes(seed: int, count: int = 512, m_min: int = 100, m_max: int = 20_000) -> np.ndarray:
+    """Row counts of the uneven batch: m = floor(exp(U(ln m_min, ln m_max)))."""
+    rng = np.random.default_rng(seed)
+    return np.floor(np.exp(rng.uniform(np.log(m_min), np.log(m_max), count))).astype(np.int64)
+
+
+def batch_uneven(seed: int, count: int = 512, m_min: int = 100, m_max: int = 20_000,
+                 density: float = 0.01) -> list[LP]:
+    """Batch of independent LPs of uneven size: m log-uniform in [m_min, m_max], n = 2m,
+    Bernoulli(density) N(0,1) matrices, box [0, 1] on every variable, planted optima.
+    Instance k draws from its own stream (seed, k), so a prefix of the batch does not depend
+    on `count`."""
+    ms = batch_sizes(seed, count, m_min, m_max)
+    out = []
+    for k, m in enumerate(ms.tolist()):
+        rng = np.random.default_rng([seed, k])
+        n = 2 * m
+        rp, ci, v = bernoulli_csr(rng, m, n, density)
+        out.append(known_optimum(rng, m, n, rp, ci, v, np.zeros(n), np.ones(n),
+                                 frac_at_bound=0.4, y_nonzero=0.5, name=f"batch{seed}_{k}_{m}x{n}"))
+    return out

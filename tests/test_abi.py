@@ -2,6 +2,7 @@
 point include/lp.h declares, the Python mirror of lp_params matches the C layout, and input
 validation rejects bad problems before any CUDA call."""
 import ctypes as C
+import glob
 import math
 import os
 import re
@@ -14,13 +15,15 @@ import paper_2507_14051_b300 as lpx
 from paper_2507_14051_b300 import gen
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "lp.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_entry_points():
-    with open(HEADER) as f:
-        text = f.read()
-    return re.findall(r"LP_API\s+[\w\s\*]+?\b(lp_\w+)\s*\(", text)
+    names = []
+    for h in HEADERS:
+        with open(h) as f:
+            names += re.findall(r"LP_API\s+[\w\s\*]+?\b(lp_\w+)\s*\(", f.read())
+    return names
 
 
 def test_header_declares_the_boundary():
@@ -132,3 +135,68 @@ def test_valid_create_without_gpu_fails_loudly():
     with pytest.raises(lpx.LPError) as e:
         _create(gen.small_lp(0))
     assert e.value.code in (lpx.LP_ERR_CUDA, lpx.LP_ERR_OUT_OF_MEMORY)
+
+
+# ------------------------------------------------------------------------- batch (lp_batch.h)
+
+def _batch(seed=0, count=3):
+    return gen.batch_uneven(seed, count=count, m_min=20, m_max=60, density=0.05)
+
+
+@pytest.mark.parametrize("case", sorted(BAD_INPUTS))
+def test_batch_create_rejects_invalid_instance(case):
+    import copy
+    lps = [copy.deepcopy(lp) for lp in _batch()]
+    bad = lps[2]
+    arrs = _arrays(bad)
+    BAD_INPUTS[case](arrs)
+    for k, a in zip(("row_ptr", "col_idx", "val", "c", "l_c", "u_c", "l_v", "u_v"), arrs):
+        setattr(bad, k, a)
+    with pytest.raises(lpx.LPError) as e:
+        lpx.BatchSolver(lps)
+    assert e.value.code == lpx.LP_ERR_INVALID_INPUT
+    assert "instance 2" in lpx.lp_last_error()
+
+
+def test_batch_create_rejects_invalid_arguments():
+    lps = _batch()
+    with pytest.raises(lpx.LPError) as e:
+        lpx.BatchSolver(lps, eta=[0.1, -1.0, 0.1])
+    assert e.value.code == lpx.LP_ERR_INVALID_ARG
+    with pytest.raises(lpx.LPError) as e:
+        lpx.BatchSolver(lps, gamma=2.0)
+    assert e.value.code == lpx.LP_ERR_INVALID_ARG
+    L = lpx.load()
+    h = C.c_void_p()
+    assert L.lp_batch_create(0, None, None, None, None, None, None, None, None, None, None, None, None,
+                             None, None, C.byref(h)) == lpx.LP_ERR_INVALID_ARG
+    with pytest.raises(lpx.LPError) as e:
+        lpx.BatchSolver(lps, lane_target=[8, 0, 8])
+    assert e.value.code == lpx.LP_ERR_INVALID_ARG
+    assert L.lp_batch_solve(None, 1e-8, 10, None) == lpx.LP_ERR_INVALID_ARG
+    assert L.lp_batch_get(None, 0, None, None, None, None, None) == lpx.LP_ERR_INVALID_ARG
+    assert L.lp_batch_get_all(None, None, None, None, None, None) == lpx.LP_ERR_INVALID_ARG
+    L.lp_batch_destroy(None)
+
+
+def test_batch_valid_create_without_gpu_fails_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lpx.LPError) as e:
+        lpx.BatchSolver(_batch())
+    assert e.value.code in (lpx.LP_ERR_CUDA, lpx.LP_ERR_OUT_OF_MEMORY)
+
+
+def test_tune_rejects_invalid_input_before_any_cuda_call():
+    lp = gen.small_lp(0)
+    bad = lp.col_idx.copy()
+    bad[0] = lp.n + 5
+    L = lpx.load()
+    best = C.c_int32(0)
+    rp = np.ascontiguousarray(lp.row_ptr, np.int64)
+    v = np.ascontiguousarray(lp.val)
+    assert L.lp_tune_lane_target(lp.m, lp.n, lp.nnz, rp.ctypes.data, bad.ctypes.data, v.ctypes.data, None,
+                                 C.byref(best), None) == lpx.LP_ERR_INVALID_INPUT
+    assert L.lp_tune_lane_target(lp.m, lp.n, lp.nnz, rp.ctypes.data, bad.ctypes.data, v.ctypes.data, None,
+                                 None, None) == lpx.LP_ERR_INVALID_ARG
