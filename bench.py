@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="miplib", choices=["miplib", "mcf", "small", "batch"])
+    ap.add_argument("--workload", default="miplib", choices=["miplib", "mcf", "small", "batch", "diff"])
+    ap.add_argument("--unroll", type=int, default=2000, help="diff workload: unrolled iterations K")
     ap.add_argument("--batch-count", type=int, default=512, help="instances of the batch workload")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--max-iter", type=int, default=100000)
@@ -560,12 +561,136 @@ def run_batch(args):
     return 0
 
 
+def diff_work(lps, K, C):
+    """Algorithmic bytes of one forward + backward pass of the unrolled layer (FP64 values, 32-bit
+    indices): forward K iterations of two SpMVs (12 nnz + 4 (rows+1) + 8 gathered entries per
+    row side) and the elementwise passes (column: 8 x 9 n, row: 8 x 8 m); backward recomputes
+    the forward once more (from the checkpoints) and runs K adjoint iterations of the same size
+    plus one add pass (8 x 3 m).  Clamp codes: 1 byte per entry per iteration, written and read."""
+    tot = 0
+    for lp in lps:
+        m, n, z = lp.m, lp.n, lp.nnz
+        spmv = (12 * z + 4 * (n + 1) + 8 * m) + (12 * z + 4 * (m + 1) + 8 * n)
+        fwd = spmv + 8 * 9 * n + 8 * 8 * m
+        bwd = spmv + 8 * 11 * n + 8 * 8 * m + 8 * 3 * m + 2 * (m + n)
+        tot += K * (2 * fwd + bwd)
+    return tot
+
+
+def run_diff(args):
+    """Differentiable layer workload: 64 LPs (m = 1000, n = 2000, 1 % density); one step = the
+    unrolled forward (K iterations, checkpoints every 100) and the reverse pass of
+    L = |x - x_target|^2 through the autograd layer."""
+    import torch
+    import paper_2507_14051_b300 as lpx
+    from paper_2507_14051_b300 import gen
+    from paper_2507_14051_b300.diff import UnrolledLPBatch
+    from paper_2507_14051_b300.dist import reduce_elapsed_and_work
+
+    rank, local, world = _env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    count = 64
+    lps = [gen.small_lp(1000 * rank + k, m=1000, n=2000, density=0.01) for k in range(count)]
+    K, C = args.unroll, 100
+    wl = f"{count} LPs m=1000 n=2000 1 % density N(0,1) box [0,1] (planted optima), K={K} unrolled steps, checkpoints every {C}"
+    t0 = time.perf_counter()
+    layer = UnrolledLPBatch(lps, K=K, checkpoint_every=C)
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    dev = torch.device("cuda")
+    cat = lambda name: torch.tensor(np.concatenate([getattr(lp, name) for lp in lps]), device=dev)
+    base = {k: cat(k) for k in ("c", "l_c", "u_c", "l_v", "u_v")}
+    xt = torch.rand(base["c"].shape[0], dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(rank))
+
+    def step(host=None):
+        vals = base if host is None else {k: torch.from_numpy(v).to(dev, non_blocking=True) for k, v in host.items()}
+        c = vals["c"].clone().requires_grad_(True)
+        lc = vals["l_c"].clone().requires_grad_(True)
+        uc = vals["u_c"].clone().requires_grad_(True)
+        x, y = layer(c, lc, uc, vals["l_v"], vals["u_v"])
+        L = ((x - xt) ** 2).sum()
+        L.backward()
+        return L, c.grad, lc.grad, uc.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    e1.synchronize()
+    clocks = sampler.stop()
+    elapsed_s, steps = reduce_elapsed_and_work(e0.elapsed_time(e1) / 1e3, args.steps)
+    value = steps / elapsed_s
+    hbm_peak, peak_src = load_peaks()
+    bytes_step = diff_work(lps, K, C)
+    achieved = bytes_step / (elapsed_s / args.steps) / 1e9
+    # end to end: objective and bounds from pinned host memory, loss and gradients back to host
+    host = {k: v.cpu().numpy() for k, v in base.items()}
+    pinned = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in host.items()}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        L, gc, glc, guc = step(pinned)
+        out = (float(L.detach()), gc.cpu(), glc.cpu(), guc.cpu())
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(v.nbytes for v in host.values())
+    d2h = 8 + 8 * (base["c"].shape[0] + 2 * base["l_c"].shape[0])
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle's unrolled map (forward only) on instance 0, extrapolated to the batch
+        from oracle import diff as od
+        ks = 200
+        t0 = time.perf_counter()
+        tr, eta = od.schedule(lps[0], ks)
+        od.unrolled(lps[0], tr, eta, ks)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / (dt * (K / ks) * count), "unit": "forward steps/s (no backward)", "cores": 1,
+               "kind": "oracle",
+               "sample": f"oracle solve + unrolled map, {ks} iterations of instance 0 ({dt:.1f} s), "
+                         f"scaled to {count} instances x {K} iterations"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "forward+backward steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl, "loss": "|x - x_target|^2", "grads": "c, l_c, u_c",
+                       "l2": "working set 61 MB fits L2; not flushed (it is re-read every unrolled step)",
+                       "parallelism": f"independent batches x{world}"},
+            "unrolled_iters_per_s": value * K, "setup_ms": setup_ms,
+            "roofline": {"bound": "hbm", "kernel": "whole step (forward, recompute, adjoint)", "unit": "GB/s",
+                         "achieved": achieved, "peak": hbm_peak, "frac": achieved / hbm_peak, "traffic": None,
+                         "alg_bytes_per_step": bytes_step, "peak_source": f"HBM {peak_src} copy {hbm_peak} GB/s"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": args.e2e_steps / e2e_s, "unit": "forward+backward steps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+            "gpu_launches": args.steps * (2 + 2 * 5 * K + 5 * K + 10), "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    layer.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "diff":
+        return run_diff(args)
     return run_ours(args)
 
 

@@ -37,7 +37,8 @@ EXPORTED = ("lp_default_params", "lp_create", "lp_set_params", "lp_solve", "lp_g
             "lp_get_info", "lp_get_trace", "lp_destroy", "lp_last_error", "lp_time_kernels",
             "lp_debug_spmv", "lp_debug_layout", "lp_power_norm_noalloc",
             "lp_batch_create", "lp_batch_solve", "lp_batch_get", "lp_batch_get_all",
-            "lp_batch_time_loop", "lp_batch_destroy", "lp_tune_lane_target")
+            "lp_batch_time_loop", "lp_batch_destroy", "lp_tune_lane_target",
+            "lp_batch_set_data", "lp_batch_unroll", "lp_batch_unroll_vjp", "lp_batch_get_trace")
 
 
 class lp_params(C.Structure):
@@ -121,6 +122,10 @@ def load(path: str | None = None) -> C.CDLL:
         L.lp_batch_create.argtypes = [C.c_int32, vp, vp, vp, pp, pp, pp, pp, pp, pp, pp, pp, vp, vp,
                                       C.POINTER(lp_params), C.POINTER(C.c_void_p)]
         L.lp_tune_lane_target.argtypes = [C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, C.c_char_p, i32p, dp]
+        L.lp_batch_set_data.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int32]
+        L.lp_batch_unroll.argtypes = [vp, C.c_int64, C.c_int64, vp, vp, vp]
+        L.lp_batch_unroll_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.lp_batch_get_trace.argtypes = [vp, C.c_int32, dp, C.c_int64, i64p]
         L.lp_batch_solve.argtypes = [vp, C.c_double, C.c_int64, vp]
         L.lp_batch_get.argtypes = [vp, C.c_int32, vp, vp, i32p, dp, i64p]
         L.lp_batch_get_all.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -354,6 +359,33 @@ class BatchSolver:
         _check(load().lp_batch_get_all(self.h, st.ctypes.data, kkt.ctypes.data, it.ctypes.data,
                                        it32.ctypes.data, eta.ctypes.data), "lp_batch_get_all")
         return dict(status=st, kkt=kkt, iters=it, iters_fp32=it32, eta=eta)
+
+    def set_data(self, c=None, l_c=None, u_c=None, l_v=None, u_v=None):
+        """Replaces objectives / bounds (concatenated over instances, original order): numpy
+        arrays (host) or torch CUDA float64 tensors (device), all of one kind."""
+        arrs = [a for a in (c, l_c, u_c, l_v, u_v) if a is not None]
+        where = LP_HOST if all(isinstance(a, np.ndarray) for a in arrs) else LP_DEVICE
+        conv = (lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)) if where == LP_HOST \
+            else (lambda a: a)
+        keep = [conv(a) for a in (c, l_c, u_c, l_v, u_v)]
+        _check(load().lp_batch_set_data(self.h, *[_ptr(a) for a in keep], where), "lp_batch_set_data")
+
+    def unroll(self, K, checkpoint_every, x=None, y=None, stream=None):
+        """Forward of the differentiable unrolled solve; x, y: device float64 outputs or None."""
+        _check(load().lp_batch_unroll(self.h, int(K), int(checkpoint_every), _ptr(x), _ptr(y), stream),
+               "lp_batch_unroll")
+
+    def unroll_vjp(self, dl_dx=None, dl_dy=None, dl_dc=None, dl_dlc=None, dl_duc=None, dl_dlv=None,
+                   dl_duv=None, stream=None):
+        _check(load().lp_batch_unroll_vjp(self.h, _ptr(dl_dx), _ptr(dl_dy), _ptr(dl_dc), _ptr(dl_dlc),
+                                          _ptr(dl_duc), _ptr(dl_dlv), _ptr(dl_duv), stream), "lp_batch_unroll_vjp")
+
+    def trace(self, k, cap):
+        out = np.zeros((max(int(cap), 1), 4))
+        rows = C.c_int64(0)
+        _check(load().lp_batch_get_trace(self.h, k, out.ctypes.data_as(C.POINTER(C.c_double)), int(cap),
+                                         C.byref(rows)), "lp_batch_get_trace")
+        return out[: rows.value]
 
     def time_loop(self, iters, fp64=True, stream=None):
         """(ms per launch of the batch loop kernel, iterations per launch)."""

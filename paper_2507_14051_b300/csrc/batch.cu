@@ -38,73 +38,11 @@
 #include <thread>
 #include <vector>
 
-#include "host_util.h"
-#include "lp_batch.h"
-#include "step.cuh"
+#include "batch.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace pdhg {
-
-constexpr int kBatchUnroll = 16;  // iterations per launch of the batch loop kernel
-constexpr int kMaxInst = LP_BATCH_MAX_INSTANCES;
-
-// Place of one instance in the concatenated arrays.
-struct BInst {
-  int32_t row0, m, col0, n;
-  int32_t ta0, nta;  // its tasks in the row-task list (A)
-  int32_t tt0, ntt;  // its tasks in the column-task list (A^T)
-  int32_t local;     // 1: solved by one block (kb_block_loop), not by the grid loop
-  int32_t pad;
-};
-
-// Step of the coming row phase of one instance (written by the previous column control).
-struct BRow {
-  RowStep st;
-  int32_t par;  // t & 1: which xhat buffer holds xhat_t
-};
-
-// Step of the coming column phase of one instance (written by the row control).
-struct BCol {
-  int32_t restart, check, cand, par;
-  double ha, hb, he, tau;
-};
-
-// Batch-wide state of a stage.
-struct BatchCtl {
-  unsigned int n_done;   // instances finished in this stage
-  int32_t overrun;       // the loop outran max_iter (internal error)
-  int64_t bodies, max_bodies;
-  unsigned int pw_left;  // power iteration: instances not converged yet
-};
-
-// Power iteration state of one instance.
-struct BPw {
-  double lam, prev, s;
-  int32_t done, iters;
-};
-
-template <class V>
-struct BatchArgs {
-  RowArgsT<V> ra;  // concatenated row-side vectors and A (bins unused)
-  ColArgsT<V> ca;  // concatenated column-side vectors and A^T (bins unused)
-  const int4* tasksA;
-  const int4* tasksT;
-  const BInst* inst;
-  int32_t count;
-  Ctl* ctl;
-  BRow* rstep;
-  BCol* cstep;
-  int32_t* done;
-  double* tpartA;
-  double* tpartT;
-  BatchCtl* bc;
-};
-
-// Task descriptor: x = first (global) row, y = rows in the tile, z = (G << 24) | entries per
-// lane, w = instance.
-__device__ __forceinline__ int task_lanes(const int4& t) { return t.z >> 24; }
-__device__ __forceinline__ int task_per_lane(const int4& t) { return t.z & 0xFFFFFF; }
 
 // Largest k < nact with pref[k] <= j (pref non-decreasing, pref[0] = 0 <= j).
 __device__ __forceinline__ int find_act(const int32_t* pref, int nact, int j) {
@@ -333,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 3) kb_loop(BatchArgs<V> a, int32_t i
       ctl_load(&sc, a.ctl + ii);
       __syncthreads();
       if (threadIdx.x == 0) {
-        row_control(sc, tot, check != 0, nullptr);
+        row_control(sc, tot, check != 0, trace_of(a, ii));
         a.cstep[ii] = make_bcol(sc);
         if (sc.done) {
           a.done[ii] = 1;
@@ -391,12 +329,14 @@ __global__ void __launch_bounds__(kThreads, 3) kb_loop(BatchArgs<V> a, int32_t i
 // Block-local instances are marked done for the grid loop (n_local of them).
 __global__ void kb_init_ctl(int32_t count, const Ctl* __restrict__ init, const BInst* __restrict__ inst,
                             Ctl* ctl, int32_t* done, BRow* rstep, BatchCtl* bc, double tol,
-                            int64_t max_iter, int32_t patience, int64_t max_bodies, int32_t n_local) {
+                            int64_t max_iter, int32_t patience, int64_t max_bodies, int32_t n_local,
+                            int64_t trace_cap) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
     Ctl c = init[k];
     c.tol = tol;
     c.max_iter = max_iter;
     c.patience = patience;
+    c.trace_cap = trace_cap;
     c.best_kkt = INFINITY;
     c.cand_slot = 0;
     c.best_slot = -1;
@@ -443,22 +383,6 @@ __global__ void __launch_bounds__(kThreads) kb_init(BatchArgs<V> a) {
       a.ctl[k].sx0 = s[0];
     }
     __syncthreads();
-  }
-}
-
-// y = A x over a task list (no epilogue): hand-over products and the power iteration.
-template <class V>
-__global__ void __launch_bounds__(kThreads) kb_spmv(const int4* __restrict__ tasks, int32_t ntasks,
-                                                    const int32_t* __restrict__ rp,
-                                                    const int32_t* __restrict__ ci,
-                                                    const V* __restrict__ val, const V* __restrict__ x,
-                                                    V* __restrict__ y) {
-  const LoadPolicy pol = make_policy();
-  const int lane = threadIdx.x & 31;
-  for (int j = blockIdx.x * kWarps + (threadIdx.x >> 5); j < ntasks; j += gridDim.x * kWarps) {
-    const int4 td = tasks[j];
-    const V v = tile_spmv(rp, ci, val, x, td.x, td.y, task_lanes(td), task_per_lane(td), lane, pol);
-    if (lane < td.y) y[td.x + lane] = v;
   }
 }
 
@@ -575,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 2) kb_block_loop(BatchArgs<V> a, con
       }
       const int nr = st.check ? 5 : 3;
       block_reduce(s, nr);
-      if (threadIdx.x == 0) row_control(sc, s, st.check != 0, nullptr);
+      if (threadIdx.x == 0) row_control(sc, s, st.check != 0, trace_of(a, ii));
       __syncthreads();
       if (sc.done) break;
       if (threadIdx.x == 0) cst = col_step(sc, a.ca);
@@ -689,70 +613,6 @@ using namespace pdhg_host;
 
 // ====================================================================== host side
 
-struct lp_batch {
-  int device = 0, num_sms = 0;
-  int32_t count = 0;
-  lp_params prm{};
-  int64_t sum_m = 0, sum_n = 0, sum_nnz = 0;
-  int32_t ntA = 0, ntT = 0;
-  std::vector<BInst> inst;
-  std::vector<double> eta;
-  int32_t n_local = 0;
-  int32_t* local_list = nullptr;  // device: the block-local instances
-  int grid = 1, gridS = 1;
-  bool solved = false;
-  cudaStream_t last_stream = nullptr;
-  cudaStream_t setup_stream = nullptr;
-
-  // device
-  int32_t *rpA = nullptr, *ciA = nullptr, *rpT = nullptr, *ciT = nullptr;
-  double *valA = nullptr, *valT = nullptr;
-  int32_t *row_perm = nullptr, *col_perm = nullptr;  // per instance, local original index
-  double *c = nullptr, *lv = nullptr, *uv = nullptr, *inv_dc = nullptr, *dc = nullptr;
-  double *x = nullptr, *x0 = nullptr, *xh0 = nullptr, *xh1 = nullptr, *aty = nullptr, *aty0 = nullptr;
-  double *lc = nullptr, *uc = nullptr, *inv_dr = nullptr, *dr = nullptr;
-  double *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
-  double* out_buf = nullptr;
-  struct F32 {
-    float *valA = nullptr, *valT = nullptr;
-    float *c = nullptr, *lv = nullptr, *uv = nullptr, *inv_dc = nullptr;
-    float *x = nullptr, *x0 = nullptr, *xh0 = nullptr, *xh1 = nullptr, *aty = nullptr, *aty0 = nullptr;
-    float *lc = nullptr, *uc = nullptr, *inv_dr = nullptr;
-    float *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
-    float *xb0 = nullptr, *xb1 = nullptr, *yb0 = nullptr, *yb1 = nullptr;
-  } f32;
-  int4 *tasksA = nullptr, *tasksT = nullptr;
-  BInst* d_inst = nullptr;
-  Ctl *ctl = nullptr, *ctl_init = nullptr;
-  BRow* rstep = nullptr;
-  BCol* cstep = nullptr;
-  int32_t* done = nullptr;
-  double *tpartA = nullptr, *tpartT = nullptr;
-  BatchCtl* bc = nullptr;
-  BPw* pw = nullptr;
-  cudaGraph_t graph64 = nullptr, graph32 = nullptr;
-  cudaGraphExec_t exec64 = nullptr, exec32 = nullptr;
-
-  std::vector<void*> allocations;
-  template <class T>
-  cudaError_t alloc(T** p, size_t count_) {
-    void* v = nullptr;
-    cudaError_t e = cudaMalloc(&v, (count_ > 0 ? count_ : 1) * sizeof(T));
-    if (e == cudaSuccess) allocations.push_back(v);
-    *p = static_cast<T*>(v);
-    return e;
-  }
-  ~lp_batch() {
-    if (last_stream) cudaStreamSynchronize(last_stream);
-    if (exec64) cudaGraphExecDestroy(exec64);
-    if (graph64) cudaGraphDestroy(graph64);
-    if (exec32) cudaGraphExecDestroy(exec32);
-    if (graph32) cudaGraphDestroy(graph32);
-    for (void* p : allocations) cudaFree(p);
-    if (setup_stream) cudaStreamDestroy(setup_stream);
-  }
-};
-
 namespace {
 
 // Tiles of rows already sorted by decreasing length class (the single-instance schedule without
@@ -788,44 +648,6 @@ struct Built {
   std::vector<int4> tA, tT;
   double c_norm = 0.0, lu_norm = 0.0;
 };
-
-template <class V>
-void fill_batch_args(const lp_batch* h, BatchArgs<V>& a);
-
-template <>
-void fill_batch_args<double>(const lp_batch* h, BatchArgs<double>& a) {
-  a = BatchArgs<double>{};
-  a.ra.rp = h->rpA; a.ra.ci = h->ciA; a.ra.val = h->valA;
-  a.ra.xh0 = h->xh0; a.ra.xh1 = h->xh1;
-  a.ra.y = h->y; a.ra.y0 = h->y0; a.ra.yh = h->yh; a.ra.ax = h->ax; a.ra.ax0 = h->ax0; a.ra.axh = h->axh;
-  a.ra.lc = h->lc; a.ra.uc = h->uc; a.ra.inv_dr = h->inv_dr;
-  a.ca.rp = h->rpT; a.ca.ci = h->ciT; a.ca.val = h->valT; a.ca.yh = h->yh;
-  a.ca.xh0 = h->xh0; a.ca.xh1 = h->xh1;
-  a.ca.x = h->x; a.ca.x0 = h->x0; a.ca.aty = h->aty; a.ca.aty0 = h->aty0;
-  a.ca.c = h->c; a.ca.lv = h->lv; a.ca.uv = h->uv; a.ca.inv_dc = h->inv_dc;
-  a.tasksA = h->tasksA; a.tasksT = h->tasksT; a.inst = h->d_inst; a.count = h->count;
-  a.ctl = h->ctl; a.rstep = h->rstep; a.cstep = h->cstep; a.done = h->done;
-  a.tpartA = h->tpartA; a.tpartT = h->tpartT; a.bc = h->bc;
-}
-
-template <>
-void fill_batch_args<float>(const lp_batch* h, BatchArgs<float>& a) {
-  const auto& f = h->f32;
-  a = BatchArgs<float>{};
-  a.ra.rp = h->rpA; a.ra.ci = h->ciA; a.ra.val = f.valA;
-  a.ra.xh0 = f.xh0; a.ra.xh1 = f.xh1;
-  a.ra.y = f.y; a.ra.y0 = f.y0; a.ra.yh = f.yh; a.ra.ax = f.ax; a.ra.ax0 = f.ax0; a.ra.axh = f.axh;
-  a.ra.lc = f.lc; a.ra.uc = f.uc; a.ra.inv_dr = f.inv_dr;
-  a.ra.yb0 = f.yb0; a.ra.yb1 = f.yb1;
-  a.ca.rp = h->rpT; a.ca.ci = h->ciT; a.ca.val = f.valT; a.ca.yh = f.yh;
-  a.ca.xh0 = f.xh0; a.ca.xh1 = f.xh1;
-  a.ca.x = f.x; a.ca.x0 = f.x0; a.ca.aty = f.aty; a.ca.aty0 = f.aty0;
-  a.ca.c = f.c; a.ca.lv = f.lv; a.ca.uv = f.uv; a.ca.inv_dc = f.inv_dc;
-  a.ca.xb0 = f.xb0; a.ca.xb1 = f.xb1;
-  a.tasksA = h->tasksA; a.tasksT = h->tasksT; a.inst = h->d_inst; a.count = h->count;
-  a.ctl = h->ctl; a.rstep = h->rstep; a.cstep = h->cstep; a.done = h->done;
-  a.tpartA = h->tpartA; a.tpartT = h->tpartT; a.bc = h->bc;
-}
 
 template <class V>
 cudaError_t launch_batch_loop(const lp_batch* h, const BatchArgs<V>& a, int32_t iters,
@@ -1227,7 +1049,7 @@ template <class V>
 lp_status enqueue_batch_start(lp_batch* h, double tol, int64_t max_iter, int32_t patience, cudaStream_t s) {
   const int g = grid_for(h->count, 256, 4 * h->num_sms);
   kb_init_ctl<<<g, 256, 0, s>>>(h->count, h->ctl_init, h->d_inst, h->ctl, h->done, h->rstep, h->bc, tol,
-                                max_iter, patience, bodies_for(max_iter), h->n_local);
+                                max_iter, patience, bodies_for(max_iter), h->n_local, 0);
   BatchArgs<V> a;
   fill_batch_args<V>(h, a);
   kb_init<V><<<h->gridS, kThreads, 0, s>>>(a);
@@ -1253,6 +1075,41 @@ lp_status enqueue_stage(lp_batch* h, cudaGraphExec_t exec, int64_t max_iter, cud
 lp_batch* checked(lp_batch_handle h) { return h; }
 
 }  // namespace
+
+// Differentiation support: a solve of exactly K FP64 iterations (tolerance 0) of every
+// instance that records each instance's trace rows (r, omega, restart flag, k): the frozen
+// schedule of the unrolled map.
+lp_status batch_schedule_solve(lp_batch* h, int64_t K, cudaStream_t s) {
+  if (h->trace_cap < K) {
+    cudaFree(h->trace);
+    h->trace = nullptr;
+    h->trace_cap = 0;
+    CK(cudaMalloc(&h->trace, sizeof(double) * 4 * (size_t)K * (size_t)h->count));
+    h->trace_cap = K;
+  }
+  const int g = grid_for(h->count, 256, 4 * h->num_sms);
+  kb_init_ctl<<<g, 256, 0, s>>>(h->count, h->ctl_init, h->d_inst, h->ctl, h->done, h->rstep, h->bc, 0.0, K, 0,
+                                bodies_for(K), h->n_local, h->trace_cap);
+  BatchArgs<double> a;
+  fill_batch_args<double>(h, a);
+  a.trace = h->trace;
+  a.trace_cap = h->trace_cap;
+  kb_init<double><<<h->gridS, kThreads, 0, s>>>(a);
+  CK(cudaGetLastError());
+  if (h->n_local < h->count) {
+    const int64_t launches = (K + kBatchUnroll - 1) / kBatchUnroll;
+    for (int64_t q = 0; q < launches; ++q)
+      CK(launch_batch_loop<double>(h, a, kBatchUnroll, cudaGraphConditionalHandle{}, 0, s));
+  }
+  if (h->n_local > 0) {
+    const int gl = std::min(h->n_local, 8 * h->num_sms);
+    kb_block_loop<double><<<gl, kThreads, 0, s>>>(a, h->local_list, h->n_local, K + 2);
+    CK(cudaGetLastError());
+  }
+  h->solved = true;
+  h->last_stream = s;
+  return LP_OK;
+}
 
 
 // ------------------------------------------------------------------ schedule tuner
@@ -1630,6 +1487,26 @@ lp_status lp_batch_time_loop(lp_batch_handle hh, int64_t iters, int32_t precisio
   ms_out[1] = (double)kBatchUnroll;
   h->solved = true;
   h->last_stream = s;
+  return LP_OK;
+}
+
+lp_status lp_batch_get_trace(lp_batch_handle hh, int32_t k, double* out, int64_t cap, int64_t* rows) {
+  pdhg_set_last_error(std::string());
+  lp_batch* h = checked(hh);
+  if (!h || !rows || (cap > 0 && !out)) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  if (k < 0 || k >= h->count) return fail(LP_ERR_INVALID_ARG, "instance index out of range");
+  if (!h->trace) return fail(LP_ERR_NOT_SOLVED, "no traced run (lp_batch_unroll) yet");
+  CK(cudaSetDevice(h->device));
+  CK(cudaStreamSynchronize(h->last_stream));
+  Ctl c;
+  CK(cudaMemcpy(&c, h->ctl + k, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  int64_t r = std::min<int64_t>(c.iters, h->trace_cap);
+  if (r > cap) r = cap;
+  if (r < 0) r = 0;
+  if (r > 0)
+    CK(cudaMemcpy(out, h->trace + (size_t)k * (size_t)h->trace_cap * 4, sizeof(double) * 4 * (size_t)r,
+                  cudaMemcpyDeviceToHost));
+  *rows = r;
   return LP_OK;
 }
 

@@ -333,3 +333,33 @@ def batch_uneven(seed: int, count: int = 512, m_min: int = 100, m_max: int = 20_
         out.append(known_optimum(rng, m, n, rp, ci, v, np.zeros(n), np.ones(n),
                                  frac_at_bound=0.4, y_nonzero=0.5, name=f"batch{seed}_{k}_{m}x{n}"))
     return out
+
+
+def vertex_lp(seed: int, m: int = 20, n: int = 40, density: float = 0.3) -> LP:
+    """LP with a unique, nondegenerate optimal vertex: equality rows A x = b, box [0, 1], exactly
+    m variables strictly inside the box (their columns A_F form a well-conditioned square block)
+    and n - m at a bound with a nonzero reduced cost; every dual multiplier nonzero.  Built for
+    derivatives of the solution with respect to b and the bounds (the active-set KKT system)."""
+    rng = np.random.default_rng(seed)
+    for _ in range(100):
+        mask = rng.random((m, n)) < density
+        F = rng.permutation(n)[:m]
+        mask[np.arange(m), F] = True  # a nonzero "diagonal" in the free block
+        A = np.where(mask, rng.standard_normal((m, n)), 0.0)
+        if np.linalg.cond(A[:, F]) < 1e3:
+            break
+    N = np.setdiff1d(np.arange(n), F)
+    x = np.empty(n)
+    x[F] = rng.uniform(0.2, 0.8, m)
+    at_hi = rng.random(len(N)) < 0.5
+    x[N] = np.where(at_hi, 1.0, 0.0)
+    r = np.zeros(n)
+    r[N] = np.where(at_hi, -1.0, 1.0) * rng.uniform(0.5, 1.5, len(N))
+    y = np.where(rng.random(m) < 0.5, 1.0, -1.0) * rng.uniform(0.5, 1.5, m)
+    b = A @ x
+    c = A.T @ y + r
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(mask.sum(axis=1), out=row_ptr[1:])
+    rows, cols = np.nonzero(mask)
+    return LP(m, n, row_ptr, cols.astype(np.int32), A[rows, cols].astype(np.float64), c, b.copy(), b.copy(),
+              np.zeros(n), np.ones(n), x, y, r, name=f"vertex_{m}x{n}_s{seed}")
