@@ -101,6 +101,11 @@ typedef struct {
                               the best, the phase stops (precision 1: hands over to FP64 with
                               omega and the PID state of the best check; precision 2: ends with
                               LP_SOLVE_STALLED).  0 disables the guard. */
+  int32_t rescale;         /* 1: bound/objective rescaling after the diagonal preconditioning --
+                              objective / ||c~||_2, bounds / ||finite (l_c~, u_c~)||_2.  This change
+                              of variables maps every PDHG step, restart decision and PID error
+                              onto those of the unrescaled iteration started from
+                              omega0 * ||c~|| / ||b~||, which is how it is applied.  0: off */
   int64_t batch_local_nnz; /* lp_batch_* only: instances with at most this many nonzeros are
                               solved by one thread block each (block barriers only) instead of
                               by the grid-wide loop; 0 puts every instance on the grid loop */
@@ -109,7 +114,7 @@ typedef struct {
 /* Fills p with the defaults: gamma 1, betas 0.2 / 0.8 / 0.36, K_P 0.5, K_I 0.001, K_D 0,
  * eta 0 (power iteration), omega0 1, check_every 64, restarts and PID on, power_tol 1e-7,
  * power_max_iter 10000, seed 0, Ruiz 10 + Pock-Chambolle alpha 1, no trace, unroll 8,
- * lane_target 8, persistent -1, precision 0, switch_tol 1e-5, fp32_patience 32,
+ * lane_target 8, persistent -1, precision 0, switch_tol 1e-5, fp32_patience 32, rescale 0,
  * batch_local_nnz 16384.  Returns LP_ERR_INVALID_ARG if p is NULL. */
 LP_API lp_status lp_default_params(lp_params* p);
 

@@ -49,13 +49,14 @@ class Params(C.Structure):
         ("ruiz_iters", C.c_int32),
         ("pc_enabled", C.c_int32),
         ("pc_alpha", C.c_double),
+        ("rescale", C.c_int32),
     ]
 
 
 DEFAULTS = dict(gamma=1.0, beta_sufficient=0.2, beta_necessary=0.8, beta_artificial=0.36,
                 k_p=0.5, k_i=0.001, k_d=0.0, eta=0.0, omega0=1.0, check_every=64,
                 restart_enabled=1, pid_enabled=1, power_tol=1e-7, power_max_iter=10000,
-                power_seed=0, ruiz_iters=10, pc_enabled=1, pc_alpha=1.0)
+                power_seed=0, ruiz_iters=10, pc_enabled=1, pc_alpha=1.0, rescale=0)
 
 
 def make_params(**kw) -> Params:

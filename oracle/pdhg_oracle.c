@@ -54,6 +54,8 @@ typedef struct {
   int32_t ruiz_iters;      /* diagonal preconditioning: Ruiz passes (0: none) */
   int32_t pc_enabled;      /* then one Pock-Chambolle pass with exponent pc_alpha */
   double pc_alpha;
+  int32_t rescale;         /* then divide the objective by ||c~||_2 and all bounds by the 2-norm
+                              of the finite constraint bounds (1 where a norm is 0) */
 } orc_params;
 
 enum { ORC_OPTIMAL = 1, ORC_ITER_LIMIT = 2, ORC_NUMERICAL = 3 };
@@ -394,6 +396,28 @@ int32_t orc_solve(int32_t m, int32_t n, const int64_t* rp, const int32_t* ci, co
     lc[i] = lc_in[i] * dr[i];
     uc[i] = uc_in[i] * dr[i];
   }
+  /* bound/objective rescaling: x' = x~ / beta, y' = y~ / gamma_c with beta = ||finite (l_c~,
+     u_c~)||_2, gamma_c = ||c~||_2; the LP in (x', y') has objective c~ / gamma_c and bounds / beta */
+  double beta = 1.0, gamma_c = 1.0;
+  if (prm->rescale) {
+    double b2 = 0.0, c2 = 0.0;
+    for (int32_t i = 0; i < m; ++i) {
+      if (isfinite(lc[i])) b2 += lc[i] * lc[i];
+      if (isfinite(uc[i])) b2 += uc[i] * uc[i];
+    }
+    for (int32_t j = 0; j < n; ++j) c2 += c[j] * c[j];
+    if (b2 > 0.0) beta = sqrt(b2);
+    if (c2 > 0.0) gamma_c = sqrt(c2);
+    for (int32_t j = 0; j < n; ++j) {
+      c[j] /= gamma_c;
+      lv[j] /= beta;
+      uv[j] /= beta;
+    }
+    for (int32_t i = 0; i < m; ++i) {
+      lc[i] /= beta;
+      uc[i] /= beta;
+    }
+  }
 
   double eta = prm->eta;
   if (!(eta > 0.0)) {
@@ -436,8 +460,8 @@ int32_t orc_solve(int32_t m, int32_t n, const int64_t* rp, const int32_t* ci, co
     if (!isfinite(r2)) { status = ORC_NUMERICAL; break; }
     int last = (t + 1 == max_iter);
     if (((t + 1) % prm->check_every) == 0 || last) {
-      for (int32_t j = 0; j < n; ++j) xo[j] = xh[j] * dc[j];
-      for (int32_t i = 0; i < m; ++i) yo[i] = yh[i] * dr[i];
+      for (int32_t j = 0; j < n; ++j) xo[j] = xh[j] * dc[j] * beta;
+      for (int32_t i = 0; i < m; ++i) yo[i] = yh[i] * dr[i] * gamma_c;
       orc_kkt(m, n, rp, ci, val_in, c_in, lc_in, uc_in, lv_in, uv_in, xo, yo, kkt);
       if (kkt[0] <= tol && kkt[1] <= tol && kkt[2] <= tol) { status = ORC_OPTIMAL; break; }
     }
@@ -464,8 +488,8 @@ int32_t orc_solve(int32_t m, int32_t n, const int64_t* rp, const int32_t* ci, co
       k += 1;
     }
   }
-  for (int32_t j = 0; j < n; ++j) xo[j] = xh[j] * dc[j];
-  for (int32_t i = 0; i < m; ++i) yo[i] = yh[i] * dr[i];
+  for (int32_t j = 0; j < n; ++j) xo[j] = xh[j] * dc[j] * beta;
+  for (int32_t i = 0; i < m; ++i) yo[i] = yh[i] * dr[i] * gamma_c;
   if (status == ORC_NUMERICAL || max_iter <= 0)
     orc_kkt(m, n, rp, ci, val_in, c_in, lc_in, uc_in, lv_in, uv_in, xo, yo, kkt);
   if (n > 0) memcpy(x_out, xo, sizeof(double) * (size_t)n);

@@ -69,6 +69,7 @@ class lp_params(C.Structure):
         ("precision", C.c_int32),
         ("switch_tol", C.c_double),
         ("fp32_patience", C.c_int32),
+        ("rescale", C.c_int32),
         ("batch_local_nnz", C.c_int64),
     ]
 

@@ -983,11 +983,22 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
   }
 
   // ---- scalar-state templates ----
+  std::vector<double> ratio(K, 1.0);
+  if (h->prm.rescale) {
+    std::vector<double> hc(sn), hl(sm), hu(sm);
+    if (sn > 0) CK(cudaMemcpy(hc.data(), h->c, sizeof(double) * sn, cudaMemcpyDeviceToHost));
+    if (sm > 0) CK(cudaMemcpy(hl.data(), h->lc, sizeof(double) * sm, cudaMemcpyDeviceToHost));
+    if (sm > 0) CK(cudaMemcpy(hu.data(), h->uc, sizeof(double) * sm, cudaMemcpyDeviceToHost));
+    for (int32_t k = 0; k < K; ++k) {
+      const BInst& I = h->inst[k];
+      ratio[k] = rescale_ratio(hc.data() + I.col0, I.n, hl.data() + I.row0, hu.data() + I.row0, I.m);
+    }
+  }
   std::vector<Ctl> init(K);
   for (int32_t k = 0; k < K; ++k) {
     Ctl& ci0 = init[k];
     ci0 = Ctl{};
-    const double e0 = h->eta[k], om = h->prm.omega0;
+    const double e0 = h->eta[k], om = h->prm.omega0 * (h->prm.rescale ? ratio[k] : 1.0);
     ci0.eta = e0;
     ci0.omega = om;
     ci0.tau = e0 / om;

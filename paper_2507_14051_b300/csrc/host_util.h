@@ -118,7 +118,21 @@ inline lp_status check_params(const lp_params& p) {
   if (!(p.switch_tol >= 0.0)) return fail(LP_ERR_INVALID_ARG, "switch_tol must be >= 0");
   if (p.fp32_patience < 0) return fail(LP_ERR_INVALID_ARG, "fp32_patience must be >= 0");
   if (p.batch_local_nnz < 0) return fail(LP_ERR_INVALID_ARG, "batch_local_nnz must be >= 0");
+  if (p.rescale < 0 || p.rescale > 1) return fail(LP_ERR_INVALID_ARG, "rescale must be 0 or 1");
   return LP_OK;
+}
+
+// ||c~||_2 / ||finite (l_c~, u_c~)||_2 of preconditioned data (each norm taken as 1 when 0): the
+// initial-weight factor that makes the plain iteration equal to the bound/objective-rescaled one.
+inline double rescale_ratio(const double* c, int64_t n, const double* lc, const double* uc, int64_t m) {
+  double c2 = 0.0, b2 = 0.0;
+  for (int64_t j = 0; j < n; ++j) c2 += c[j] * c[j];
+  for (int64_t i = 0; i < m; ++i) {
+    if (std::isfinite(lc[i])) b2 += lc[i] * lc[i];
+    if (std::isfinite(uc[i])) b2 += uc[i] * uc[i];
+  }
+  const double gamma = c2 > 0.0 ? std::sqrt(c2) : 1.0, beta = b2 > 0.0 ? std::sqrt(b2) : 1.0;
+  return gamma / beta;
 }
 
 }  // namespace pdhg_host

@@ -69,7 +69,8 @@ struct lp_solver {
   double lu_norm = 0.0, c_norm = 0.0;
   double eta = 0.0, norm_A = 0.0;
   int64_t pw_iters = 0;
-  bool power_valid = false;  // norm_A holds the power-iteration estimate for the current settings
+  bool power_valid = false;
+  double rescale_ratio = 1.0;  // ||c~|| / ||b~|| of the preconditioned data  // norm_A holds the power-iteration estimate for the current settings
   bool solved = false;
   cudaStream_t last_stream = nullptr;
   cudaStream_t setup_stream = nullptr;
@@ -511,6 +512,13 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
     CK(cudaGetLastError());
   }
   CK(cudaStreamSynchronize(s));
+  {
+    std::vector<double> hc(n), hl(m), hu(m);
+    if (n > 0) CK(cudaMemcpy(hc.data(), h->c, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (m > 0) CK(cudaMemcpy(hl.data(), h->lc, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    if (m > 0) CK(cudaMemcpy(hu.data(), h->uc, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    h->rescale_ratio = rescale_ratio(hc.data(), n, hl.data(), hu.data(), m);
+  }
 
   lp_status st = set_eta(h);
   if (st != LP_OK) return st;
@@ -549,6 +557,7 @@ lp_status lp_default_params(lp_params* p) {
   p->precision = 0;
   p->switch_tol = 1e-5;
   p->fp32_patience = 32;
+  p->rescale = 0;
   p->batch_local_nnz = 16384;
   return LP_OK;
 }
@@ -647,19 +656,20 @@ template <class V>
 lp_status enqueue_start(lp_solver* h, double tol, int64_t max_iter, cudaStream_t s) {
   Ctl init{};
   init.eta = h->eta;
-  init.omega = h->prm.omega0;
-  init.tau = h->eta / h->prm.omega0;
-  init.sigma = h->eta * h->prm.omega0;
-  init.inv_sigma = 1.0 / (h->eta * h->prm.omega0);
-  init.w_over_eta = h->prm.omega0 / h->eta;
-  init.inv_eta_w = 1.0 / (h->eta * h->prm.omega0);
+  const double om0 = h->prm.omega0 * (h->prm.rescale ? h->rescale_ratio : 1.0);
+  init.omega = om0;
+  init.tau = h->eta / om0;
+  init.sigma = h->eta * om0;
+  init.inv_sigma = 1.0 / (h->eta * om0);
+  init.w_over_eta = om0 / h->eta;
+  init.inv_eta_w = 1.0 / (h->eta * om0);
   init.restart_enabled = h->prm.restart_enabled;
   init.pid_enabled = h->prm.pid_enabled;
   init.max_iter = max_iter;
   init.check_every = h->prm.check_every;
   init.trace_cap = h->trace_cap;
   init.tol = tol;
-  init.omega_used = h->prm.omega0;
+  init.omega_used = om0;
   for (int q = 0; q < 8; ++q) init.kkt[q] = NAN;
   init.lu_norm = h->lu_norm;
   init.c_norm = h->c_norm;

@@ -28,7 +28,7 @@ pytestmark = pytest.mark.gpu
 
 SHARED = ("gamma", "beta_sufficient", "beta_necessary", "beta_artificial", "k_p", "k_i", "k_d",
           "eta", "omega0", "check_every", "restart_enabled", "pid_enabled", "power_tol",
-          "power_max_iter", "power_seed", "ruiz_iters", "pc_enabled", "pc_alpha")
+          "power_max_iter", "power_seed", "ruiz_iters", "pc_enabled", "pc_alpha", "rescale")
 RTOL_ITER = 1e-10
 
 
@@ -297,3 +297,51 @@ def test_set_params_changes_the_run(cuda_device):
     assert not np.array_equal(a["x"], b["x"])
     assert_iterates_close(b["x"], o["x"])
     np.testing.assert_array_equal(tr[:, 2], o["trace"][:, 2])
+
+
+# --------------------------------------------------------------------------- rescaling
+
+def _rescale_ratio(lp):
+    """||c~|| / ||finite (l_c~, u_c~)|| of the oracle's preconditioned data."""
+    val, dr, dc = oracle.scale(lp)
+    b = np.concatenate([lp.l_c * dr, lp.u_c * dr])
+    b = b[np.isfinite(b)]
+    beta = np.linalg.norm(b) if np.any(b != 0) else 1.0
+    gam = np.linalg.norm(lp.c * dc) if np.any(lp.c != 0) else 1.0
+    return gam / beta
+
+
+@pytest.mark.parametrize("make", [lambda: gen.small_lp(6), lambda: gen.free_and_boxed_mix(2, 60, 90),
+                                  lambda: gen.miplib_like(8, 2000, 4000, 1000)])
+def test_rescaling_matches_the_oracle(cuda_device, make):
+    """The oracle divides objective and bounds explicitly; the GPU starts from the equivalent
+    primal weight omega0 ||c~|| / ||b~||.  Same iterates, restarts and epoch steps; the GPU's
+    omega is the oracle's times that ratio (the oracle iterates in the rescaled variables)."""
+    lp = make()
+    eta = oracle_eta(lp)
+    iters = 400
+    o = oracle_solve(lp, 0.0, iters, trace=True, eta=eta, rescale=1)
+    tie = first_near_tie(o["trace"])
+    if tie is not None and tie < iters - 1:
+        iters = tie + 1
+        o = oracle_solve(lp, 0.0, iters, trace=True, eta=eta, rescale=1)
+    g = gpu_solve(lp, 0.0, iters, trace=True, eta=eta, rescale=1)
+    np.testing.assert_array_equal(g["trace"][:, 2], o["trace"][:, 2])
+    np.testing.assert_array_equal(g["trace"][:, 3], o["trace"][:, 3])
+    w = _rescale_ratio(lp)
+    r = o["trace"][:, 0]
+    w_tol = 1e-13 * float(np.max(r)) / np.maximum(r, 1e-300) + 1e-11
+    assert np.all(np.abs(g["trace"][:, 1] - o["trace"][:, 1] * w) <= w_tol * g["trace"][:, 1])
+    assert_iterates_close(g["x"], o["x"], rtol=1e-9)
+    assert_iterates_close(g["y"], o["y"], rtol=1e-9)
+
+
+def test_rescaled_solve_to_tolerance(cuda_device):
+    lp = gen.small_lp(7)
+    eta = oracle_eta(lp)
+    g = gpu_solve(lp, 1e-8, 100000, eta=eta, rescale=1)
+    o = oracle_solve(lp, 1e-8, 100000, eta=eta, rescale=1, trace=True)
+    assert g["status"] == o["status"] == oracle.OPTIMAL
+    if first_near_tie(o["trace"]) is None:
+        assert g["iters"] == o["iters"]
+    assert oracle.kkt(lp, g["x"], g["y"])[3] <= 1e-8
