@@ -106,6 +106,12 @@ typedef struct {
                               of variables maps every PDHG step, restart decision and PID error
                               onto those of the unrescaled iteration started from
                               omega0 * ||c~|| / ||b~||, which is how it is applied.  0: off */
+  int32_t tile_rows;       /* rows per warp tile (1..32, rounded down to a power of two): a tile
+                              of R rows, each read by G lanes (G from lane_target), takes R G / 32
+                              passes and runs its R row epilogues in R lanes at once; 0: automatic
+                              (1 for lp_solve, whose latency-bound sizes want short tasks; 32 for
+                              the batch, whose long rows would otherwise spend one warp's FP64
+                              issue on each row's epilogue) */
   int64_t batch_local_nnz; /* lp_batch_* only: instances with at most this many nonzeros are
                               solved by one thread block each (block barriers only) instead of
                               by the grid-wide loop; 0 puts every instance on the grid loop */
@@ -115,7 +121,7 @@ typedef struct {
  * eta 0 (power iteration), omega0 1, check_every 64, restarts and PID on, power_tol 1e-7,
  * power_max_iter 10000, seed 0, Ruiz 10 + Pock-Chambolle alpha 1, no trace, unroll 8,
  * lane_target 8, persistent -1, precision 0, switch_tol 1e-5, fp32_patience 32, rescale 0,
- * batch_local_nnz 16384.  Returns LP_ERR_INVALID_ARG if p is NULL. */
+ * tile_rows 0, batch_local_nnz 16384.  Returns LP_ERR_INVALID_ARG if p is NULL. */
 LP_API lp_status lp_default_params(lp_params* p);
 
 typedef struct lp_solver* lp_handle;

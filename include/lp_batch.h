@@ -33,9 +33,9 @@ typedef struct lp_batch* lp_batch_handle;
  *   eta   NULL: instance k uses p->eta if > 0, else 0.998 / ||A~_k||_2 from a power iteration
  *         on its own preconditioned matrix (Section 3, "Stepsize"); or double[count], each > 0,
  *         the step size of each instance.
- *   lane_target  NULL: p->lane_target for every instance; or int32[count] in [1, 64], the tile
- *         schedule of each instance (entries per lane, as lp_params.lane_target), e.g. from
- *         lp_tune_lane_target.
+ *   tiles NULL: p->lane_target and p->tile_rows for every instance; or int32[2 * count], the
+ *         tile schedule of each instance as (lane_target in [1, 64], tile_rows in [1, 32]),
+ *         e.g. from lp_tune_schedule.
  *   p     shared parameters (NULL: lp_default_params).  precision 0, 1 and 2 as for lp_solve;
  *         in a batch the FP32 phase of every instance ends before the FP64 phase of any
  *         instance starts.  trace_cap, unroll and persistent are ignored (no trace; the batch
@@ -52,8 +52,7 @@ LP_API lp_status lp_batch_create(int32_t count, const int32_t* m, const int32_t*
                                  const double* const* c, const double* const* l_c,
                                  const double* const* u_c, const double* const* l_v,
                                  const double* const* u_v, const double* eta,
-                                 const int32_t* lane_target, const lp_params* p,
-                                 lp_batch_handle* out);
+                                 const int32_t* tiles, const lp_params* p, lp_batch_handle* out);
 
 /*
  * Enqueues one solve of every instance from the zero start on `stream` (a cudaStream_t, NULL for
@@ -96,19 +95,21 @@ LP_API lp_status lp_batch_time_loop(lp_batch_handle h, int64_t iters, int32_t pr
 /*
  * Tile-schedule tuner (this library's own; the paper has no counterpart).  For the HOST CSR
  * matrix (row_ptr int64[m+1], col_idx int32[nnz], val double[nnz], validated as in lp_create)
- * it builds the length-binned layout of lp_batch_create, times the device SpMVs y = A x and
- * y = A^T x for lane_target in {2, 4, 8, 16, 32} (mean of 20 launches after 3 warm-up
- * launches, CUDA events on the legacy default stream) and returns the fastest in *best.
+ * it times the batch loop kernel (lp_batch_time_loop, 32 FP64 iterations, CUDA events) on a
+ * batch of copies of the matrix (about 4M nonzeros in all, at most 256 copies, all on the grid
+ * loop, box bounds [-1, 1] and a fixed objective so that every clamp is exercised) for each
+ * schedule (lane_target, tile_rows) in {8, 16, 32} x {1, 8, 32}, and returns the fastest.
  * Results are cached per shape class -- the size classes of m, n, nnz and the share of nonzeros
  * in each row-length and column-length class -- in the process and, if cache_path is not NULL,
- * in that text file (one "class value" line per entry, appended).  A cached class returns
- * without timing unless ms_out is given; ms_out (NULL or double[5]) receives the time of each
- * candidate.  Errors: LP_ERR_INVALID_ARG, LP_ERR_INVALID_INPUT, LP_ERR_TOO_LARGE,
- * LP_ERR_OUT_OF_MEMORY, LP_ERR_CUDA.
+ * in that text file (one "class 100*lane_target+tile_rows" line per entry, appended).  A cached
+ * class returns without timing unless ms_out is given; ms_out (NULL or double[9]) receives the
+ * time per iteration of each candidate, in the order above with lane_target varying fastest.
+ * Errors: LP_ERR_INVALID_ARG, LP_ERR_INVALID_INPUT, LP_ERR_TOO_LARGE, LP_ERR_OUT_OF_MEMORY,
+ * LP_ERR_CUDA.
  */
-LP_API lp_status lp_tune_lane_target(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
-                                     const int32_t* col_idx, const double* val,
-                                     const char* cache_path, int32_t* best, double* ms_out);
+LP_API lp_status lp_tune_schedule(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
+                                  const int32_t* col_idx, const double* val, const char* cache_path,
+                                  int32_t* lane_target, int32_t* tile_rows, double* ms_out);
 
 /* Frees the batch (waits for its work first).  NULL is a no-op. */
 LP_API void lp_batch_destroy(lp_batch_handle h);

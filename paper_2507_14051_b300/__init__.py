@@ -37,7 +37,7 @@ EXPORTED = ("lp_default_params", "lp_create", "lp_set_params", "lp_solve", "lp_g
             "lp_get_info", "lp_get_trace", "lp_destroy", "lp_last_error", "lp_time_kernels",
             "lp_debug_spmv", "lp_debug_layout", "lp_power_norm_noalloc",
             "lp_batch_create", "lp_batch_solve", "lp_batch_get", "lp_batch_get_all",
-            "lp_batch_time_loop", "lp_batch_destroy", "lp_tune_lane_target",
+            "lp_batch_time_loop", "lp_batch_destroy", "lp_tune_schedule",
             "lp_batch_set_data", "lp_batch_unroll", "lp_batch_unroll_vjp", "lp_batch_get_trace")
 
 
@@ -70,6 +70,7 @@ class lp_params(C.Structure):
         ("switch_tol", C.c_double),
         ("fp32_patience", C.c_int32),
         ("rescale", C.c_int32),
+        ("tile_rows", C.c_int32),
         ("batch_local_nnz", C.c_int64),
     ]
 
@@ -122,7 +123,7 @@ def load(path: str | None = None) -> C.CDLL:
         pp = C.POINTER(C.c_void_p)
         L.lp_batch_create.argtypes = [C.c_int32, vp, vp, vp, pp, pp, pp, pp, pp, pp, pp, pp, vp, vp,
                                       C.POINTER(lp_params), C.POINTER(C.c_void_p)]
-        L.lp_tune_lane_target.argtypes = [C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, C.c_char_p, i32p, dp]
+        L.lp_tune_schedule.argtypes = [C.c_int32, C.c_int32, C.c_int64, vp, vp, vp, C.c_char_p, i32p, i32p, dp]
         L.lp_batch_set_data.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int32]
         L.lp_batch_unroll.argtypes = [vp, C.c_int64, C.c_int64, vp, vp, vp]
         L.lp_batch_unroll_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -315,7 +316,7 @@ class BatchSolver:
     ``eta``: None (power iteration per instance, or params' eta) or a sequence of per-instance
     step sizes."""
 
-    def __init__(self, lps, eta=None, lane_target=None, **params):
+    def __init__(self, lps, eta=None, tiles=None, **params):
         self.count = len(lps)
         self.shapes = [(int(lp.m), int(lp.n)) for lp in lps]
         cols = {"row_ptr": np.int64, "col_idx": np.int32, "val": np.float64, "c": np.float64,
@@ -326,7 +327,7 @@ class BatchSolver:
         n = np.array([s[1] for s in self.shapes], np.int32)
         nnz = np.array([int(a[-1]) for a in keep["row_ptr"]], np.int64)
         eta_arr = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
-        lt_arr = None if lane_target is None else np.ascontiguousarray(lane_target, dtype=np.int32)
+        lt_arr = None if tiles is None else np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(-1))
         self.params = lp_default_params(**params)
         h = C.c_void_p()
         _check(load().lp_batch_create(self.count, m.ctypes.data, n.ctypes.data, nnz.ctypes.data,
@@ -413,22 +414,26 @@ class BatchSolver:
         self.close()
 
 
-def lp_tune_lane_target(lp, cache_path: str | None = None, timings: bool = False):
-    """Fastest tile schedule (lane_target) for lp's matrix, cached per shape class (see
-    include/lp_batch.h).  Returns best, or (best, ms per candidate [2, 4, 8, 16, 32])."""
+TUNE_CANDIDATES = [(8, 1), (16, 1), (32, 1), (8, 8), (16, 8), (32, 8), (8, 32), (16, 32), (32, 32)]
+
+
+def lp_tune_schedule(lp, cache_path: str | None = None, timings: bool = False):
+    """Fastest tile schedule (lane_target, tile_rows) for lp's matrix in the batch loop, cached per
+    shape class (see include/lp_batch.h).  Returns the pair, or (pair, ms per iteration of each
+    of TUNE_CANDIDATES)."""
     rp = np.ascontiguousarray(lp.row_ptr, dtype=np.int64)
     ci = np.ascontiguousarray(lp.col_idx, dtype=np.int32)
     v = np.ascontiguousarray(lp.val, dtype=np.float64)
-    best = C.c_int32(0)
-    ms = np.zeros(5)
-    _check(load().lp_tune_lane_target(int(lp.m), int(lp.n), int(rp[-1]), rp.ctypes.data, ci.ctypes.data,
-                                      v.ctypes.data, None if cache_path is None else cache_path.encode(),
-                                      C.byref(best), ms.ctypes.data_as(C.POINTER(C.c_double)) if timings else None),
-           "lp_tune_lane_target")
-    return (best.value, ms) if timings else best.value
+    lt, tr = C.c_int32(0), C.c_int32(0)
+    ms = np.zeros(len(TUNE_CANDIDATES))
+    _check(load().lp_tune_schedule(int(lp.m), int(lp.n), int(rp[-1]), rp.ctypes.data, ci.ctypes.data, v.ctypes.data,
+                                   None if cache_path is None else cache_path.encode(), C.byref(lt), C.byref(tr),
+                                   ms.ctypes.data_as(C.POINTER(C.c_double)) if timings else None),
+           "lp_tune_schedule")
+    return ((lt.value, tr.value), ms) if timings else (lt.value, tr.value)
 
 
 def tune_batch(lps, cache_path: str | None = None):
-    """Per-instance tile schedules for a batch: one tuning run per shape class (the library
-    caches by class), so a batch of many similar instances costs a few timings."""
-    return [lp_tune_lane_target(lp, cache_path) for lp in lps]
+    """Per-instance tile schedules for a batch (for BatchSolver(tiles=...)): one tuning run per
+    shape class, the library caching by class."""
+    return [lp_tune_schedule(lp, cache_path) for lp in lps]

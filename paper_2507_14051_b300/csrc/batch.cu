@@ -168,6 +168,7 @@ __device__ __forceinline__ void row_phase(const BatchArgs<V>& a, const int32_t* 
     const int4 td = a.tasksA[tix];
     const BRow br = a.rstep[ii];
     const V* __restrict__ xg = br.par ? a.ra.xh1 : a.ra.xh0;
+    if (lane < td.y) row_prefetch(a.ra, br.st, td.x + lane);
     const V v = tile_spmv(a.ra.rp, a.ra.ci, a.ra.val, xg, td.x, td.y, task_lanes(td), task_per_lane(td),
                           lane, pol);
     double acc[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -206,6 +207,7 @@ __device__ __forceinline__ void col_phase(const BatchArgs<V>& a, const int32_t* 
     st.tau = bc.tau;
     st.xc = bc.par ? a.ca.xh1 : a.ca.xh0;
     st.xn = bc.par ? a.ca.xh0 : a.ca.xh1;
+    if (lane < td.y) col_prefetch(a.ca, st, td.x + lane);
     const V u = tile_spmv(a.ca.rp, a.ca.ci, a.ca.val, a.ca.yh, td.x, td.y, task_lanes(td),
                           task_per_lane(td), lane, pol);
     double acc[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -493,6 +495,7 @@ __global__ void __launch_bounds__(kThreads, 2) kb_block_loop(BatchArgs<V> a, con
       double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
       for (int j = warp; j < I.nta; j += kWarps) {
         const int4 td = a.tasksA[I.ta0 + j];
+        if (lane < td.y) row_prefetch(a.ra, st, td.x + lane);
         const V v = tile_spmv(a.ra.rp, a.ra.ci, a.ra.val, xg, td.x, td.y, task_lanes(td), task_per_lane(td),
                               lane, pol);
         if (lane < td.y) row_epilogue(a.ra, st, td.x + lane, v, s);
@@ -508,6 +511,7 @@ __global__ void __launch_bounds__(kThreads, 2) kb_block_loop(BatchArgs<V> a, con
       double s2[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
       for (int j = warp; j < I.ntt; j += kWarps) {
         const int4 td = a.tasksT[I.tt0 + j];
+        if (lane < td.y) col_prefetch(a.ca, cs, td.x + lane);
         const V u = tile_spmv(a.ca.rp, a.ca.ci, a.ca.val, a.ca.yh, td.x, td.y, task_lanes(td),
                               task_per_lane(td), lane, pol);
         if (lane < td.y) col_epilogue(a.ca, cs, td.x + lane, u, s2);
@@ -615,9 +619,9 @@ using namespace pdhg_host;
 
 namespace {
 
-// Tiles of rows already sorted by decreasing length class (the single-instance schedule without
-// chunks: a row of any length gets at most one warp).
-void make_tasks(const std::vector<int32_t>& rp, int lane_target, int32_t row_base, int32_t inst,
+// Tiles of rows already sorted by decreasing length class, shaped by tile_shape (the
+// single-instance schedule without chunks: a row of any length gets at most one warp).
+void make_tasks(const std::vector<int32_t>& rp, int lane_target, int tile_rows, int32_t row_base, int32_t inst,
                 std::vector<int4>& out) {
   const int32_t rows = (int32_t)rp.size() - 1;
   int32_t r = 0;
@@ -625,17 +629,10 @@ void make_tasks(const std::vector<int32_t>& rp, int lane_target, int32_t row_bas
     const int cls = length_class(rp[r + 1] - rp[r]);
     int32_t e = r + 1;
     while (e < rows && length_class(rp[e + 1] - rp[e]) == cls) ++e;
-    const int64_t lc = int64_t(1) << cls;
-    const int64_t rr = (int64_t)32 * lane_target / lc;
-    int R = (int)(rr < 1 ? 1 : (rr > 32 ? 32 : rr));
-    int Rp = 1;
-    while (Rp * 2 <= R) Rp *= 2;
-    R = Rp;
-    const int G = 32 / R;
-    const int64_t per_lane = (lc + G - 1) / G;
-    const int32_t pl = (int32_t)(per_lane < 0xFFFFFF ? per_lane : 0xFFFFFF);
-    for (int32_t q = r; q < e; q += R)
-      out.push_back(make_int4(row_base + q, std::min<int32_t>(R, e - q), (G << 24) | pl, inst));
+    const TileShape ts = tile_shape(int64_t(1) << cls, lane_target, tile_rows);
+    const int32_t pl = ts.per_lane < 0xFFFFFF ? ts.per_lane : 0xFFFFFF;
+    for (int32_t q = r; q < e; q += ts.rows)
+      out.push_back(make_int4(row_base + q, std::min<int32_t>(ts.rows, e - q), (ts.lanes << 24) | pl, inst));
     r = e;
   }
 }
@@ -753,7 +750,7 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
                             const int64_t* const* rp, const int32_t* const* ci, const double* const* val,
                             const double* const* c, const double* const* lc, const double* const* uc,
                             const double* const* lv, const double* const* uv, const double* eta,
-                            const int32_t* lane_target) {
+                            const int32_t* tiles) {
   const int32_t K = h->count;
 
   // ---- sizes and offsets ----
@@ -810,9 +807,10 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
     for (int32_t i = 0; i < mk; ++i) rpl[i + 1] = rpl[i] + (int32_t)rlen[b.row_perm[i]];
     cpl[0] = 0;
     for (int32_t j = 0; j < nk; ++j) cpl[j + 1] = cpl[j] + (int32_t)clen[b.col_perm[j]];
-    const int lt = lane_target ? lane_target[k] : h->prm.lane_target;
-    make_tasks(rpl, lt, h->inst[k].row0, k, b.tA);
-    make_tasks(cpl, lt, h->inst[k].col0, k, b.tT);
+    const int lt = tiles ? tiles[2 * k] : h->prm.lane_target;
+    const int tr = tiles ? tiles[2 * k + 1] : (h->prm.tile_rows > 0 ? h->prm.tile_rows : kBatchTileRows);
+    make_tasks(rpl, lt, tr, h->inst[k].row0, k, b.tA);
+    make_tasks(cpl, lt, tr, h->inst[k].col0, k, b.tT);
     b.rlen_perm.swap(rpl);
     b.clen_perm.swap(cpl);
     return LP_OK;
@@ -1127,8 +1125,10 @@ lp_status batch_schedule_solve(lp_batch* h, int64_t K, cudaStream_t s) {
 
 namespace {
 
-constexpr int kTuneCand[] = {2, 4, 8, 16, 32};
-constexpr int kTuneN = 5;
+// Candidate tile schedules (lane_target, tile_rows).
+constexpr int kTuneLane[] = {8, 16, 32, 8, 16, 32, 8, 16, 32};
+constexpr int kTuneRows[] = {1, 1, 1, 8, 8, 8, 32, 32, 32};
+constexpr int kTuneN = 9;
 
 // Length-class signature of a CSR (rows) and of its transpose (columns): the schedule depends
 // on the matrix only through these, so they key the cache together with the sizes' classes.
@@ -1149,22 +1149,6 @@ std::string shape_class(int32_t m, int32_t n, int64_t nnz, const int64_t* rp, co
   }
   return key;
 }
-
-// Device buffers freed at scope exit.
-struct DevBufs {
-  std::vector<void*> p;
-  ~DevBufs() {
-    for (void* q : p) cudaFree(q);
-  }
-  template <class T>
-  cudaError_t get(T** out, size_t cnt) {
-    void* v = nullptr;
-    cudaError_t e = cudaMalloc(&v, std::max<size_t>(cnt, 1) * sizeof(T));
-    if (e == cudaSuccess) p.push_back(v);
-    *out = static_cast<T*>(v);
-    return e;
-  }
-};
 
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune_cache;
@@ -1205,113 +1189,64 @@ void cache_store(const std::string& key, const char* path, int best) {
 
 }  // namespace
 
-lp_status lp_tune_lane_target(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
-                              const int32_t* col_idx, const double* val, const char* cache_path,
-                              int32_t* best_out, double* ms_out) {
+lp_status lp_tune_schedule(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                           const double* val, const char* cache_path, int32_t* lane_target_out,
+                           int32_t* tile_rows_out, double* ms_out) {
   pdhg_set_last_error(std::string());
-  if (!best_out || !row_ptr || (nnz > 0 && (!col_idx || !val))) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  if (!lane_target_out || !tile_rows_out || !row_ptr || (nnz > 0 && (!col_idx || !val)))
+    return fail(LP_ERR_INVALID_ARG, "NULL argument");
   if (m < 0 || n < 0 || nnz < 0) return fail(LP_ERR_INVALID_ARG, "negative size");
   if (nnz >= INT32_MAX) return fail(LP_ERR_TOO_LARGE, "nnz must be below 2^31");
-  std::vector<double> ones(std::max(m, n) + 1, 0.0);
-  std::vector<double> zc(n, 0.0);
-  std::vector<double> lo(std::max(m, n), -INFINITY), hi(std::max(m, n), INFINITY);
-  lp_status st = validate(m, n, nnz, row_ptr, col_idx, val, zc.data(), lo.data(), hi.data(), lo.data(), hi.data());
+  // a box LP on the given matrix: every clamp of the iteration is exercised
+  std::vector<double> zc(n, 0.0), lo_n(n, -1.0), hi_n(n, 1.0), lo_m(m, -1.0), hi_m(m, 1.0);
+  for (int32_t j = 0; j < n; ++j) zc[j] = (j % 3 == 0) ? 1.0 : -0.5;
+  lp_status st = validate(m, n, nnz, row_ptr, col_idx, val, zc.data(), lo_m.data(), hi_m.data(), lo_n.data(),
+                          hi_n.data());
   if (st != LP_OK) return st;
   const std::string key = shape_class(m, n, nnz, row_ptr, col_idx);
   int cached = 0;
   if (!ms_out && cache_lookup(key, cache_path, &cached)) {
-    *best_out = cached;
+    *lane_target_out = cached / 100;
+    *tile_rows_out = cached % 100;
     return LP_OK;
   }
-  // permuted CSR of A and A^T (as lp_batch_create builds them), one upload
-  std::vector<int64_t> rlen(m), clen(n, 0);
-  for (int32_t i = 0; i < m; ++i) rlen[i] = row_ptr[i + 1] - row_ptr[i];
-  for (int64_t p = 0; p < nnz; ++p) clen[col_idx[p]]++;
-  std::vector<int32_t> rperm, cperm;
-  order_by_class(rlen, rperm);
-  order_by_class(clen, cperm);
-  std::vector<int32_t> cinv(n);
-  for (int32_t j = 0; j < n; ++j) cinv[cperm[j]] = j;
-  std::vector<int32_t> rpA(m + 1), ciA(nnz), rpT(n + 1), ciT(nnz), cur(n);
-  std::vector<double> vA(nnz), vT(nnz);
-  rpA[0] = 0;
-  for (int32_t i = 0; i < m; ++i) rpA[i + 1] = rpA[i] + (int32_t)rlen[rperm[i]];
-  for (int32_t i = 0; i < m; ++i) {
-    int32_t q = rpA[i];
-    for (int64_t p = row_ptr[rperm[i]]; p < row_ptr[rperm[i] + 1]; ++p, ++q) {
-      ciA[q] = cinv[col_idx[p]];
-      vA[q] = val[p];
-    }
-  }
-  rpT[0] = 0;
-  for (int32_t j = 0; j < n; ++j) rpT[j + 1] = rpT[j] + (int32_t)clen[cperm[j]];
-  for (int32_t j = 0; j < n; ++j) cur[j] = rpT[j];
-  for (int32_t i = 0; i < m; ++i)
-    for (int32_t q = rpA[i]; q < rpA[i + 1]; ++q) {
-      const int32_t pos = cur[ciA[q]]++;
-      ciT[pos] = i;
-      vT[pos] = vA[q];
-    }
-  int dev = 0, sms = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  DevBufs B;
-  int32_t *d_rpA, *d_ciA, *d_rpT, *d_ciT;
-  double *d_vA, *d_vT, *d_x, *d_y;
-  int4* d_t;
-  CK(B.get(&d_rpA, m + 1)); CK(B.get(&d_ciA, nnz)); CK(B.get(&d_vA, nnz));
-  CK(B.get(&d_rpT, n + 1)); CK(B.get(&d_ciT, nnz)); CK(B.get(&d_vT, nnz));
-  CK(B.get(&d_x, std::max(m, n))); CK(B.get(&d_y, std::max(m, n)));
-  CK(cudaMemcpy(d_rpA, rpA.data(), sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(d_rpT, rpT.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
-  if (nnz > 0) {
-    CK(cudaMemcpy(d_ciA, ciA.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_vA, vA.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_ciT, ciT.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_vT, vT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
-  }
-  std::fill(ones.begin(), ones.end(), 1.0);
-  CK(cudaMemcpy(d_x, ones.data(), sizeof(double) * std::max(m, n), cudaMemcpyHostToDevice));
-  size_t tmax = 0;
-  std::vector<std::vector<int4>> tA(kTuneN), tT(kTuneN);
-  for (int q = 0; q < kTuneN; ++q) {
-    make_tasks(rpA, kTuneCand[q], 0, 0, tA[q]);
-    make_tasks(rpT, kTuneCand[q], 0, 0, tT[q]);
-    tmax = std::max(tmax, tA[q].size() + tT[q].size());
-  }
-  CK(B.get(&d_t, tmax));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  // copies of the instance, enough to fill the device (about 4M nonzeros), on the grid loop
+  const int32_t rep = (int32_t)std::max<int64_t>(1, std::min<int64_t>(256, (int64_t(1) << 22) / std::max<int64_t>(nnz, 1)));
+  std::vector<int32_t> vm(rep, m), vn(rep, n);
+  std::vector<int64_t> vz(rep, nnz);
+  std::vector<const int64_t*> vrp(rep, row_ptr);
+  std::vector<const int32_t*> vci(rep, col_idx);
+  std::vector<const double*> vval(rep, val), vc(rep, zc.data()), vlc(rep, lo_m.data()), vuc(rep, hi_m.data()),
+      vlv(rep, lo_n.data()), vuv(rep, hi_n.data());
+  lp_params prm;
+  lp_default_params(&prm);
+  prm.batch_local_nnz = 0;
   double best_ms = INFINITY;
-  int best = 8;
-  const int reps = 20;
+  int best = 0;
+  std::vector<int32_t> tiles(2 * (size_t)rep);
   for (int q = 0; q < kTuneN; ++q) {
-    const int32_t na = (int32_t)tA[q].size(), nt = (int32_t)tT[q].size();
-    if (na > 0) CK(cudaMemcpy(d_t, tA[q].data(), sizeof(int4) * na, cudaMemcpyHostToDevice));
-    if (nt > 0) CK(cudaMemcpy(d_t + na, tT[q].data(), sizeof(int4) * nt, cudaMemcpyHostToDevice));
-    const int gA = grid_for(std::max(na, 1), kWarps, 8 * sms), gT = grid_for(std::max(nt, 1), kWarps, 8 * sms);
-    for (int r = 0; r < 3 + reps; ++r) {
-      if (r == 3) CK(cudaEventRecord(e0, 0));
-      if (na > 0) kb_spmv<double><<<gA, kThreads>>>(d_t, na, d_rpA, d_ciA, d_vA, d_x, d_y);
-      if (nt > 0) kb_spmv<double><<<gT, kThreads>>>(d_t + na, nt, d_rpT, d_ciT, d_vT, d_y, d_x);
+    for (int32_t k = 0; k < rep; ++k) {
+      tiles[2 * k] = kTuneLane[q];
+      tiles[2 * k + 1] = kTuneRows[q];
     }
-    CK(cudaGetLastError());
-    CK(cudaEventRecord(e1, 0));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0.0f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    const double per = (double)ms / reps;
-    if (ms_out) ms_out[q] = per;
-    if (per < best_ms) {
-      best_ms = per;
-      best = kTuneCand[q];
+    lp_batch_handle h = nullptr;
+    st = lp_batch_create(rep, vm.data(), vn.data(), vz.data(), vrp.data(), vci.data(), vval.data(), vc.data(),
+                         vlc.data(), vuc.data(), vlv.data(), vuv.data(), nullptr, tiles.data(), &prm, &h);
+    if (st != LP_OK) return st;
+    double out[2] = {0.0, 0.0};
+    st = lp_batch_time_loop(h, 32, 1, nullptr, out);
+    lp_batch_destroy(h);
+    if (st != LP_OK) return st;
+    const double per_iter = out[0] / out[1];
+    if (ms_out) ms_out[q] = per_iter;
+    if (per_iter < best_ms) {
+      best_ms = per_iter;
+      best = q;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cache_store(key, cache_path, best);
-  *best_out = best;
+  cache_store(key, cache_path, 100 * kTuneLane[best] + kTuneRows[best]);
+  *lane_target_out = kTuneLane[best];
+  *tile_rows_out = kTuneRows[best];
   return LP_OK;
 }
 
@@ -1321,7 +1256,7 @@ lp_status lp_batch_create(int32_t count, const int32_t* m, const int32_t* n, con
                           const int64_t* const* row_ptr, const int32_t* const* col_idx,
                           const double* const* val, const double* const* c, const double* const* l_c,
                           const double* const* u_c, const double* const* l_v,
-                          const double* const* u_v, const double* eta, const int32_t* lane_target,
+                          const double* const* u_v, const double* eta, const int32_t* tiles,
                           const lp_params* p, lp_batch_handle* out) {
   pdhg_set_last_error(std::string());
   if (!out) return fail(LP_ERR_INVALID_ARG, "out is NULL");
@@ -1339,14 +1274,14 @@ lp_status lp_batch_create(int32_t count, const int32_t* m, const int32_t* n, con
     for (int32_t k = 0; k < count; ++k)
       if (!(eta[k] > 0.0) || !std::isfinite(eta[k]))
         return fail(LP_ERR_INVALID_ARG, "eta[" + std::to_string(k) + "] must be finite and > 0");
-  if (lane_target)
+  if (tiles)
     for (int32_t k = 0; k < count; ++k)
-      if (lane_target[k] < 1 || lane_target[k] > 64)
-        return fail(LP_ERR_INVALID_ARG, "lane_target[" + std::to_string(k) + "] must be in [1, 64]");
+      if (tiles[2 * k] < 1 || tiles[2 * k] > 64 || tiles[2 * k + 1] < 1 || tiles[2 * k + 1] > 32)
+        return fail(LP_ERR_INVALID_ARG, "tiles[" + std::to_string(k) + "] must be (lane_target in [1, 64], tile_rows in [1, 32])");
   lp_batch* h = new lp_batch();
   h->count = count;
   h->prm = prm;
-  st = batch_create_impl(h, m, n, nnz, row_ptr, col_idx, val, c, l_c, u_c, l_v, u_v, eta, lane_target);
+  st = batch_create_impl(h, m, n, nnz, row_ptr, col_idx, val, c, l_c, u_c, l_v, u_v, eta, tiles);
   if (st != LP_OK) {
     const std::string keep = lp_last_error();
     delete h;

@@ -13,6 +13,7 @@
 namespace pdhg {
 
 constexpr int kBatchUnroll = 16;  // iterations per launch of the batch loop kernel
+constexpr int kBatchTileRows = 32;  // rows per tile of the batch when lp_params.tile_rows is 0
 constexpr int kMaxInst = LP_BATCH_MAX_INSTANCES;
 
 // Place of one instance in the concatenated arrays.

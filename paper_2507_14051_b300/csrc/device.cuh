@@ -130,6 +130,11 @@ __device__ __forceinline__ float ld_stream(const float* p, uint64_t pol) {
   asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
   return v;
 }
+// Prefetch of the line holding *p into L1 (no register is written; the later load hits L1).
+template <class T>
+__device__ __forceinline__ void prefetch_l1(const T* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 // Gathered vector entries: L2 evict-last.
 __device__ __forceinline__ double ld_gather(const double* p, uint64_t pol) {
   double v;
@@ -228,16 +233,18 @@ __device__ __forceinline__ V tile_spmv(const int32_t* __restrict__ rp, const int
 }
 
 // Visits every row of a binned CSR matrix once with its dot product against xg and calls
-// epi(row, value, acc) in exactly one lane: lane L < nrows of the warp that owns a tile (acc =
-// that thread's running sums `s`), or lane 0 of the warp that finishes a long row's last chunk
-// (acc = a zeroed array then stored in bins.contrib for the last block to add in row order).
-// Every sum therefore has a fixed order that depends only on the grid size: results are
-// bit-reproducible run to run.
-template <class V, class Epi>
-__device__ __forceinline__ void for_each_row(const BinTable& bins, const int32_t* __restrict__ rp,
-                                             const int32_t* __restrict__ ci, const V* __restrict__ val,
-                                             const V* __restrict__ xg, const LoadPolicy& pol,
-                                             double (&s)[kNumSums], Epi&& epi) {
+// epi(row, value, in, acc) in exactly one lane: lane L < nrows of the warp that owns a tile (acc =
+// that thread's running sums `s`; in = pre(row), issued before the tile's SpMV so that the
+// row's own operands load while the SpMV runs), or lane 0 of the warp that finishes a long
+// row's last chunk (acc = a zeroed array then stored in bins.contrib for the last block to add
+// in row order; in = pre(row) loaded there).  Every sum therefore has a fixed order that
+// depends only on the grid size: results are bit-reproducible run to run.
+template <class V, class Pre, class Epi>
+__device__ __forceinline__ void for_each_row_pf(const BinTable& bins, const int32_t* __restrict__ rp,
+                                                const int32_t* __restrict__ ci, const V* __restrict__ val,
+                                                const V* __restrict__ xg, const LoadPolicy& pol,
+                                                double (&s)[kNumSums], Pre&& pre, Epi&& epi) {
+  using In = decltype(pre(0));
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * kWarps;
   const int total = bins.nchunks + bins.ntasks;
@@ -256,7 +263,8 @@ __device__ __forceinline__ void for_each_row(const BinTable& bins, const int32_t
           for (int q = 0; q < ch.z; ++q) tot += __ldcg(bins.part + ch.y + q);
           bins.arrivals[ch.x] = 0u;
           double c[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-          epi(ch.x, (V)tot, c);
+          In in = pre(ch.x);
+          epi(ch.x, (V)tot, in, c);
 #pragma unroll
           for (int q = 0; q < kNumSums; ++q) bins.contrib[ch.x * kNumSums + q] = c[q];
         }
@@ -267,9 +275,23 @@ __device__ __forceinline__ void for_each_row(const BinTable& bins, const int32_t
     const int row0 = B.row0 + (task - bins.nchunks - B.task0) * B.rows_per_tile;
     const int nrows = min(B.rows_per_tile, B.row1 - row0);
     const int lc = B.per_lane;
+    In in{};
+    if (lane < nrows) in = pre(row0 + lane);
     const V v = tile_spmv(rp, ci, val, xg, row0, nrows, B.lanes, lc, lane, pol);
-    if (lane < nrows) epi(row0 + lane, v, s);
+    if (lane < nrows) epi(row0 + lane, v, in, s);
   }
+}
+
+struct NoOperands {};
+
+// for_each_row_pf without per-row operands: epi(row, value, acc).
+template <class V, class Epi>
+__device__ __forceinline__ void for_each_row(const BinTable& bins, const int32_t* __restrict__ rp,
+                                             const int32_t* __restrict__ ci, const V* __restrict__ val,
+                                             const V* __restrict__ xg, const LoadPolicy& pol,
+                                             double (&s)[kNumSums], Epi&& epi) {
+  for_each_row_pf(bins, rp, ci, val, xg, pol, s, [](int) { return NoOperands{}; },
+                  [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) { epi(i, v, acc); });
 }
 
 // Sums the first nsums of each thread's v[] over the block in a fixed order (shared-memory

@@ -97,6 +97,30 @@ inline lp_status validate(int32_t m, int32_t n, int64_t nnz, const int64_t* rp, 
   return LP_OK;
 }
 
+// Tile shape of a length class whose longest row has Lc entries: G lanes per row so that a lane
+// reads at most lane_target entries in one pass (G a power of two <= 32), 32 / G rows per pass,
+// and R rows per tile (a power of two, at least one pass's rows, at most 32): a tile takes
+// R * G / 32 passes, and its epilogue runs in R lanes at once.
+struct TileShape {
+  int lanes, rows, per_lane;
+};
+inline TileShape tile_shape(int64_t Lc, int lane_target, int tile_rows) {
+  const int64_t rr = (int64_t)32 * lane_target / Lc;
+  int R0 = (int)(rr < 1 ? 1 : (rr > 32 ? 32 : rr));
+  int p = 1;
+  while (p * 2 <= R0) p *= 2;
+  R0 = p;
+  int R = tile_rows < 1 ? 1 : (tile_rows > 32 ? 32 : tile_rows);
+  p = 1;
+  while (p * 2 <= R) p *= 2;
+  R = p > R0 ? p : R0;
+  TileShape t;
+  t.lanes = 32 / R0;
+  t.rows = R;
+  t.per_lane = (int)((Lc + t.lanes - 1) / t.lanes);
+  return t;
+}
+
 // Range checks of lp_params (shared by lp_create, lp_set_params and lp_batch_create).
 inline lp_status check_params(const lp_params& p) {
   if (!(p.gamma >= 0.0 && p.gamma <= 1.0)) return fail(LP_ERR_INVALID_ARG, "gamma must be in [0, 1]");
@@ -119,6 +143,7 @@ inline lp_status check_params(const lp_params& p) {
   if (p.fp32_patience < 0) return fail(LP_ERR_INVALID_ARG, "fp32_patience must be >= 0");
   if (p.batch_local_nnz < 0) return fail(LP_ERR_INVALID_ARG, "batch_local_nnz must be >= 0");
   if (p.rescale < 0 || p.rescale > 1) return fail(LP_ERR_INVALID_ARG, "rescale must be 0 or 1");
+  if (p.tile_rows < 0 || p.tile_rows > 32) return fail(LP_ERR_INVALID_ARG, "tile_rows must be in [0, 32]");
   return LP_OK;
 }
 

@@ -52,8 +52,12 @@ __global__ void __launch_bounds__(kThreads, 3) k1_rows(RowArgsT<V> a) {
   const V* __restrict__ xh = (ctl->t & 1) ? a.xh1 : a.xh0;
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const LoadPolicy pol = make_policy();
-  for_each_row(a.bins, a.rp, a.ci, a.val, xh, pol, s,
-               [&](int i, V v, double (&acc)[kNumSums]) { row_epilogue(a, st, i, v, acc); });
+  for_each_row_pf(a.bins, a.rp, a.ci, a.val, xh, pol, s,
+                  [&](int i) {
+                    row_prefetch(a, st, i);
+                    return NoOperands{};
+                  },
+                  [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) { row_epilogue(a, st, i, v, acc); });
   const int nsums = st.check ? 5 : 3;
   if (!block_sums_last(s, nsums, a.partials, &ctl->count1)) return;
   double tot[kNumSums];
@@ -70,8 +74,12 @@ __global__ void __launch_bounds__(kThreads, 3) k2_cols(ColArgsT<V> a) {
   const ColStepT<V> st = col_step(*ctl, a);
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const LoadPolicy pol = make_policy();
-  for_each_row(a.bins, a.rp, a.ci, a.val, a.yh, pol, s,
-               [&](int j, V u, double (&acc)[kNumSums]) { col_epilogue(a, st, j, u, acc); });
+  for_each_row_pf(a.bins, a.rp, a.ci, a.val, a.yh, pol, s,
+                  [&](int j) {
+                    col_prefetch(a, st, j);
+                    return NoOperands{};
+                  },
+                  [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) { col_epilogue(a, st, j, u, acc); });
   const int nsums = st.check ? 5 : 2;
   if (!block_sums_last(s, nsums, a.partials, &ctl->count2)) return;
   double tot[kNumSums];
@@ -118,8 +126,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_loop(RowArgsT<V> ra, ColArgsT<V
     const RowStep st = rst;
     const V* __restrict__ xh = (sc.t & 1) ? ra.xh1 : ra.xh0;
     double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for_each_row(ra.bins, ra.rp, ra.ci, ra.val, xh, pol, s,
-                 [&](int i, V v, double (&acc)[kNumSums]) { row_epilogue(ra, st, i, v, acc); });
+    for_each_row_pf(ra.bins, ra.rp, ra.ci, ra.val, xh, pol, s,
+                    [&](int i) {
+                      row_prefetch(ra, st, i);
+                      return NoOperands{};
+                    },
+                    [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) { row_epilogue(ra, st, i, v, acc); });
     const int nr = st.check ? 5 : 3;
     store_block_partials(s, nr, part_rows);
     grid.sync();
@@ -133,8 +145,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_loop(RowArgsT<V> ra, ColArgsT<V
     __syncthreads();
     const ColStepT<V> cs = cst;
     double s2[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for_each_row(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, s2,
-                 [&](int j, V u, double (&acc)[kNumSums]) { col_epilogue(ca, cs, j, u, acc); });
+    for_each_row_pf(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, s2,
+                    [&](int j) {
+                      col_prefetch(ca, cs, j);
+                      return NoOperands{};
+                    },
+                    [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) { col_epilogue(ca, cs, j, u, acc); });
     const int nc = cs.check ? 5 : 2;
     store_block_partials(s2, nc, part_cols);
     grid.sync();

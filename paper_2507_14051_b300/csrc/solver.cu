@@ -102,10 +102,9 @@ namespace {
 
 // Schedule over rows already sorted by decreasing length class.  The leading rows longer than
 // kLongRowMin become chunk tasks of kChunkNnz entries.  Each remaining length class becomes a
-// bin whose warp task is a tile of R = min(32, 32 * lane_target / Lc) rows (Lc the class's
-// longest length) read in a single pass with G = 32 / R lanes per row, i.e. at most
-// lane_target entries per lane.
-BinTable make_bins(const std::vector<int32_t>& rp, int lane_target, std::vector<int4>& chunks) {
+// bin of tiles shaped by tile_shape: G lanes per row (at most lane_target entries per lane and
+// pass) and R rows per tile.
+BinTable make_bins(const std::vector<int32_t>& rp, int lane_target, int tile_rows, std::vector<int4>& chunks) {
   BinTable bt{};
   const int32_t rows = (int32_t)rp.size() - 1;
   int32_t r = 0;
@@ -123,20 +122,15 @@ BinTable make_bins(const std::vector<int32_t>& rp, int lane_target, std::vector<
     const int cls = length_class(rp[r + 1] - rp[r]);
     int32_t e = r + 1;
     while (e < rows && length_class(rp[e + 1] - rp[e]) == cls) ++e;
-    const int64_t lc = int64_t(1) << cls;
-    int64_t rr = (int64_t)32 * lane_target / lc;
-    int R = (int)(rr < 1 ? 1 : (rr > 32 ? 32 : rr));
-    int Rp = 1;
-    while (Rp * 2 <= R) Rp *= 2;  // a power of two, so that G = 32 / R is one too
-    R = Rp;
+    const TileShape ts = tile_shape(int64_t(1) << cls, lane_target, tile_rows);
     Bin& b = bt.bin[bt.nbins++];
     b.row0 = r;
     b.row1 = e;
-    b.lanes = 32 / R;
-    b.rows_per_tile = R;
+    b.lanes = ts.lanes;
+    b.rows_per_tile = ts.rows;
     b.task0 = task;
-    b.per_lane = (int32_t)((lc + b.lanes - 1) / b.lanes);
-    task += (e - r + R - 1) / R;
+    b.per_lane = ts.per_lane;
+    task += (e - r + ts.rows - 1) / ts.rows;
     r = e;
   }
   bt.ntasks = task;
@@ -377,8 +371,8 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
       valT[pos] = valA[q];
     }
   std::vector<int4> chunksA, chunksT;
-  h->binsA = make_bins(rpA, h->prm.lane_target, chunksA);
-  h->binsT = make_bins(rpT, h->prm.lane_target, chunksT);
+  h->binsA = make_bins(rpA, h->prm.lane_target, h->prm.tile_rows > 0 ? h->prm.tile_rows : 1, chunksA);
+  h->binsT = make_bins(rpT, h->prm.lane_target, h->prm.tile_rows > 0 ? h->prm.tile_rows : 1, chunksT);
 
   int occA = 0, occT = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, iter_kernels<double>().rows, kThreads, 0));
@@ -558,6 +552,7 @@ lp_status lp_default_params(lp_params* p) {
   p->switch_tol = 1e-5;
   p->fp32_patience = 32;
   p->rescale = 0;
+  p->tile_rows = 0;
   p->batch_local_nnz = 16384;
   return LP_OK;
 }
@@ -626,6 +621,7 @@ lp_status lp_set_params(lp_handle h, const lp_params* p) {
   h->prm.pc_alpha = old.pc_alpha;
   h->prm.lane_target = old.lane_target;  // the bin tables are built at lp_create
   h->prm.precision = old.precision;      // the FP32 buffers are made at lp_create
+  h->prm.tile_rows = old.tile_rows;      // so are the tiles
   if (p->power_seed != old.power_seed || p->power_tol != old.power_tol ||
       p->power_max_iter != old.power_max_iter)
     h->power_valid = false;

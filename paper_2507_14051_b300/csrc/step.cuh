@@ -70,19 +70,48 @@ __device__ __forceinline__ RowStep row_step(const Ctl& c) {
   return st;
 }
 
+// Operands of the row epilogue that depend only on the row: loaded before the row's SpMV so
+// that their latency overlaps it.
 template <class V>
-__device__ __forceinline__ void row_epilogue(const RowArgsT<V>& a, const RowStep& st, int i, V v,
-                                             double (&acc)[kNumSums]) {
+struct RowIn {
+  V y0, yh, y, axh, ax, ax0, lo, hi;
+};
+
+template <class V>
+__device__ __forceinline__ RowIn<V> row_load(const RowArgsT<V>& a, const RowStep& st, int i) {
+  RowIn<V> in;
+  if (st.mode == 0) {
+    in.y0 = a.y0[i];
+    in.yh = a.yh[i];
+    in.y = a.y[i];
+    in.axh = a.axh[i];
+    in.ax = a.ax[i];
+    in.ax0 = a.ax0[i];
+  } else if (st.mode == 1) {
+    in.yh = a.yh[i];
+    in.axh = a.axh[i];
+    in.y0 = in.y = in.ax = in.ax0 = V(0);
+  } else {
+    in.y0 = in.yh = in.y = in.axh = in.ax = in.ax0 = V(0);
+  }
+  in.lo = a.lc[i];
+  in.hi = a.uc[i];
+  return in;
+}
+
+template <class V>
+__device__ __forceinline__ void row_finish(const RowArgsT<V>& a, const RowStep& st, int i, V v,
+                                           const RowIn<V>& in, double (&acc)[kNumSums]) {
   const V ha = (V)st.ha, hb = (V)st.hb, he = (V)st.he;
   const V sigma = (V)st.sigma, inv_sigma = (V)st.inv_sigma;
   V yi, axi, y0i;
   if (st.mode == 0) {
-    y0i = a.y0[i];
-    yi = fmav(ha, a.yh[i], fmav(hb, a.y[i], he * y0i));
-    axi = fmav(ha, a.axh[i], fmav(hb, a.ax[i], he * a.ax0[i]));
+    y0i = in.y0;
+    yi = fmav(ha, in.yh, fmav(hb, in.y, he * y0i));
+    axi = fmav(ha, in.axh, fmav(hb, in.ax, he * in.ax0));
   } else if (st.mode == 1) {
-    yi = a.yh[i];
-    axi = a.axh[i];
+    yi = in.yh;
+    axi = in.axh;
     y0i = yi;
     a.y0[i] = yi;
     a.ax0[i] = axi;
@@ -91,7 +120,7 @@ __device__ __forceinline__ void row_epilogue(const RowArgsT<V>& a, const RowStep
     axi = V(0);
     y0i = V(0);
   }
-  const V lo = a.lc[i], hi = a.uc[i];
+  const V lo = in.lo, hi = in.hi;
   const V w = fmav(V(2), v, -axi);  // A(2 xhat - x)
   const V sv = fmav(-yi, inv_sigma, w);
   const V yn = sigma * (clampd(sv, lo, hi) - sv);
@@ -112,6 +141,30 @@ __device__ __forceinline__ void row_epilogue(const RowArgsT<V>& a, const RowStep
   }
   a.yh[i] = yn;
   a.axh[i] = v;
+}
+
+template <class V>
+__device__ __forceinline__ void row_epilogue(const RowArgsT<V>& a, const RowStep& st, int i, V v,
+                                             double (&acc)[kNumSums]) {
+  row_finish(a, st, i, v, row_load(a, st, i), acc);
+}
+
+// Issued before the row's SpMV: brings the row epilogue's operands to L1 while the SpMV runs,
+// without holding registers across it.
+template <class V>
+__device__ __forceinline__ void row_prefetch(const RowArgsT<V>& a, const RowStep& st, int i) {
+  if (st.mode == 0) {
+    prefetch_l1(a.y0 + i);
+    prefetch_l1(a.y + i);
+    prefetch_l1(a.ax + i);
+    prefetch_l1(a.ax0 + i);
+  }
+  if (st.mode != 2) {
+    prefetch_l1(a.yh + i);
+    prefetch_l1(a.axh + i);
+  }
+  prefetch_l1(a.lc + i);
+  prefetch_l1(a.uc + i);
 }
 
 // Scalar control after the row phase of iteration c.t, on totals tot[0..2] (and tot[3..4] on
@@ -196,10 +249,33 @@ __device__ __forceinline__ ColStepT<V> col_step(const Ctl& c, const ColArgsT<V>&
 }
 
 template <class V>
-__device__ __forceinline__ void col_epilogue(const ColArgsT<V>& a, const ColStepT<V>& st, int j, V u,
-                                             double (&acc)[kNumSums]) {
+struct ColIn {
+  V xc, x0, x, aty, aty0, c, lo, hi;
+};
+
+template <class V>
+__device__ __forceinline__ ColIn<V> col_load(const ColArgsT<V>& a, const ColStepT<V>& st, int j) {
+  ColIn<V> in;
+  in.xc = st.xc[j];
+  if (st.restart) {
+    in.x0 = in.x = in.aty = in.aty0 = V(0);
+  } else {
+    in.x0 = a.x0[j];
+    in.x = a.x[j];
+    in.aty = a.aty[j];
+    in.aty0 = a.aty0[j];
+  }
+  in.c = a.c[j];
+  in.lo = a.lv[j];
+  in.hi = a.uv[j];
+  return in;
+}
+
+template <class V>
+__device__ __forceinline__ void col_finish(const ColArgsT<V>& a, const ColStepT<V>& st, int j, V u,
+                                           const ColIn<V>& in, double (&acc)[kNumSums]) {
   const V ha = (V)st.ha, hb = (V)st.hb, he = (V)st.he, tau = (V)st.tau;
-  const V xc = st.xc[j];
+  const V xc = in.xc;
   V xj, atyj, x0j;
   if (st.restart) {
     xj = xc;
@@ -208,11 +284,11 @@ __device__ __forceinline__ void col_epilogue(const ColArgsT<V>& a, const ColStep
     a.x0[j] = xc;
     a.aty0[j] = u;
   } else {
-    x0j = a.x0[j];
-    xj = fmav(ha, xc, fmav(hb, a.x[j], he * x0j));
-    atyj = fmav(ha, u, fmav(hb, a.aty[j], he * a.aty0[j]));
+    x0j = in.x0;
+    xj = fmav(ha, xc, fmav(hb, in.x, he * x0j));
+    atyj = fmav(ha, u, fmav(hb, in.aty, he * in.aty0));
   }
-  const V cj = a.c[j], lo = a.lv[j], hi = a.uv[j];
+  const V cj = in.c, lo = in.lo, hi = in.hi;
   const V xn = clampd(fmav(-tau, cj - atyj, xj), lo, hi);
   const V dx = xj - xn;
   acc_fma(acc[0], dx, dx);
@@ -231,6 +307,26 @@ __device__ __forceinline__ void col_epilogue(const ColArgsT<V>& a, const ColStep
   a.x[j] = xj;
   a.aty[j] = atyj;
   st.xn[j] = xn;
+}
+
+template <class V>
+__device__ __forceinline__ void col_epilogue(const ColArgsT<V>& a, const ColStepT<V>& st, int j, V u,
+                                             double (&acc)[kNumSums]) {
+  col_finish(a, st, j, u, col_load(a, st, j), acc);
+}
+
+template <class V>
+__device__ __forceinline__ void col_prefetch(const ColArgsT<V>& a, const ColStepT<V>& st, int j) {
+  prefetch_l1(st.xc + j);
+  if (!st.restart) {
+    prefetch_l1(a.x0 + j);
+    prefetch_l1(a.x + j);
+    prefetch_l1(a.aty + j);
+    prefetch_l1(a.aty0 + j);
+  }
+  prefetch_l1(a.c + j);
+  prefetch_l1(a.lv + j);
+  prefetch_l1(a.uv + j);
 }
 
 // Scalar control after the column phase: carries the x-side sums to the next residual, runs

@@ -171,7 +171,7 @@ def test_batch_create_rejects_invalid_arguments():
     assert L.lp_batch_create(0, None, None, None, None, None, None, None, None, None, None, None, None,
                              None, None, C.byref(h)) == lpx.LP_ERR_INVALID_ARG
     with pytest.raises(lpx.LPError) as e:
-        lpx.BatchSolver(lps, lane_target=[8, 0, 8])
+        lpx.BatchSolver(lps, tiles=[(8, 1), (0, 1), (8, 1)])
     assert e.value.code == lpx.LP_ERR_INVALID_ARG
     assert L.lp_batch_solve(None, 1e-8, 10, None) == lpx.LP_ERR_INVALID_ARG
     assert L.lp_batch_get(None, 0, None, None, None, None, None) == lpx.LP_ERR_INVALID_ARG
@@ -193,10 +193,10 @@ def test_tune_rejects_invalid_input_before_any_cuda_call():
     bad = lp.col_idx.copy()
     bad[0] = lp.n + 5
     L = lpx.load()
-    best = C.c_int32(0)
+    lt, tr = C.c_int32(0), C.c_int32(0)
     rp = np.ascontiguousarray(lp.row_ptr, np.int64)
     v = np.ascontiguousarray(lp.val)
-    assert L.lp_tune_lane_target(lp.m, lp.n, lp.nnz, rp.ctypes.data, bad.ctypes.data, v.ctypes.data, None,
-                                 C.byref(best), None) == lpx.LP_ERR_INVALID_INPUT
-    assert L.lp_tune_lane_target(lp.m, lp.n, lp.nnz, rp.ctypes.data, bad.ctypes.data, v.ctypes.data, None,
-                                 None, None) == lpx.LP_ERR_INVALID_ARG
+    assert L.lp_tune_schedule(lp.m, lp.n, lp.nnz, rp.ctypes.data, bad.ctypes.data, v.ctypes.data, None,
+                              C.byref(lt), C.byref(tr), None) == lpx.LP_ERR_INVALID_INPUT
+    assert L.lp_tune_schedule(lp.m, lp.n, lp.nnz, rp.ctypes.data, bad.ctypes.data, v.ctypes.data, None,
+                              None, None, None) == lpx.LP_ERR_INVALID_ARG

@@ -200,22 +200,22 @@ def test_batch_time_loop(cuda_device):
 def test_tuner_picks_the_fastest_candidate_and_caches(cuda_device, tmp_path):
     lp = gen.miplib_like(3, 4000, 8000, 2000)
     cache = str(tmp_path / "schedules.txt")
-    best, ms = lpx.lp_tune_lane_target(lp, cache, timings=True)
-    assert best == [2, 4, 8, 16, 32][int(np.argmin(ms))]
+    best, ms = lpx.lp_tune_schedule(lp, cache, timings=True)
+    assert best == lpx.TUNE_CANDIDATES[int(np.argmin(ms))]
     assert np.all(ms > 0)
-    lines = open(cache).read().split("\n")
-    assert len([ln for ln in lines if ln.strip()]) == 1 and lines[0].endswith(f" {best}")
-    assert lpx.lp_tune_lane_target(lp, cache) == best       # from the cache: no new line
+    lines = [ln for ln in open(cache).read().split("\n") if ln.strip()]
+    assert len(lines) == 1 and lines[0].endswith(f" {100 * best[0] + best[1]}")
+    assert lpx.lp_tune_schedule(lp, cache) == best       # from the cache: no new line
     assert len([ln for ln in open(cache).read().split("\n") if ln.strip()]) == 1
 
 
 @pytest.mark.parametrize("local", [0, 10 ** 9])
 def test_batch_with_per_instance_schedules_matches_oracle(cuda_device, local):
-    """Each instance's tile schedule changes only how its rows are split among lanes."""
+    """Each instance's tile schedule changes only how its rows are split among lanes and tiles."""
     lps = small_batch(9, count=6)
-    lanes = [2, 32, 8, 4, 16, 1]
+    tiles = [(2, 1), (32, 32), (8, 4), (4, 32), (16, 8), (1, 2)]
     etas = [o_eta(lp) for lp in lps]
-    with lpx.BatchSolver(lps, eta=etas, lane_target=lanes, batch_local_nnz=local) as b:
+    with lpx.BatchSolver(lps, eta=etas, tiles=tiles, batch_local_nnz=local) as b:
         b.solve(0.0, 200)
         res = [b.get(k) for k in range(len(lps))]
     for lp, e, g in zip(lps, etas, res):

@@ -177,7 +177,8 @@ def test_small_lp_iterates(cuda_device, seed, iters):
                                      dict(k_p=0.3, k_i=0.05, k_d=0.2), dict(check_every=1),
                                      dict(check_every=7, unroll=3), dict(lane_target=1), dict(lane_target=16),
                                      dict(persistent=0), dict(persistent=0, check_every=5, unroll=2),
-                                     dict(persistent=1, unroll=5)])
+                                     dict(persistent=1, unroll=5), dict(tile_rows=32), dict(tile_rows=4, lane_target=2),
+                                     dict(tile_rows=32, persistent=0)])
 def test_variants_iterates(cuda_device, variant):
     compare_fixed(gen.free_and_boxed_mix(3, 300, 450), 400, **variant)
 
