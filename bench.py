@@ -37,8 +37,8 @@ sys.path.insert(0, ROOT)
 METRIC = "time to 1e-8 rel KKT, PDHG iter/s, SpMV+update HBM GB/s vs peak"
 FP64_NOMINAL_GOPS = 625.0  # 1.25 TFLOP/s FP64 per GPU (nominal) / 2 flops per DFMA
 FP64_MEASURED_GOPS = 474.0  # DFMA/DADD/DMUL issue rate measured by a register-only loop on a B300
-KERNEL_SOURCES = ("paper_2507_14051_b300/csrc/iterate.cu", "paper_2507_14051_b300/csrc/device.cuh",
-                  "paper_2507_14051_b300/csrc/kernels.cuh")
+KERNEL_SOURCES = tuple(sorted(os.path.relpath(p, ROOT) for p in
+                             __import__("glob").glob(os.path.join(ROOT, "paper_2507_14051_b300", "csrc", "*.cu*"))))
 
 
 def parse():

@@ -25,7 +25,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + [os.path.join(ROOT, "include", "lp.h")]
+    deps = (sources() + glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + glob.glob(os.path.join(HERE, "csrc", "*.h"))
+            + glob.glob(os.path.join(ROOT, "include", "*.h")))
     return any(os.path.getmtime(d) > t for d in deps)
 
 

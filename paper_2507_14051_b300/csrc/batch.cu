@@ -495,9 +495,8 @@ __global__ void __launch_bounds__(kThreads, 2) kb_block_loop(BatchArgs<V> a, con
       double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
       for (int j = warp; j < I.nta; j += kWarps) {
         const int4 td = a.tasksA[I.ta0 + j];
-        if (lane < td.y) row_prefetch(a.ra, st, td.x + lane);
-        const V v = tile_spmv(a.ra.rp, a.ra.ci, a.ra.val, xg, td.x, td.y, task_lanes(td), task_per_lane(td),
-                              lane, pol);
+        const V v = tile_spmv<V, true>(a.ra.rp, a.ra.ci, a.ra.val, xg, td.x, td.y, task_lanes(td),
+                                       task_per_lane(td), lane, pol);
         if (lane < td.y) row_epilogue(a.ra, st, td.x + lane, v, s);
       }
       const int nr = st.check ? 5 : 3;
@@ -511,9 +510,8 @@ __global__ void __launch_bounds__(kThreads, 2) kb_block_loop(BatchArgs<V> a, con
       double s2[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
       for (int j = warp; j < I.ntt; j += kWarps) {
         const int4 td = a.tasksT[I.tt0 + j];
-        if (lane < td.y) col_prefetch(a.ca, cs, td.x + lane);
-        const V u = tile_spmv(a.ca.rp, a.ca.ci, a.ca.val, a.ca.yh, td.x, td.y, task_lanes(td),
-                              task_per_lane(td), lane, pol);
+        const V u = tile_spmv<V, true>(a.ca.rp, a.ca.ci, a.ca.val, a.ca.yh, td.x, td.y, task_lanes(td),
+                                       task_per_lane(td), lane, pol);
         if (lane < td.y) col_epilogue(a.ca, cs, td.x + lane, u, s2);
       }
       const int nc = cs.check ? 5 : 2;

@@ -135,15 +135,16 @@ template <class T>
 __device__ __forceinline__ void prefetch_l1(const T* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
-// Gathered vector entries: L2 evict-last.
+// Gathered vector entries: L2 evict-last.  A coherent load (not .nc): the persistent kernels
+// gather vectors that their previous phase wrote, after a grid or block barrier.
 __device__ __forceinline__ double ld_gather(const double* p, uint64_t pol) {
   double v;
-  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
   return v;
 }
 __device__ __forceinline__ float ld_gather(const float* p, uint64_t pol) {
   float v;
-  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
   return v;
 }
 
@@ -158,9 +159,16 @@ __device__ __forceinline__ double start_entry(uint64_t seed, uint64_t i) {
   return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
 }
 
+// Read-only loads that allocate in L1: for data a block re-reads every iteration (the
+// block-local loop over a small instance).
+__device__ __forceinline__ double ld_cached(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_cached(const float* p) { return __ldg(p); }
+__device__ __forceinline__ int32_t ld_cached(const int32_t* p) { return __ldg(p); }
+
 // Partial dot product of one lane: entries b+first, b+first+stride, ... < e, loaded ILP at a
 // time (all loads of a batch issued before any is used) and accumulated in entry order.
-template <int ILP, class V>
+// kCached: matrix loads through L1 (ld_cached) instead of streaming past it.
+template <int ILP, class V, bool kCached = false>
 __device__ __forceinline__ V strided_dot_n(const int32_t* __restrict__ ci, const V* __restrict__ val,
                                            const V* __restrict__ xg, int first, int e, int stride,
                                            const LoadPolicy& pol) {
@@ -172,8 +180,13 @@ __device__ __forceinline__ V strided_dot_n(const int32_t* __restrict__ ci, const
     for (int u = 0; u < ILP; ++u) {
       const int k = k0 + u * stride;
       if (k < e) {
-        v[u] = ld_stream(val + k, pol.stream);
-        c[u] = ld_stream(ci + k, pol.stream);
+        if (kCached) {
+          v[u] = ld_cached(val + k);
+          c[u] = ld_cached(ci + k);
+        } else {
+          v[u] = ld_stream(val + k, pol.stream);
+          c[u] = ld_stream(ci + k, pol.stream);
+        }
       } else {
         v[u] = V(0);
         c[u] = -1;
@@ -192,21 +205,21 @@ __device__ __forceinline__ V strided_dot_n(const int32_t* __restrict__ ci, const
 // The same with the batch sized to `per_lane`, the most entries any lane of the warp has
 // (uniform across the warp): short rows then issue no FP64 fma for absent entries, which on
 // this GPU's FP64 unit would cost as much as real ones.
-template <class V>
+template <class V, bool kCached = false>
 __device__ __forceinline__ V strided_dot(const int32_t* __restrict__ ci, const V* __restrict__ val,
                                          const V* __restrict__ xg, int first, int e, int stride,
                                          int per_lane, const LoadPolicy& pol) {
-  if (per_lane <= 1) return strided_dot_n<1>(ci, val, xg, first, e, stride, pol);
-  if (per_lane <= 2) return strided_dot_n<2>(ci, val, xg, first, e, stride, pol);
-  if (per_lane <= 4) return strided_dot_n<4>(ci, val, xg, first, e, stride, pol);
-  return strided_dot_n<kIlp>(ci, val, xg, first, e, stride, pol);
+  if (per_lane <= 1) return strided_dot_n<1, V, kCached>(ci, val, xg, first, e, stride, pol);
+  if (per_lane <= 2) return strided_dot_n<2, V, kCached>(ci, val, xg, first, e, stride, pol);
+  if (per_lane <= 4) return strided_dot_n<4, V, kCached>(ci, val, xg, first, e, stride, pol);
+  return strided_dot_n<kIlp, V, kCached>(ci, val, xg, first, e, stride, pol);
 }
 
 // Dot products of the rows [row0, row0 + nrows) (nrows <= 32) of a CSR matrix with xg.
 // G lanes per row, 32/G rows per pass; lane L returns the value of row L (garbage for
 // L >= nrows).  Summation: each lane accumulates its strided entries in order, then a
 // fixed xor butterfly over the G lanes (deterministic).
-template <class V>
+template <class V, bool kCached = false>
 __device__ __forceinline__ V tile_spmv(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                        const V* __restrict__ val, const V* __restrict__ xg, int row0,
                                        int nrows, int G, int per_lane, int lane, const LoadPolicy& pol) {
@@ -224,7 +237,7 @@ __device__ __forceinline__ V tile_spmv(const int32_t* __restrict__ rp, const int
     const int q = p * rpp + g;  // row of this lane's group in this pass
     const int b = __shfl_sync(kFull, my_b, q & 31);
     const int e = __shfl_sync(kFull, my_e, q & 31);
-    V acc = q < nrows ? strided_dot(ci, val, xg, b + sub, e, G, per_lane, pol) : V(0);
+    V acc = q < nrows ? strided_dot<V, kCached>(ci, val, xg, b + sub, e, G, per_lane, pol) : V(0);
     for (int off = G >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
     const V v = __shfl_sync(kFull, acc, (lane % rpp) * G);
     if (lane / rpp == p) mine = v;
