@@ -509,8 +509,19 @@ def run_batch(args):
     # roofline of the grid loop kernel (all grid instances running, 16 iterations per launch)
     hbm_peak, peak_src = load_peaks()
     ms64, per = b.time_loop(64, fp64=True, stream=sp)
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            tj = json.load(f)
+        if tj.get("source_digest") == source_digest():
+            per_nnz_it = tj["kb_loop"]["batch"]["dram_bytes_per_grid_nnz_iteration"]
+            traffic = per_nnz_it * sum(lp.nnz for lp in lps if lp.nnz > local_nnz) * 16
+    except (OSError, ValueError, KeyError):
+        traffic = None
     roof = {"bound": "hbm", "kernel": "kb_loop<double>", "unit": "GB/s", "peak": hbm_peak,
-            "traffic": None, "iters_per_launch": per, "ms_per_launch": ms64}
+            "traffic": traffic, "iters_per_launch": per, "ms_per_launch": ms64,
+            "traffic_note": "ncu DRAM bytes per grid nonzero and iteration on a 64-instance batch, "
+                            "scaled to this batch's grid nonzeros x 16 iterations"}
     roof["achieved"] = batch_work(lps, local_nnz, 8) * per / (ms64 * 1e-3) / 1e9
     roof["frac"] = roof["achieved"] / hbm_peak
     if args.precision != 0:
