@@ -33,6 +33,13 @@ struct Sched {
   int rho;
 };
 
+// Iteration of a kernel = clk->t0 + its offset in the segment; clk->K = the map's length (the
+// seeds enter at its last iteration).  One captured segment serves every segment this way.
+__global__ void kd_set_clock(DiffClock* clk, int64_t t0, int64_t K) {
+  clk->t0 = t0;
+  clk->K = K;
+}
+
 // Frozen schedule of instance k at iteration t from its trace row (r, omega, restart, k_t).
 __device__ __forceinline__ Sched sched_at(const double* __restrict__ trace, int64_t cap, int k, int64_t t,
                                           const double* __restrict__ eta, double gamma) {
@@ -59,11 +66,12 @@ __device__ __forceinline__ uint8_t clamp_code(double v, double lo, double hi) {
 
 // Forward, column side of iteration t: xhat, xbar (and the codes of a).
 __global__ void kd_col_fwd(int64_t n, const int32_t* __restrict__ icol, const double* __restrict__ trace,
-                           int64_t cap, const double* __restrict__ eta, double gamma, int64_t t,
+                           int64_t cap, const double* __restrict__ eta, double gamma, const DiffClock* __restrict__ clk, int32_t off,
                            const double* __restrict__ c, const double* __restrict__ lv,
                            const double* __restrict__ uv, const double* __restrict__ x,
                            const double* __restrict__ aty, double* __restrict__ xh, double* __restrict__ xbar,
                            uint8_t* __restrict__ code) {
+  const int64_t t = clk->t0 + off;
   GRID_STRIDE(j, n) {
     const Sched s = sched_at(trace, cap, icol[j], t, eta, gamma);
     const double xj = x[j];
@@ -78,10 +86,11 @@ __global__ void kd_col_fwd(int64_t n, const int32_t* __restrict__ icol, const do
 
 // Forward, row side of iteration t: yhat, the y update (Halpern or restart) and the codes of s.
 __global__ void kd_row_fwd(int64_t m, const int32_t* __restrict__ irow, const double* __restrict__ trace,
-                           int64_t cap, const double* __restrict__ eta, double gamma, int64_t t,
+                           int64_t cap, const double* __restrict__ eta, double gamma, const DiffClock* __restrict__ clk, int32_t off,
                            const double* __restrict__ lc, const double* __restrict__ uc,
                            const double* __restrict__ v, double* __restrict__ y, double* __restrict__ y0,
                            double* __restrict__ yh, uint8_t* __restrict__ code) {
+  const int64_t t = clk->t0 + off;
   GRID_STRIDE(i, m) {
     const Sched s = sched_at(trace, cap, irow[i], t, eta, gamma);
     const double yi = y[i];
@@ -101,8 +110,9 @@ __global__ void kd_row_fwd(int64_t m, const int32_t* __restrict__ irow, const do
 
 // Forward: the x update of iteration t (after A xbar has been taken).
 __global__ void kd_col_upd(int64_t n, const int32_t* __restrict__ icol, const double* __restrict__ trace,
-                           int64_t cap, const double* __restrict__ eta, double gamma, int64_t t,
+                           int64_t cap, const double* __restrict__ eta, double gamma, const DiffClock* __restrict__ clk, int32_t off,
                            const double* __restrict__ xh, double* __restrict__ x, double* __restrict__ x0) {
+  const int64_t t = clk->t0 + off;
   GRID_STRIDE(j, n) {
     const Sched s = sched_at(trace, cap, icol[j], t, eta, gamma);
     const double h = xh[j];
@@ -118,10 +128,11 @@ __global__ void kd_col_upd(int64_t n, const int32_t* __restrict__ icol, const do
 // Adjoint, row side of iteration t (first half): from (ly, ly0) of (y', y0') to lv = ls and the
 // partial adjoints of (y, y0); accumulates the row-bound gradients.
 __global__ void kd_row_bwd(int64_t m, const int32_t* __restrict__ irow, const double* __restrict__ trace,
-                           int64_t cap, const double* __restrict__ eta, double gamma, int64_t t,
+                           int64_t cap, const double* __restrict__ eta, double gamma, const DiffClock* __restrict__ clk, int32_t off,
                            const uint8_t* __restrict__ code, const double* __restrict__ seed,
                            double* __restrict__ ly, double* __restrict__ ly0, double* __restrict__ lv,
                            double* __restrict__ glc, double* __restrict__ guc) {
+  const int64_t t = clk->t0 + off;
   GRID_STRIDE(i, m) {
     const Sched s = sched_at(trace, cap, irow[i], t, eta, gamma);
     const double a_y = ly[i], a_y0 = ly0[i];
@@ -135,7 +146,7 @@ __global__ void kd_row_bwd(int64_t m, const int32_t* __restrict__ irow, const do
       lyp = s.be * a_y;
       ly0p = a_y0 + s.ep * a_y;
     }
-    if (seed) lyh += seed[i];
+    if (seed && t == clk->K - 1) lyh += seed[i];
     const uint8_t cd = code[i];
     const double ls = cd == 0 ? 0.0 : -s.sigma * lyh;
     if (cd == 1) glc[i] += s.sigma * lyh;
@@ -149,11 +160,12 @@ __global__ void kd_row_bwd(int64_t m, const int32_t* __restrict__ irow, const do
 // Adjoint, column side of iteration t: from (lx, lx0) and lxbar = A^T lv to the adjoints of
 // (x, x0) and laty = tau la; accumulates the gradients of c and the variable bounds.
 __global__ void kd_col_bwd(int64_t n, const int32_t* __restrict__ icol, const double* __restrict__ trace,
-                           int64_t cap, const double* __restrict__ eta, double gamma, int64_t t,
+                           int64_t cap, const double* __restrict__ eta, double gamma, const DiffClock* __restrict__ clk, int32_t off,
                            const uint8_t* __restrict__ code, const double* __restrict__ seed,
                            const double* __restrict__ lxbar, double* __restrict__ lx, double* __restrict__ lx0,
                            double* __restrict__ laty, double* __restrict__ gc, double* __restrict__ glv,
                            double* __restrict__ guv) {
+  const int64_t t = clk->t0 + off;
   GRID_STRIDE(j, n) {
     const Sched s = sched_at(trace, cap, icol[j], t, eta, gamma);
     const double a_x = lx[j], a_x0 = lx0[j];
@@ -167,7 +179,7 @@ __global__ void kd_col_bwd(int64_t n, const int32_t* __restrict__ icol, const do
       lxp = s.be * a_x;
       lx0p = a_x0 + s.ep * a_x;
     }
-    if (seed) lxh += seed[j];
+    if (seed && t == clk->K - 1) lxh += seed[j];
     const double lb = lxbar[j];
     lxh += 2.0 * lb;
     lxp -= lb;
@@ -266,7 +278,8 @@ lp_status diff_buffers(lp_batch* h) {
     return e;
   };
   const size_t n = (size_t)h->sum_n, m = (size_t)h->sum_m;
-  CK(get(&d->irow, m)); CK(get(&d->icol, n));
+  CK(get(&d->irow, m)); CK(get(&d->icol, n)); CK(get(&d->clk, 1));
+  CK(cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking));
   for (double** p : {&d->x, &d->x0, &d->xh, &d->xbar, &d->aty, &d->lx, &d->lx0, &d->lxbar, &d->laty, &d->sx,
                      &d->gc, &d->glv, &d->guv})
     CK(get(p, n));
@@ -294,42 +307,42 @@ lp_status grow(T** p, int64_t* cap, int64_t need) {
   return LP_OK;
 }
 
-// One forward iteration t of every instance on the diff state.  code_x / code_y: where to
-// store the clamp codes (NULL: not stored).
-lp_status forward_step(lp_batch* h, int64_t t, uint8_t* code_x, uint8_t* code_y, cudaStream_t s) {
+// One forward iteration (clock t0 + off) of every instance on the diff state.  code_x / code_y:
+// where to store the clamp codes (NULL: not stored).
+lp_status forward_step(lp_batch* h, int32_t off, uint8_t* code_x, uint8_t* code_y, cudaStream_t s) {
   Diff* d = h->diff;
   const int64_t n = h->sum_n, m = h->sum_m;
   const double g = h->prm.gamma;
   const int gA = grid_for(h->ntA, kWarps, 8 * h->num_sms), gT = grid_for(h->ntT, kWarps, 8 * h->num_sms);
   if (h->ntT > 0) kb_spmv<double><<<gT, kThreads, 0, s>>>(h->tasksT, h->ntT, h->rpT, h->ciT, h->valT, d->y, d->aty);
   if (n > 0)
-    kd_col_fwd<<<vgrid(h, n), 256, 0, s>>>(n, d->icol, h->trace, h->trace_cap, h->d_eta, g, t, h->c, h->lv, h->uv,
+    kd_col_fwd<<<vgrid(h, n), 256, 0, s>>>(n, d->icol, h->trace, h->trace_cap, h->d_eta, g, d->clk, off, h->c, h->lv, h->uv,
                                            d->x, d->aty, d->xh, d->xbar, code_x);
   if (h->ntA > 0) kb_spmv<double><<<gA, kThreads, 0, s>>>(h->tasksA, h->ntA, h->rpA, h->ciA, h->valA, d->xbar, d->v);
   if (m > 0)
-    kd_row_fwd<<<vgrid(h, m), 256, 0, s>>>(m, d->irow, h->trace, h->trace_cap, h->d_eta, g, t, h->lc, h->uc, d->v,
+    kd_row_fwd<<<vgrid(h, m), 256, 0, s>>>(m, d->irow, h->trace, h->trace_cap, h->d_eta, g, d->clk, off, h->lc, h->uc, d->v,
                                            d->y, d->y0, d->yh, code_y);
   if (n > 0)
-    kd_col_upd<<<vgrid(h, n), 256, 0, s>>>(n, d->icol, h->trace, h->trace_cap, h->d_eta, g, t, d->xh, d->x, d->x0);
+    kd_col_upd<<<vgrid(h, n), 256, 0, s>>>(n, d->icol, h->trace, h->trace_cap, h->d_eta, g, d->clk, off, d->xh, d->x, d->x0);
   CK(cudaGetLastError());
   return LP_OK;
 }
 
-// One adjoint iteration t (codes of t in code_x / code_y; seeds at the last iteration).
-lp_status backward_step(lp_batch* h, int64_t t, const uint8_t* code_x, const uint8_t* code_y, bool last,
-                        cudaStream_t s) {
+// One adjoint iteration (clock t0 + off; codes of that iteration in code_x / code_y; the seeds
+// enter at the map's last iteration).
+lp_status backward_step(lp_batch* h, int32_t off, const uint8_t* code_x, const uint8_t* code_y, cudaStream_t s) {
   Diff* d = h->diff;
   const int64_t n = h->sum_n, m = h->sum_m;
   const double g = h->prm.gamma;
   const int gA = grid_for(h->ntA, kWarps, 8 * h->num_sms), gT = grid_for(h->ntT, kWarps, 8 * h->num_sms);
   if (m > 0)
-    kd_row_bwd<<<vgrid(h, m), 256, 0, s>>>(m, d->irow, h->trace, h->trace_cap, h->d_eta, g, t, code_y,
-                                           last ? d->sy : nullptr, d->ly, d->ly0, d->lv, d->glc, d->guc);
+    kd_row_bwd<<<vgrid(h, m), 256, 0, s>>>(m, d->irow, h->trace, h->trace_cap, h->d_eta, g, d->clk, off, code_y,
+                                           d->sy, d->ly, d->ly0, d->lv, d->glc, d->guc);
   if (n > 0) {
     if (h->ntT > 0) kb_spmv<double><<<gT, kThreads, 0, s>>>(h->tasksT, h->ntT, h->rpT, h->ciT, h->valT, d->lv, d->lxbar);
     else CK(cudaMemsetAsync(d->lxbar, 0, sizeof(double) * n, s));
-    kd_col_bwd<<<vgrid(h, n), 256, 0, s>>>(n, d->icol, h->trace, h->trace_cap, h->d_eta, g, t, code_x,
-                                           last ? d->sx : nullptr, d->lxbar, d->lx, d->lx0, d->laty, d->gc, d->glv,
+    kd_col_bwd<<<vgrid(h, n), 256, 0, s>>>(n, d->icol, h->trace, h->trace_cap, h->d_eta, g, d->clk, off, code_x,
+                                           d->sx, d->lxbar, d->lx, d->lx0, d->laty, d->gc, d->glv,
                                            d->guv);
   }
   if (m > 0 && h->ntA > 0) {
@@ -369,6 +382,49 @@ lp_status load_ck(lp_batch* h, int64_t q, cudaStream_t s) {
 
 lp_status zero(double* p, int64_t len, cudaStream_t s) {
   if (len > 0) CK(cudaMemsetAsync(p, 0, sizeof(double) * (size_t)len, s));
+  return LP_OK;
+}
+
+// The graph of one segment of len iterations (offsets 0..len-1 of the clock): kind 0 forward,
+// 1 forward storing the clamp codes of offset o at codes + o (n + m), 2 the adjoint from offset
+// len-1 down to 0.  Captured once per (kind, len, codes buffer) and replayed for every segment.
+lp_status segment_graph(lp_batch* h, int kind, int64_t len, cudaGraphExec_t* out) {
+  Diff* d = h->diff;
+  const uint8_t* codes = kind == 0 ? nullptr : d->mx;
+  if (d->seg[kind] && d->seg_len[kind] == len && d->seg_codes[kind] == codes) {
+    *out = d->seg[kind];
+    return LP_OK;
+  }
+  if (d->seg[kind]) {
+    cudaGraphExecDestroy(d->seg[kind]);
+    d->seg[kind] = nullptr;
+  }
+  const size_t n = (size_t)h->sum_n, m = (size_t)h->sum_m;
+  uint8_t* cx = d->mx;
+  uint8_t* cy = d->mx + (size_t)len * n;
+  CK(cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeThreadLocal));
+  lp_status st = LP_OK;
+  for (int64_t o = 0; o < len && st == LP_OK; ++o) {
+    if (kind == 0) st = forward_step(h, (int32_t)o, nullptr, nullptr, d->cap);
+    else if (kind == 1) st = forward_step(h, (int32_t)o, cx + o * n, cy + o * m, d->cap);
+    else {
+      const int64_t q = len - 1 - o;
+      st = backward_step(h, (int32_t)q, cx + q * n, cy + q * m, d->cap);
+    }
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(d->cap, &g);
+  if (st != LP_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(LP_ERR_CUDA, std::string("segment capture: ") + cudaGetErrorString(e));
+  const cudaError_t ei = cudaGraphInstantiate(&d->seg[kind], g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return fail(LP_ERR_CUDA, std::string("segment instantiate: ") + cudaGetErrorString(ei));
+  d->seg_len[kind] = len;
+  d->seg_codes[kind] = codes;
+  *out = d->seg[kind];
   return LP_OK;
 }
 
@@ -472,13 +528,22 @@ lp_status lp_batch_unroll(lp_batch_handle h, int64_t K, int64_t checkpoint_every
     st = zero(p, h->sum_m, s);
     if (st != LP_OK) return st;
   }
-  for (int64_t t = 0; t < K; ++t) {
-    if (t % C == 0) {
-      st = save_ck(h, t / C, s);
+  cudaGraphExec_t gf = nullptr;
+  if (K >= C) {
+    st = segment_graph(h, 0, C, &gf);
+    if (st != LP_OK) return st;
+  }
+  for (int64_t q = 0; q < nck; ++q) {
+    const int64_t t0 = q * C, len = std::min(C, K - t0);
+    st = save_ck(h, q, s);
+    if (st != LP_OK) return st;
+    kd_set_clock<<<1, 1, 0, s>>>(d->clk, t0, K);
+    if (len == C) {
+      CK(cudaGraphLaunch(gf, s));
+    } else {
+      for (int64_t o = 0; o < len && st == LP_OK; ++o) st = forward_step(h, (int32_t)o, nullptr, nullptr, s);
       if (st != LP_OK) return st;
     }
-    st = forward_step(h, t, nullptr, nullptr, s);
-    if (st != LP_OK) return st;
   }
   // 3. the output zhat of the last iteration in the original variables
   if (x && h->sum_n > 0)
@@ -504,9 +569,7 @@ lp_status lp_batch_unroll_vjp(lp_batch_handle h, const double* dl_dx, const doub
   const int64_t n = h->sum_n, m = h->sum_m, K = d->K, C = d->C;
   lp_status st = grow(&d->mx, &d->cap_mask, C * std::max<int64_t>(n + m, 1));
   if (st != LP_OK) return st;
-  d->my = nullptr;  // the row codes follow the column codes in the same buffer
-  uint8_t* codes_x = d->mx;
-  uint8_t* codes_y = d->mx + (size_t)C * (size_t)n;
+  d->my = nullptr;  // the row codes of a segment follow its column codes in the same buffer
   // seeds: lxhat = dL/dx * d_c, lyhat = dL/dy * d_r at the permuted positions
   if (dl_dx && n > 0) kd_gather<<<vgrid(h, n), 256, 0, s>>>(n, d->icol, h->d_inst, 1, h->col_perm, dl_dx, h->dc, 0, d->sx);
   else st = zero(d->sx, n, s);
@@ -523,18 +586,30 @@ lp_status lp_batch_unroll_vjp(lp_batch_handle h, const double* dl_dx, const doub
     if (st != LP_OK) return st;
   }
   CK(cudaGetLastError());
+  cudaGraphExec_t grec = nullptr, gbwd = nullptr;
+  if (K >= C) {
+    st = segment_graph(h, 1, C, &grec);
+    if (st == LP_OK) st = segment_graph(h, 2, C, &gbwd);
+    if (st != LP_OK) return st;
+  }
   for (int64_t q = (K + C - 1) / C - 1; q >= 0; --q) {
-    const int64_t t0 = q * C, t1 = std::min(K, t0 + C);
+    const int64_t t0 = q * C, len = std::min(C, K - t0);
     st = load_ck(h, q, s);
     if (st != LP_OK) return st;
-    for (int64_t t = t0; t < t1; ++t) {
-      st = forward_step(h, t, codes_x + (size_t)(t - t0) * n, codes_y + (size_t)(t - t0) * m, s);
-      if (st != LP_OK) return st;
+    kd_set_clock<<<1, 1, 0, s>>>(d->clk, t0, K);
+    if (len == C) {
+      CK(cudaGraphLaunch(grec, s));
+      CK(cudaGraphLaunch(gbwd, s));
+      continue;
     }
-    for (int64_t t = t1 - 1; t >= t0; --t) {
-      st = backward_step(h, t, codes_x + (size_t)(t - t0) * n, codes_y + (size_t)(t - t0) * m, t == K - 1, s);
-      if (st != LP_OK) return st;
-    }
+    // a shorter last segment: its codes are laid out for its own length
+    uint8_t* lx_codes = d->mx;
+    uint8_t* ly_codes = d->mx + (size_t)len * n;
+    for (int64_t o = 0; o < len && st == LP_OK; ++o)
+      st = forward_step(h, (int32_t)o, lx_codes + (size_t)o * n, ly_codes + (size_t)o * m, s);
+    for (int64_t o = len - 1; o >= 0 && st == LP_OK; --o)
+      st = backward_step(h, (int32_t)o, lx_codes + (size_t)o * n, ly_codes + (size_t)o * m, s);
+    if (st != LP_OK) return st;
   }
   // gradients in the original variables: c~ = d_c c, l_v~ = l_v / d_c, l_c~ = d_r l_c
   if (dl_dc && n > 0) kd_scatter<<<vgrid(h, n), 256, 0, s>>>(n, d->icol, h->d_inst, 1, h->col_perm, d->gc, h->dc, 0, dl_dc);
