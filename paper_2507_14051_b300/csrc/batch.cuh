@@ -104,38 +104,33 @@ using namespace pdhg_host;
 
 // ====================================================================== host side
 
-// Iteration clock of the differentiable solve's kernels (diff.cu).
-struct DiffClock {
-  int64_t t0, K;
+// Frozen schedule of one instance at one iteration of the differentiable solve (diff.cu).
+struct DiffSched {
+  double tau, sigma, al, be, ep;
+  int rho;
 };
 
 // Buffers of the differentiable unrolled solve (diff.cu), made on first use; a buffer that must
-// grow (trace, checkpoints) is freed and made again.  Segment graphs: one segment of seg_len
-// iterations captured forward (0), forward recording clamp codes (1) and adjoint (2).
+// grow (trace, checkpoints) is freed and made again.
 struct Diff {
   int64_t K = 0, C = 0;          // steps and checkpoint spacing of the last forward
   int64_t cap_trace = 0, cap_ck = 0, cap_mask = 0;
   bool forward_done = false;
   int32_t *irow = nullptr, *icol = nullptr;  // instance of each global row / column
   double *x = nullptr, *y = nullptr, *x0 = nullptr, *y0 = nullptr, *xh = nullptr, *yh = nullptr;
-  double *xbar = nullptr, *v = nullptr, *aty = nullptr;
+  double *xbar = nullptr;
   double *lx = nullptr, *ly = nullptr, *lx0 = nullptr, *ly0 = nullptr, *lv = nullptr;
-  double *lxbar = nullptr, *laty = nullptr, *ltmp = nullptr, *sx = nullptr, *sy = nullptr;
+  double *lxbar = nullptr, *laty = nullptr, *sx = nullptr, *sy = nullptr;
   double *gc = nullptr, *glv = nullptr, *guv = nullptr, *glc = nullptr, *guc = nullptr;
   double* ck = nullptr;                       // checkpoints: (x, y, x0, y0) every C steps
+  DiffSched* sched = nullptr;                 // schedule table (instance, iteration)
+  int64_t cap_sched = 0;
   uint8_t *mx = nullptr, *my = nullptr;       // clamp codes of one segment
   std::vector<void*> own;                     // fixed-size buffers
-  DiffClock* clk = nullptr;
-  cudaGraphExec_t seg[3] = {nullptr, nullptr, nullptr};
-  int64_t seg_len[3] = {0, 0, 0};
-  const uint8_t* seg_codes[3] = {nullptr, nullptr, nullptr};
-  cudaStream_t cap = nullptr;
   ~Diff() {
-    for (cudaGraphExec_t g : seg)
-      if (g) cudaGraphExecDestroy(g);
-    if (cap) cudaStreamDestroy(cap);
     for (void* p : own) cudaFree(p);
     cudaFree(ck);
+    cudaFree(sched);
     cudaFree(mx);
     cudaFree(my);
   }

@@ -20,29 +20,23 @@
 // The clamp codes (0 inside, 1 below the lower bound, 2 above the upper bound) are all the
 // backward pass needs from the forward one; they are recomputed segment by segment from the
 // checkpoints.
+#include <cooperative_groups.h>
+
 #include <type_traits>
 
 #include "batch.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pdhg {
 
 namespace {
 
-struct Sched {
-  double tau, sigma, al, be, ep;
-  int rho;
-};
-
-// Iteration of a kernel = clk->t0 + its offset in the segment; clk->K = the map's length (the
-// seeds enter at its last iteration).  One captured segment serves every segment this way.
-__global__ void kd_set_clock(DiffClock* clk, int64_t t0, int64_t K) {
-  clk->t0 = t0;
-  clk->K = K;
-}
+using Sched = ::DiffSched;
 
 // Frozen schedule of instance k at iteration t from its trace row (r, omega, restart, k_t).
-__device__ __forceinline__ Sched sched_at(const double* __restrict__ trace, int64_t cap, int k, int64_t t,
-                                          const double* __restrict__ eta, double gamma) {
+__device__ __forceinline__ Sched sched_from_trace(const double* __restrict__ trace, int64_t cap, int k, int64_t t,
+                                                  const double* __restrict__ eta, double gamma) {
   const double* r = trace + ((size_t)k * (size_t)cap + (size_t)t) * 4;
   const double om = r[1], e = eta[k];
   Sched s;
@@ -57,6 +51,15 @@ __device__ __forceinline__ Sched sched_at(const double* __restrict__ trace, int6
   return s;
 }
 
+// The schedule of every instance and iteration t < K, once, into a table of rows (k, t): the
+// per-entry kernels then read their instance's row instead of dividing for every entry.
+__global__ void kd_sched_table(const double* __restrict__ trace, int64_t cap, int32_t count, int64_t K,
+                               const double* __restrict__ eta, double gamma, Sched* __restrict__ table) {
+  const int64_t total = (int64_t)count * K;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x)
+    table[q] = sched_from_trace(trace, cap, (int)(q / K), q % K, eta, gamma);
+}
+
 __device__ __forceinline__ uint8_t clamp_code(double v, double lo, double hi) {
   return v < lo ? 1 : (v > hi ? 2 : 0);
 }
@@ -64,139 +67,208 @@ __device__ __forceinline__ uint8_t clamp_code(double v, double lo, double hi) {
 #define GRID_STRIDE(i, len) \
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (len); i += (int64_t)gridDim.x * blockDim.x)
 
-// Forward, column side of iteration t: xhat, xbar (and the codes of a).
-__global__ void kd_col_fwd(int64_t n, const int32_t* __restrict__ icol, const double* __restrict__ trace,
-                           int64_t cap, const double* __restrict__ eta, double gamma, const DiffClock* __restrict__ clk, int32_t off,
-                           const double* __restrict__ c, const double* __restrict__ lv,
-                           const double* __restrict__ uv, const double* __restrict__ x,
-                           const double* __restrict__ aty, double* __restrict__ xh, double* __restrict__ xbar,
-                           uint8_t* __restrict__ code) {
-  const int64_t t = clk->t0 + off;
-  GRID_STRIDE(j, n) {
-    const Sched s = sched_at(trace, cap, icol[j], t, eta, gamma);
-    const double xj = x[j];
-    const double a = fma(-s.tau, c[j] - aty[j], xj);
-    const double lo = lv[j], hi = uv[j];
-    const double h = clampd(a, lo, hi);
-    xh[j] = h;
-    xbar[j] = 2.0 * h - xj;
-    if (code) code[j] = clamp_code(a, lo, hi);
-  }
-}
+// Everything one unrolled iteration touches (the batch's permuted, scaled data; the
+// differentiation state).
+struct DiffArgs {
+  const int32_t *rpA, *ciA, *rpT, *ciT;
+  const double *valA, *valT;
+  const int4 *tasksA, *tasksT;
+  int32_t ntA, ntT;
+  int64_t n, m;
+  const int32_t *irow, *icol;
+  const Sched* sched;  // rows (instance, iteration), K per instance
+  int64_t K;
+  const double *c, *lv, *uv, *lc, *uc;
+  double *x, *y, *x0, *y0, *xh, *yh, *xbar;                 // forward state
+  double *lx, *ly, *lx0, *ly0, *lsv, *laty;                 // adjoint state (lsv: adjoint of s = of A xbar)
+  const double *sx, *sy;                                     // seeds (at the map's last iteration)
+  double *gc, *glv, *guv, *glc, *guc;                        // gradients (scaled, permuted)
+};
 
-// Forward, row side of iteration t: yhat, the y update (Halpern or restart) and the codes of s.
-__global__ void kd_row_fwd(int64_t m, const int32_t* __restrict__ irow, const double* __restrict__ trace,
-                           int64_t cap, const double* __restrict__ eta, double gamma, const DiffClock* __restrict__ clk, int32_t off,
-                           const double* __restrict__ lc, const double* __restrict__ uc,
-                           const double* __restrict__ v, double* __restrict__ y, double* __restrict__ y0,
-                           double* __restrict__ yh, uint8_t* __restrict__ code) {
-  const int64_t t = clk->t0 + off;
-  GRID_STRIDE(i, m) {
-    const Sched s = sched_at(trace, cap, irow[i], t, eta, gamma);
-    const double yi = y[i];
-    const double sv = v[i] - yi / s.sigma;
-    const double lo = lc[i], hi = uc[i];
-    const double h = s.sigma * (clampd(sv, lo, hi) - sv);
-    yh[i] = h;
-    if (code) code[i] = clamp_code(sv, lo, hi);
-    if (s.rho) {
-      y[i] = h;
-      y0[i] = h;
+// Forward, column j, iteration t: the x update of iteration t - 1 (deferred to here, where the
+// same lane owns x[j]), then xhat = clamp(x - tau (c - A^T y)), xbar = 2 xhat - x.
+__device__ __forceinline__ void col_fwd(const DiffArgs& a, int64_t j, int64_t t, int64_t t_first, double u,
+                                        uint8_t* code) {
+  const int k = a.icol[j];
+  double xj = a.x[j];
+  if (t > t_first) {
+    const Sched& p = a.sched[(size_t)k * (size_t)a.K + (size_t)(t - 1)];
+    const double h = a.xh[j];
+    if (p.rho) {
+      xj = h;
+      a.x0[j] = h;
     } else {
-      y[i] = s.al * h + s.be * yi + s.ep * y0[i];
+      xj = p.al * h + p.be * xj + p.ep * a.x0[j];
     }
+    a.x[j] = xj;
+  }
+  const Sched& s = a.sched[(size_t)k * (size_t)a.K + (size_t)t];
+  const double av = fma(-s.tau, a.c[j] - u, xj);
+  const double lo = a.lv[j], hi = a.uv[j];
+  const double h = clampd(av, lo, hi);
+  a.xh[j] = h;
+  a.xbar[j] = 2.0 * h - xj;
+  if (code) code[j] = clamp_code(av, lo, hi);
+}
+
+// Forward, the x update of iteration t alone (the last iteration of a launch).
+__device__ __forceinline__ void col_upd(const DiffArgs& a, int64_t j, int64_t t) {
+  const Sched& p = a.sched[(size_t)a.icol[j] * (size_t)a.K + (size_t)t];
+  const double h = a.xh[j];
+  if (p.rho) {
+    a.x[j] = h;
+    a.x0[j] = h;
+  } else {
+    a.x[j] = p.al * h + p.be * a.x[j] + p.ep * a.x0[j];
   }
 }
 
-// Forward: the x update of iteration t (after A xbar has been taken).
-__global__ void kd_col_upd(int64_t n, const int32_t* __restrict__ icol, const double* __restrict__ trace,
-                           int64_t cap, const double* __restrict__ eta, double gamma, const DiffClock* __restrict__ clk, int32_t off,
-                           const double* __restrict__ xh, double* __restrict__ x, double* __restrict__ x0) {
-  const int64_t t = clk->t0 + off;
-  GRID_STRIDE(j, n) {
-    const Sched s = sched_at(trace, cap, icol[j], t, eta, gamma);
-    const double h = xh[j];
-    if (s.rho) {
-      x[j] = h;
-      x0[j] = h;
-    } else {
-      x[j] = s.al * h + s.be * x[j] + s.ep * x0[j];
-    }
+// Forward, row i, iteration t: yhat = sigma (clamp(s) - s), s = A xbar - y / sigma, then the y
+// update (Halpern or restart).
+__device__ __forceinline__ void row_fwd(const DiffArgs& a, int64_t i, int64_t t, double v, uint8_t* code) {
+  const Sched& s = a.sched[(size_t)a.irow[i] * (size_t)a.K + (size_t)t];
+  const double yi = a.y[i];
+  const double sv = v - yi / s.sigma;
+  const double lo = a.lc[i], hi = a.uc[i];
+  const double h = s.sigma * (clampd(sv, lo, hi) - sv);
+  a.yh[i] = h;
+  if (code) code[i] = clamp_code(sv, lo, hi);
+  if (s.rho) {
+    a.y[i] = h;
+    a.y0[i] = h;
+  } else {
+    a.y[i] = s.al * h + s.be * yi + s.ep * a.y0[i];
   }
 }
 
-// Adjoint, row side of iteration t (first half): from (ly, ly0) of (y', y0') to lv = ls and the
+// Adjoint, row i, iteration t (first half): from (ly, ly0) of (y', y0') to lv = ls and the
 // partial adjoints of (y, y0); accumulates the row-bound gradients.
-__global__ void kd_row_bwd(int64_t m, const int32_t* __restrict__ irow, const double* __restrict__ trace,
-                           int64_t cap, const double* __restrict__ eta, double gamma, const DiffClock* __restrict__ clk, int32_t off,
-                           const uint8_t* __restrict__ code, const double* __restrict__ seed,
-                           double* __restrict__ ly, double* __restrict__ ly0, double* __restrict__ lv,
-                           double* __restrict__ glc, double* __restrict__ guc) {
-  const int64_t t = clk->t0 + off;
-  GRID_STRIDE(i, m) {
-    const Sched s = sched_at(trace, cap, irow[i], t, eta, gamma);
-    const double a_y = ly[i], a_y0 = ly0[i];
-    double lyh, lyp, ly0p;
-    if (s.rho) {
-      lyh = a_y + a_y0;
-      lyp = 0.0;
-      ly0p = 0.0;
-    } else {
-      lyh = s.al * a_y;
-      lyp = s.be * a_y;
-      ly0p = a_y0 + s.ep * a_y;
-    }
-    if (seed && t == clk->K - 1) lyh += seed[i];
-    const uint8_t cd = code[i];
-    const double ls = cd == 0 ? 0.0 : -s.sigma * lyh;
-    if (cd == 1) glc[i] += s.sigma * lyh;
-    if (cd == 2) guc[i] += s.sigma * lyh;
-    lv[i] = ls;
-    ly[i] = lyp - ls / s.sigma;
-    ly0[i] = ly0p;
+__device__ __forceinline__ void row_bwd(const DiffArgs& a, int64_t i, int64_t t, int64_t K, const uint8_t* code) {
+  const Sched& s = a.sched[(size_t)a.irow[i] * (size_t)a.K + (size_t)t];
+  const double a_y = a.ly[i], a_y0 = a.ly0[i];
+  double lyh, lyp, ly0p;
+  if (s.rho) {
+    lyh = a_y + a_y0;
+    lyp = 0.0;
+    ly0p = 0.0;
+  } else {
+    lyh = s.al * a_y;
+    lyp = s.be * a_y;
+    ly0p = a_y0 + s.ep * a_y;
   }
+  if (t == K - 1) lyh += a.sy[i];
+  const uint8_t cd = code[i];
+  const double ls = cd == 0 ? 0.0 : -s.sigma * lyh;
+  if (cd == 1) a.glc[i] += s.sigma * lyh;
+  if (cd == 2) a.guc[i] += s.sigma * lyh;
+  a.lsv[i] = ls;
+  a.ly[i] = lyp - ls / s.sigma;
+  a.ly0[i] = ly0p;
 }
 
-// Adjoint, column side of iteration t: from (lx, lx0) and lxbar = A^T lv to the adjoints of
+// Adjoint, column j, iteration t: from (lx, lx0) and lxbar = (A^T lv)_j to the adjoints of
 // (x, x0) and laty = tau la; accumulates the gradients of c and the variable bounds.
-__global__ void kd_col_bwd(int64_t n, const int32_t* __restrict__ icol, const double* __restrict__ trace,
-                           int64_t cap, const double* __restrict__ eta, double gamma, const DiffClock* __restrict__ clk, int32_t off,
-                           const uint8_t* __restrict__ code, const double* __restrict__ seed,
-                           const double* __restrict__ lxbar, double* __restrict__ lx, double* __restrict__ lx0,
-                           double* __restrict__ laty, double* __restrict__ gc, double* __restrict__ glv,
-                           double* __restrict__ guv) {
-  const int64_t t = clk->t0 + off;
-  GRID_STRIDE(j, n) {
-    const Sched s = sched_at(trace, cap, icol[j], t, eta, gamma);
-    const double a_x = lx[j], a_x0 = lx0[j];
-    double lxh, lxp, lx0p;
-    if (s.rho) {
-      lxh = a_x + a_x0;
-      lxp = 0.0;
-      lx0p = 0.0;
-    } else {
-      lxh = s.al * a_x;
-      lxp = s.be * a_x;
-      lx0p = a_x0 + s.ep * a_x;
-    }
-    if (seed && t == clk->K - 1) lxh += seed[j];
-    const double lb = lxbar[j];
-    lxh += 2.0 * lb;
-    lxp -= lb;
-    const uint8_t cd = code[j];
-    const double la = cd == 0 ? lxh : 0.0;
-    if (cd == 1) glv[j] += lxh;
-    if (cd == 2) guv[j] += lxh;
-    lxp += la;
-    gc[j] -= s.tau * la;
-    laty[j] = s.tau * la;
-    lx[j] = lxp;
-    lx0[j] = lx0p;
+__device__ __forceinline__ void col_bwd(const DiffArgs& a, int64_t j, int64_t t, int64_t K, double lb,
+                                        const uint8_t* code) {
+  const Sched& s = a.sched[(size_t)a.icol[j] * (size_t)a.K + (size_t)t];
+  const double a_x = a.lx[j], a_x0 = a.lx0[j];
+  double lxh, lxp, lx0p;
+  if (s.rho) {
+    lxh = a_x + a_x0;
+    lxp = 0.0;
+    lx0p = 0.0;
+  } else {
+    lxh = s.al * a_x;
+    lxp = s.be * a_x;
+    lx0p = a_x0 + s.ep * a_x;
   }
+  if (t == K - 1) lxh += a.sx[j];
+  lxh += 2.0 * lb;
+  lxp -= lb;
+  const uint8_t cd = code[j];
+  const double la = cd == 0 ? lxh : 0.0;
+  if (cd == 1) a.glv[j] += lxh;
+  if (cd == 2) a.guv[j] += lxh;
+  lxp += la;
+  a.gc[j] -= s.tau * la;
+  a.laty[j] = s.tau * la;
+  a.lx[j] = lxp;
+  a.lx0[j] = lx0p;
 }
 
-__global__ void kd_add(int64_t len, double* __restrict__ dst, const double* __restrict__ src) {
-  GRID_STRIDE(i, len) dst[i] += src[i];
+__device__ __forceinline__ int dtask_lanes(const int4& t) { return t.z >> 24; }
+__device__ __forceinline__ int dtask_per_lane(const int4& t) { return t.z & 0xFFFFFF; }
+
+// Forward: iterations t0 .. t0 + len - 1 of every instance, one cooperative launch (all blocks
+// resident).  Per iteration: column phase (A^T y by column tiles, then col_fwd, which first
+// applies the previous iteration's deferred x update), grid barrier, row phase (A xbar by row
+// tiles, then row_fwd), grid barrier.  The last iteration's x update ends the launch, so the
+// state (x, y, x0, y0) is complete between launches.  cx / cy (or NULL): where iteration
+// t0 + o stores its clamp codes, at cx + o n and cy + o m.
+__global__ void __launch_bounds__(kThreads, 3) kd_fwd_loop(DiffArgs a, int64_t t0, int32_t len, uint8_t* cx,
+                                                           uint8_t* cy) {
+  cg::grid_group grid = cg::this_grid();
+  const LoadPolicy pol = make_policy();
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5), nw = gridDim.x * kWarps;
+  for (int32_t o = 0; o < len; ++o) {
+    const int64_t t = t0 + o;
+    uint8_t* ccx = cx ? cx + (size_t)o * (size_t)a.n : nullptr;
+    uint8_t* ccy = cy ? cy + (size_t)o * (size_t)a.m : nullptr;
+    for (int j = gw; j < a.ntT; j += nw) {
+      const int4 td = a.tasksT[j];
+      const double u = tile_spmv(a.rpT, a.ciT, a.valT, a.y, td.x, td.y, dtask_lanes(td), dtask_per_lane(td), lane, pol);
+      if (lane < td.y) col_fwd(a, td.x + lane, t, t0, u, ccx);
+    }
+    grid.sync();
+    for (int j = gw; j < a.ntA; j += nw) {
+      const int4 td = a.tasksA[j];
+      const double v = tile_spmv(a.rpA, a.ciA, a.valA, a.xbar, td.x, td.y, dtask_lanes(td), dtask_per_lane(td), lane, pol);
+      if (lane < td.y) row_fwd(a, td.x + lane, t, v, ccy);
+    }
+    grid.sync();
+  }
+  if (len > 0) GRID_STRIDE(j, a.n) col_upd(a, j, t0 + len - 1);
+}
+
+// Adjoint of iterations t0 + len - 1 down to t0 (codes of iteration t0 + o at cx + o n,
+// cy + o m), one cooperative launch.  Per iteration: column phase (lxbar = A^T lv by column
+// tiles, then col_bwd), grid barrier, row phase (A laty by row tiles, added to ly, then the
+// first half of the previous iteration's adjoint, row_bwd, in the same lane), grid barrier.
+// The launch starts with row_bwd of its last iteration.
+__global__ void __launch_bounds__(kThreads, 3) kd_bwd_loop(DiffArgs a, int64_t t0, int64_t K, int32_t len,
+                                                           const uint8_t* cx, const uint8_t* cy) {
+  cg::grid_group grid = cg::this_grid();
+  const LoadPolicy pol = make_policy();
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5), nw = gridDim.x * kWarps;
+  if (len <= 0) return;
+  {
+    const uint8_t* ccy = cy + (size_t)(len - 1) * (size_t)a.m;
+    GRID_STRIDE(i, a.m) row_bwd(a, i, t0 + len - 1, K, ccy);
+  }
+  grid.sync();
+  for (int32_t o = len - 1; o >= 0; --o) {
+    const int64_t t = t0 + o;
+    const uint8_t* ccx = cx + (size_t)o * (size_t)a.n;
+    for (int j = gw; j < a.ntT; j += nw) {
+      const int4 td = a.tasksT[j];
+      const double lb = tile_spmv(a.rpT, a.ciT, a.valT, a.lsv, td.x, td.y, dtask_lanes(td), dtask_per_lane(td), lane, pol);
+      if (lane < td.y) col_bwd(a, td.x + lane, t, K, lb, ccx);
+    }
+    grid.sync();
+    const uint8_t* ccy = o > 0 ? cy + (size_t)(o - 1) * (size_t)a.m : nullptr;
+    for (int j = gw; j < a.ntA; j += nw) {
+      const int4 td = a.tasksA[j];
+      const double w = tile_spmv(a.rpA, a.ciA, a.valA, a.laty, td.x, td.y, dtask_lanes(td), dtask_per_lane(td), lane, pol);
+      if (lane < td.y) {
+        const int64_t i = td.x + lane;
+        a.ly[i] += w;
+        if (o > 0) row_bwd(a, i, t - 1, K, ccy);
+      }
+    }
+    grid.sync();
+  }
 }
 
 // Instance of every permuted row and column.
@@ -278,12 +350,11 @@ lp_status diff_buffers(lp_batch* h) {
     return e;
   };
   const size_t n = (size_t)h->sum_n, m = (size_t)h->sum_m;
-  CK(get(&d->irow, m)); CK(get(&d->icol, n)); CK(get(&d->clk, 1));
-  CK(cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking));
-  for (double** p : {&d->x, &d->x0, &d->xh, &d->xbar, &d->aty, &d->lx, &d->lx0, &d->lxbar, &d->laty, &d->sx,
+  CK(get(&d->irow, m)); CK(get(&d->icol, n));
+  for (double** p : {&d->x, &d->x0, &d->xh, &d->xbar, &d->lx, &d->lx0, &d->lxbar, &d->laty, &d->sx,
                      &d->gc, &d->glv, &d->guv})
     CK(get(p, n));
-  for (double** p : {&d->y, &d->y0, &d->yh, &d->v, &d->ly, &d->ly0, &d->lv, &d->ltmp, &d->sy, &d->glc, &d->guc})
+  for (double** p : {&d->y, &d->y0, &d->yh, &d->ly, &d->ly0, &d->lv, &d->sy, &d->glc, &d->guc})
     CK(get(p, m));
   kd_owner<<<h->gridS, kThreads, 0, h->setup_stream>>>(h->d_inst, h->count, d->irow, d->icol);
   CK(cudaGetLastError());
@@ -307,50 +378,42 @@ lp_status grow(T** p, int64_t* cap, int64_t need) {
   return LP_OK;
 }
 
-// One forward iteration (clock t0 + off) of every instance on the diff state.  code_x / code_y:
-// where to store the clamp codes (NULL: not stored).
-lp_status forward_step(lp_batch* h, int32_t off, uint8_t* code_x, uint8_t* code_y, cudaStream_t s) {
-  Diff* d = h->diff;
-  const int64_t n = h->sum_n, m = h->sum_m;
-  const double g = h->prm.gamma;
-  const int gA = grid_for(h->ntA, kWarps, 8 * h->num_sms), gT = grid_for(h->ntT, kWarps, 8 * h->num_sms);
-  if (h->ntT > 0) kb_spmv<double><<<gT, kThreads, 0, s>>>(h->tasksT, h->ntT, h->rpT, h->ciT, h->valT, d->y, d->aty);
-  if (n > 0)
-    kd_col_fwd<<<vgrid(h, n), 256, 0, s>>>(n, d->icol, h->trace, h->trace_cap, h->d_eta, g, d->clk, off, h->c, h->lv, h->uv,
-                                           d->x, d->aty, d->xh, d->xbar, code_x);
-  if (h->ntA > 0) kb_spmv<double><<<gA, kThreads, 0, s>>>(h->tasksA, h->ntA, h->rpA, h->ciA, h->valA, d->xbar, d->v);
-  if (m > 0)
-    kd_row_fwd<<<vgrid(h, m), 256, 0, s>>>(m, d->irow, h->trace, h->trace_cap, h->d_eta, g, d->clk, off, h->lc, h->uc, d->v,
-                                           d->y, d->y0, d->yh, code_y);
-  if (n > 0)
-    kd_col_upd<<<vgrid(h, n), 256, 0, s>>>(n, d->icol, h->trace, h->trace_cap, h->d_eta, g, d->clk, off, d->xh, d->x, d->x0);
-  CK(cudaGetLastError());
+DiffArgs diff_args(const lp_batch* h) {
+  const Diff* d = h->diff;
+  DiffArgs a;
+  a.rpA = h->rpA; a.ciA = h->ciA; a.rpT = h->rpT; a.ciT = h->ciT; a.valA = h->valA; a.valT = h->valT;
+  a.tasksA = h->tasksA; a.tasksT = h->tasksT; a.ntA = h->ntA; a.ntT = h->ntT;
+  a.n = h->sum_n; a.m = h->sum_m;
+  a.irow = d->irow; a.icol = d->icol; a.sched = d->sched; a.K = d->K;
+  a.c = h->c; a.lv = h->lv; a.uv = h->uv; a.lc = h->lc; a.uc = h->uc;
+  a.x = d->x; a.y = d->y; a.x0 = d->x0; a.y0 = d->y0; a.xh = d->xh; a.yh = d->yh; a.xbar = d->xbar;
+  a.lx = d->lx; a.ly = d->ly; a.lx0 = d->lx0; a.ly0 = d->ly0; a.lsv = d->lv; a.laty = d->laty;
+  a.sx = d->sx; a.sy = d->sy;
+  a.gc = d->gc; a.glv = d->glv; a.guv = d->guv; a.glc = d->glc; a.guc = d->guc;
+  return a;
+}
+
+lp_status coop_launch(lp_batch* h, const void* fn, void** args, cudaStream_t s) {
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, 0));
+  if (occ < 1) occ = 1;
+  CK(cudaLaunchCooperativeKernel(fn, dim3((unsigned)(occ * h->num_sms)), dim3(kThreads), args, 0, s));
   return LP_OK;
 }
 
-// One adjoint iteration (clock t0 + off; codes of that iteration in code_x / code_y; the seeds
-// enter at the map's last iteration).
-lp_status backward_step(lp_batch* h, int32_t off, const uint8_t* code_x, const uint8_t* code_y, cudaStream_t s) {
-  Diff* d = h->diff;
-  const int64_t n = h->sum_n, m = h->sum_m;
-  const double g = h->prm.gamma;
-  const int gA = grid_for(h->ntA, kWarps, 8 * h->num_sms), gT = grid_for(h->ntT, kWarps, 8 * h->num_sms);
-  if (m > 0)
-    kd_row_bwd<<<vgrid(h, m), 256, 0, s>>>(m, d->irow, h->trace, h->trace_cap, h->d_eta, g, d->clk, off, code_y,
-                                           d->sy, d->ly, d->ly0, d->lv, d->glc, d->guc);
-  if (n > 0) {
-    if (h->ntT > 0) kb_spmv<double><<<gT, kThreads, 0, s>>>(h->tasksT, h->ntT, h->rpT, h->ciT, h->valT, d->lv, d->lxbar);
-    else CK(cudaMemsetAsync(d->lxbar, 0, sizeof(double) * n, s));
-    kd_col_bwd<<<vgrid(h, n), 256, 0, s>>>(n, d->icol, h->trace, h->trace_cap, h->d_eta, g, d->clk, off, code_x,
-                                           d->sx, d->lxbar, d->lx, d->lx0, d->laty, d->gc, d->glv,
-                                           d->guv);
-  }
-  if (m > 0 && h->ntA > 0) {
-    kb_spmv<double><<<gA, kThreads, 0, s>>>(h->tasksA, h->ntA, h->rpA, h->ciA, h->valA, d->laty, d->ltmp);
-    kd_add<<<vgrid(h, m), 256, 0, s>>>(m, d->ly, d->ltmp);
-  }
-  CK(cudaGetLastError());
-  return LP_OK;
+// Forward iterations t0 .. t0 + len - 1 (codes stored when cx, cy are given).
+lp_status forward_run(lp_batch* h, int64_t t0, int32_t len, uint8_t* cx, uint8_t* cy, cudaStream_t s) {
+  DiffArgs a = diff_args(h);
+  void* args[] = {&a, &t0, &len, &cx, &cy};
+  return coop_launch(h, reinterpret_cast<const void*>(kd_fwd_loop), args, s);
+}
+
+// Adjoint of iterations t0 + len - 1 down to t0 of a map of K iterations.
+lp_status backward_run(lp_batch* h, int64_t t0, int64_t K, int32_t len, const uint8_t* cx, const uint8_t* cy,
+                       cudaStream_t s) {
+  DiffArgs a = diff_args(h);
+  void* args[] = {&a, &t0, &K, &len, &cx, &cy};
+  return coop_launch(h, reinterpret_cast<const void*>(kd_bwd_loop), args, s);
 }
 
 // Checkpoint q: (x, y, x0, y0) of the diff state.
@@ -382,49 +445,6 @@ lp_status load_ck(lp_batch* h, int64_t q, cudaStream_t s) {
 
 lp_status zero(double* p, int64_t len, cudaStream_t s) {
   if (len > 0) CK(cudaMemsetAsync(p, 0, sizeof(double) * (size_t)len, s));
-  return LP_OK;
-}
-
-// The graph of one segment of len iterations (offsets 0..len-1 of the clock): kind 0 forward,
-// 1 forward storing the clamp codes of offset o at codes + o (n + m), 2 the adjoint from offset
-// len-1 down to 0.  Captured once per (kind, len, codes buffer) and replayed for every segment.
-lp_status segment_graph(lp_batch* h, int kind, int64_t len, cudaGraphExec_t* out) {
-  Diff* d = h->diff;
-  const uint8_t* codes = kind == 0 ? nullptr : d->mx;
-  if (d->seg[kind] && d->seg_len[kind] == len && d->seg_codes[kind] == codes) {
-    *out = d->seg[kind];
-    return LP_OK;
-  }
-  if (d->seg[kind]) {
-    cudaGraphExecDestroy(d->seg[kind]);
-    d->seg[kind] = nullptr;
-  }
-  const size_t n = (size_t)h->sum_n, m = (size_t)h->sum_m;
-  uint8_t* cx = d->mx;
-  uint8_t* cy = d->mx + (size_t)len * n;
-  CK(cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeThreadLocal));
-  lp_status st = LP_OK;
-  for (int64_t o = 0; o < len && st == LP_OK; ++o) {
-    if (kind == 0) st = forward_step(h, (int32_t)o, nullptr, nullptr, d->cap);
-    else if (kind == 1) st = forward_step(h, (int32_t)o, cx + o * n, cy + o * m, d->cap);
-    else {
-      const int64_t q = len - 1 - o;
-      st = backward_step(h, (int32_t)q, cx + q * n, cy + q * m, d->cap);
-    }
-  }
-  cudaGraph_t g = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(d->cap, &g);
-  if (st != LP_OK) {
-    if (g) cudaGraphDestroy(g);
-    return st;
-  }
-  if (e != cudaSuccess) return fail(LP_ERR_CUDA, std::string("segment capture: ") + cudaGetErrorString(e));
-  const cudaError_t ei = cudaGraphInstantiate(&d->seg[kind], g, 0);
-  cudaGraphDestroy(g);
-  if (ei != cudaSuccess) return fail(LP_ERR_CUDA, std::string("segment instantiate: ") + cudaGetErrorString(ei));
-  d->seg_len[kind] = len;
-  d->seg_codes[kind] = codes;
-  *out = d->seg[kind];
   return LP_OK;
 }
 
@@ -512,9 +532,15 @@ lp_status lp_batch_unroll(lp_batch_handle h, int64_t K, int64_t checkpoint_every
   lp_status st = diff_buffers(h);
   if (st != LP_OK) return st;
   Diff* d = h->diff;
-  // 1. the frozen schedule
+  // 1. the frozen schedule, and its table of step sizes and Halpern weights
   st = batch_schedule_solve(h, K, s);
   if (st != LP_OK) return st;
+  st = grow(&d->sched, &d->cap_sched, (int64_t)h->count * K);
+  if (st != LP_OK) return st;
+  kd_sched_table<<<vgrid(h, (int64_t)h->count * K), 256, 0, s>>>(h->trace, h->trace_cap, h->count, K, h->d_eta,
+                                                                  h->prm.gamma, d->sched);
+  CK(cudaGetLastError());
+  d->K = K;
   // 2. the unrolled iterations from zero, with checkpoints
   const int64_t C = checkpoint_every;
   const int64_t nck = (K + C - 1) / C;
@@ -528,22 +554,11 @@ lp_status lp_batch_unroll(lp_batch_handle h, int64_t K, int64_t checkpoint_every
     st = zero(p, h->sum_m, s);
     if (st != LP_OK) return st;
   }
-  cudaGraphExec_t gf = nullptr;
-  if (K >= C) {
-    st = segment_graph(h, 0, C, &gf);
-    if (st != LP_OK) return st;
-  }
   for (int64_t q = 0; q < nck; ++q) {
     const int64_t t0 = q * C, len = std::min(C, K - t0);
     st = save_ck(h, q, s);
+    if (st == LP_OK) st = forward_run(h, t0, (int32_t)len, nullptr, nullptr, s);
     if (st != LP_OK) return st;
-    kd_set_clock<<<1, 1, 0, s>>>(d->clk, t0, K);
-    if (len == C) {
-      CK(cudaGraphLaunch(gf, s));
-    } else {
-      for (int64_t o = 0; o < len && st == LP_OK; ++o) st = forward_step(h, (int32_t)o, nullptr, nullptr, s);
-      if (st != LP_OK) return st;
-    }
   }
   // 3. the output zhat of the last iteration in the original variables
   if (x && h->sum_n > 0)
@@ -586,29 +601,13 @@ lp_status lp_batch_unroll_vjp(lp_batch_handle h, const double* dl_dx, const doub
     if (st != LP_OK) return st;
   }
   CK(cudaGetLastError());
-  cudaGraphExec_t grec = nullptr, gbwd = nullptr;
-  if (K >= C) {
-    st = segment_graph(h, 1, C, &grec);
-    if (st == LP_OK) st = segment_graph(h, 2, C, &gbwd);
-    if (st != LP_OK) return st;
-  }
   for (int64_t q = (K + C - 1) / C - 1; q >= 0; --q) {
     const int64_t t0 = q * C, len = std::min(C, K - t0);
+    uint8_t* cx = d->mx;
+    uint8_t* cy = d->mx + (size_t)len * (size_t)n;
     st = load_ck(h, q, s);
-    if (st != LP_OK) return st;
-    kd_set_clock<<<1, 1, 0, s>>>(d->clk, t0, K);
-    if (len == C) {
-      CK(cudaGraphLaunch(grec, s));
-      CK(cudaGraphLaunch(gbwd, s));
-      continue;
-    }
-    // a shorter last segment: its codes are laid out for its own length
-    uint8_t* lx_codes = d->mx;
-    uint8_t* ly_codes = d->mx + (size_t)len * n;
-    for (int64_t o = 0; o < len && st == LP_OK; ++o)
-      st = forward_step(h, (int32_t)o, lx_codes + (size_t)o * n, ly_codes + (size_t)o * m, s);
-    for (int64_t o = len - 1; o >= 0 && st == LP_OK; --o)
-      st = backward_step(h, (int32_t)o, lx_codes + (size_t)o * n, ly_codes + (size_t)o * m, s);
+    if (st == LP_OK) st = forward_run(h, t0, (int32_t)len, cx, cy, s);
+    if (st == LP_OK) st = backward_run(h, t0, K, (int32_t)len, cx, cy, s);
     if (st != LP_OK) return st;
   }
   // gradients in the original variables: c~ = d_c c, l_v~ = l_v / d_c, l_c~ = d_r l_c
