@@ -113,8 +113,9 @@ typedef struct {
                               the batch, whose long rows would otherwise spend one warp's FP64
                               issue on each row's epilogue) */
   int64_t batch_local_nnz; /* lp_batch_* only: instances with at most this many nonzeros are
-                              solved by one thread block each (block barriers only) instead of
-                              by the grid-wide loop; 0 puts every instance on the grid loop */
+                              solved by one cluster of 8 CTAs each (cluster barriers only)
+                              instead of by the grid-wide loop; 0 puts every instance on the grid
+                              loop */
 } lp_params;
 
 /* Fills p with the defaults: gamma 1, betas 0.2 / 0.8 / 0.36, K_P 0.5, K_I 0.001, K_D 0,

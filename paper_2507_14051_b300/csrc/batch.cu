@@ -20,7 +20,9 @@
 //                 shared-memory copy of the instance's scalar state;
 //   grid barrier, column phase, grid barrier, column control (KKT test), grid barrier.
 // Every instance advances by one iteration per loop trip; finished instances drop out of the
-// task space.  Results are deterministic (fixed summation orders everywhere).
+// task space.  Results are deterministic (fixed summation orders everywhere).  Instances with
+// at most batch_local_nnz nonzeros skip the grid loop: each runs on a cluster of kLocalCtas CTAs
+// (kb_cluster_loop) with cluster barriers and distributed-shared-memory totals.
 //
 // The CUDA graph of each precision is a conditional while node around one cooperative launch
 // of kBatchUnroll iterations, so a solve needs no host synchronisation.  Mixed precision runs
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 3) kb_loop(BatchArgs<V> a, int32_t i
 
 // Start of a stage: every instance's scalar state from its template (step size, omega0, KKT
 // denominators, parameters), with the stage's tolerance, iteration limit and stall guard.
-// Block-local instances are marked done for the grid loop (n_local of them).
+// The small (cluster-loop) instances are marked done for the grid loop (n_local of them).
 __global__ void kb_init_ctl(int32_t count, const Ctl* __restrict__ init, const BInst* __restrict__ inst,
                             Ctl* ctl, int32_t* done, BRow* rstep, BatchCtl* bc, double tol,
                             int64_t max_iter, int32_t patience, int64_t max_bodies, int32_t n_local,
@@ -343,7 +345,7 @@ __global__ void kb_init_ctl(int32_t count, const Ctl* __restrict__ init, const B
     c.cand_slot = 0;
     c.best_slot = -1;
     ctl[k] = c;
-    done[k] = inst[k].local;  // the grid loop skips block-local instances
+    done[k] = inst[k].local;  // the grid loop skips the small (cluster-local) instances
     rstep[k] = make_brow(c);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -467,20 +469,46 @@ __global__ void __launch_bounds__(kThreads) kb_warm(BatchArgs<double> d, int64_t
   }
 }
 
-// Block-local loop for the small instances: one block runs every iteration of one instance (the
-// single-instance loop with the block as its grid: per-thread sums over the block's tasks, a
-// block tree, the control in thread 0, block barriers only).  It continues from the instance's
-// current state until it is done; `cap` bounds the iterations of one launch (a guard: the
-// control ends every solve by max_iter).
-template <class V>
-__global__ void __launch_bounds__(kThreads, 2) kb_block_loop(BatchArgs<V> a, const int32_t* __restrict__ list,
-                                                          int32_t nlist, int64_t cap) {
+// Loop for the small instances: a cluster of kCtas CTAs (on kCtas SMs) runs every iteration of
+// one instance.  Each CTA takes every kCtas-th of the instance's warp tasks and sums its
+// threads' epilogue sums (block tree); the CTAs' totals meet in distributed shared memory after
+// a cluster barrier, every CTA adds them in rank order and runs the same control on its own
+// shared-memory copy of the scalar state, so all copies agree bit for bit and the CTAs leave
+// the loop together.  Two cluster barriers per iteration; the iteration's arithmetic is spread
+// over kCtas SMs' FP64 units instead of one.  It continues from the instance's current state
+// until it is done; `cap` bounds the iterations of one launch (a guard: the control ends every
+// solve by max_iter).
+template <int kCtas>
+__device__ __forceinline__ void cluster_barrier() {
+  if (kCtas > 1) cg::this_cluster().sync();
+  else __syncthreads();
+}
+
+template <int kCtas>
+__device__ __forceinline__ void cluster_totals(const double* part, int nsums, double (&tot)[kNumSums]) {
+#pragma unroll
+  for (int q = 0; q < kNumSums; ++q) tot[q] = 0.0;
+  for (int r = 0; r < kCtas; ++r) {
+    const double* p = kCtas > 1 ? cg::this_cluster().map_shared_rank(const_cast<double*>(part), r) : part;
+#pragma unroll
+    for (int q = 0; q < kNumSums; ++q)
+      if (q < nsums) tot[q] += p[q];
+  }
+}
+
+template <class V, int kCtas>
+__global__ void __launch_bounds__(kThreads, 2) kb_cluster_loop(BatchArgs<V> a, const int32_t* __restrict__ list,
+                                                               int32_t nlist, int64_t cap) {
   __shared__ Ctl sc;
   __shared__ RowStep rst;
   __shared__ ColStepT<V> cst;
+  __shared__ double part[2][kNumSums];  // this CTA's row-phase and column-phase totals
   const LoadPolicy pol = make_policy();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int q = blockIdx.x; q < nlist; q += gridDim.x) {
+  const int rank = (int)(blockIdx.x % kCtas);
+  const int cid = (int)(blockIdx.x / kCtas), ncl = (int)(gridDim.x / kCtas);
+  const int w0 = rank * kWarps + warp, wstep = kCtas * kWarps;
+  for (int q = cid; q < nlist; q += ncl) {
     const int ii = list[q];
     const BInst I = a.inst[ii];
     ctl_load(&sc, a.ctl + ii);
@@ -493,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 2) kb_block_loop(BatchArgs<V> a, con
       const RowStep st = rst;
       const V* __restrict__ xg = (sc.t & 1) ? a.ra.xh1 : a.ra.xh0;
       double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      for (int j = warp; j < I.nta; j += kWarps) {
+      for (int j = w0; j < I.nta; j += wstep) {
         const int4 td = a.tasksA[I.ta0 + j];
         const V v = tile_spmv<V, true>(a.ra.rp, a.ra.ci, a.ra.val, xg, td.x, td.y, task_lanes(td),
                                        task_per_lane(td), lane, pol);
@@ -501,14 +529,21 @@ __global__ void __launch_bounds__(kThreads, 2) kb_block_loop(BatchArgs<V> a, con
       }
       const int nr = st.check ? 5 : 3;
       block_reduce(s, nr);
-      if (threadIdx.x == 0) row_control(sc, s, st.check != 0, trace_of(a, ii));
+      if (threadIdx.x == 0)
+        for (int k = 0; k < kNumSums; ++k) part[0][k] = s[k];
+      cluster_barrier<kCtas>();
+      if (threadIdx.x == 0) {
+        double tot[kNumSums];
+        cluster_totals<kCtas>(part[0], nr, tot);
+        row_control(sc, tot, st.check != 0, rank == 0 ? trace_of(a, ii) : nullptr);
+      }
       __syncthreads();
       if (sc.done) break;
       if (threadIdx.x == 0) cst = col_step(sc, a.ca);
       __syncthreads();
       const ColStepT<V> cs = cst;
       double s2[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      for (int j = warp; j < I.ntt; j += kWarps) {
+      for (int j = w0; j < I.ntt; j += wstep) {
         const int4 td = a.tasksT[I.tt0 + j];
         const V u = tile_spmv<V, true>(a.ca.rp, a.ca.ci, a.ca.val, a.ca.yh, td.x, td.y, task_lanes(td),
                                        task_per_lane(td), lane, pol);
@@ -516,7 +551,14 @@ __global__ void __launch_bounds__(kThreads, 2) kb_block_loop(BatchArgs<V> a, con
       }
       const int nc = cs.check ? 5 : 2;
       block_reduce(s2, nc);
-      if (threadIdx.x == 0) col_control(sc, s2, cs.check != 0);
+      if (threadIdx.x == 0)
+        for (int k = 0; k < kNumSums; ++k) part[1][k] = s2[k];
+      cluster_barrier<kCtas>();
+      if (threadIdx.x == 0) {
+        double tot[kNumSums];
+        cluster_totals<kCtas>(part[1], nc, tot);
+        col_control(sc, tot, cs.check != 0);
+      }
       __syncthreads();
     }
     if (threadIdx.x == 0 && !sc.done) {  // the guard tripped: stop with an internal error
@@ -525,8 +567,8 @@ __global__ void __launch_bounds__(kThreads, 2) kb_block_loop(BatchArgs<V> a, con
       sc.done = 1;
     }
     __syncthreads();
-    ctl_load(a.ctl + ii, &sc);
-    __syncthreads();
+    if (rank == 0) ctl_load(a.ctl + ii, &sc);
+    cluster_barrier<kCtas>();  // every CTA has read this instance's totals before the next one
   }
 }
 
@@ -658,6 +700,25 @@ cudaError_t launch_batch_loop(const lp_batch* h, const BatchArgs<V>& a, int32_t 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kb_loop<V>, a, iters, cond, use_cond);
+}
+
+// The small instances' loop: clusters of kLocalCtas CTAs, one instance per cluster at a time.
+template <class V>
+cudaError_t launch_local(const lp_batch* h, const BatchArgs<V>& a, int64_t cap, cudaStream_t s) {
+  const int clusters = std::max(1, std::min(h->n_local, 2 * h->num_sms / kLocalCtas));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(clusters * kLocalCtas));
+  cfg.blockDim = dim3((unsigned)kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kLocalCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kb_cluster_loop<V, kLocalCtas>, a, h->local_list, h->n_local, cap);
 }
 
 template <class V>
@@ -1064,7 +1125,7 @@ lp_status enqueue_batch_start(lp_batch* h, double tol, int64_t max_iter, int32_t
   return LP_OK;
 }
 
-// One stage of precision V: the grid loop over the grid instances (graph), then the block-local
+// One stage of precision V: the grid loop over the grid instances (graph), then the cluster
 // loop over the small ones.
 template <class V>
 lp_status enqueue_stage(lp_batch* h, cudaGraphExec_t exec, int64_t max_iter, cudaStream_t s) {
@@ -1072,9 +1133,7 @@ lp_status enqueue_stage(lp_batch* h, cudaGraphExec_t exec, int64_t max_iter, cud
   if (h->n_local > 0) {
     BatchArgs<V> a;
     fill_batch_args<V>(h, a);
-    const int g = std::min(h->n_local, 8 * h->num_sms);
-    kb_block_loop<V><<<g, kThreads, 0, s>>>(a, h->local_list, h->n_local, max_iter + 2);
-    CK(cudaGetLastError());
+    CK(launch_local<V>(h, a, max_iter + 2, s));
   }
   return LP_OK;
 }
@@ -1108,11 +1167,7 @@ lp_status batch_schedule_solve(lp_batch* h, int64_t K, cudaStream_t s) {
     for (int64_t q = 0; q < launches; ++q)
       CK(launch_batch_loop<double>(h, a, kBatchUnroll, cudaGraphConditionalHandle{}, 0, s));
   }
-  if (h->n_local > 0) {
-    const int gl = std::min(h->n_local, 8 * h->num_sms);
-    kb_block_loop<double><<<gl, kThreads, 0, s>>>(a, h->local_list, h->n_local, K + 2);
-    CK(cudaGetLastError());
-  }
+  if (h->n_local > 0) CK(launch_local<double>(h, a, K + 2, s));
   h->solved = true;
   h->last_stream = s;
   return LP_OK;

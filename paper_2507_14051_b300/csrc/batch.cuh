@@ -14,6 +14,7 @@ namespace pdhg {
 
 constexpr int kBatchUnroll = 16;  // iterations per launch of the batch loop kernel
 constexpr int kBatchTileRows = 32;  // rows per tile of the batch when lp_params.tile_rows is 0
+constexpr int kLocalCtas = 8;       // CTAs (SMs) of the cluster that runs one small instance
 constexpr int kMaxInst = LP_BATCH_MAX_INSTANCES;
 
 // Place of one instance in the concatenated arrays.
@@ -21,7 +22,7 @@ struct BInst {
   int32_t row0, m, col0, n;
   int32_t ta0, nta;  // its tasks in the row-task list (A)
   int32_t tt0, ntt;  // its tasks in the column-task list (A^T)
-  int32_t local;     // 1: solved by one block (kb_block_loop), not by the grid loop
+  int32_t local;     // 1: solved by one cluster (kb_cluster_loop), not by the grid loop
   int32_t pad;
 };
 
@@ -145,7 +146,7 @@ struct lp_batch {
   std::vector<BInst> inst;
   std::vector<double> eta;
   int32_t n_local = 0;
-  int32_t* local_list = nullptr;  // device: the block-local instances
+  int32_t* local_list = nullptr;  // device: the small instances (cluster loop)
   int grid = 1, gridS = 1;
   bool solved = false;
   cudaStream_t last_stream = nullptr;

@@ -160,7 +160,7 @@ __device__ __forceinline__ double start_entry(uint64_t seed, uint64_t i) {
 }
 
 // Read-only loads that allocate in L1: for data a block re-reads every iteration (the
-// block-local loop over a small instance).
+// cluster loop over a small instance).
 __device__ __forceinline__ double ld_cached(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float ld_cached(const float* p) { return __ldg(p); }
 __device__ __forceinline__ int32_t ld_cached(const int32_t* p) { return __ldg(p); }
