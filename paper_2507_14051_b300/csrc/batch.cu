@@ -702,23 +702,43 @@ cudaError_t launch_batch_loop(const lp_batch* h, const BatchArgs<V>& a, int32_t 
   return cudaLaunchKernelEx(&cfg, kb_loop<V>, a, iters, cond, use_cond);
 }
 
-// The small instances' loop: clusters of kLocalCtas CTAs, one instance per cluster at a time.
-template <class V>
-cudaError_t launch_local(const lp_batch* h, const BatchArgs<V>& a, int64_t cap, cudaStream_t s) {
-  const int clusters = std::max(1, std::min(h->n_local, 2 * h->num_sms / kLocalCtas));
+// The small instances' loop: clusters of kLocalCtas CTAs over the clustered list, and single
+// CTAs over the tiny instances, the two launches running side by side (a second stream, joined
+// back into s by an event).
+template <class V, int kCtas>
+cudaError_t launch_cluster_loop(const lp_batch* h, const BatchArgs<V>& a, const int32_t* list, int32_t n,
+                                int64_t cap, cudaStream_t s) {
+  const int clusters = std::max(1, std::min(n, 2 * h->num_sms / kCtas));
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)(clusters * kLocalCtas));
+  cfg.gridDim = dim3((unsigned)(clusters * kCtas));
   cfg.blockDim = dim3((unsigned)kThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kLocalCtas;
+  attr[0].val.clusterDim.x = kCtas;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kb_cluster_loop<V, kLocalCtas>, a, h->local_list, h->n_local, cap);
+  return cudaLaunchKernelEx(&cfg, kb_cluster_loop<V, kCtas>, a, list, n, cap);
+}
+
+template <class V>
+cudaError_t launch_local(const lp_batch* h, const BatchArgs<V>& a, int64_t cap, cudaStream_t s) {
+  const int32_t n_tiny = h->n_local - h->n_wide;
+  cudaError_t e = cudaSuccess;
+  if (h->n_wide > 0 && n_tiny > 0) {
+    e = cudaEventRecord(h->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_cluster_loop<V, 1>(h, a, h->local_list + h->n_wide, n_tiny, cap, h->side_stream);
+    if (e == cudaSuccess) e = launch_cluster_loop<V, kLocalCtas>(h, a, h->local_list, h->n_wide, cap, s);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_join, 0);
+    return e;
+  }
+  if (h->n_wide > 0) return launch_cluster_loop<V, kLocalCtas>(h, a, h->local_list, h->n_wide, cap, s);
+  return launch_cluster_loop<V, 1>(h, a, h->local_list, n_tiny, cap, s);
 }
 
 template <class V>
@@ -885,11 +905,17 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
     tt += (int64_t)B[k].tT.size();
   }
   if (ta >= INT32_MAX || tt >= INT32_MAX) return fail(LP_ERR_TOO_LARGE, "too many tasks");
-  std::vector<int32_t> local;
+  // small instances: clustered ones first, then the tiny ones (at most two warp tasks per warp
+  // of one CTA in each phase), which one CTA runs with less synchronisation
+  std::vector<int32_t> local, tiny;
   for (int32_t k = 0; k < K; ++k) {
     h->inst[k].local = (nnz[k] <= h->prm.batch_local_nnz) ? 1 : 0;
-    if (h->inst[k].local) local.push_back(k);
+    if (!h->inst[k].local) continue;
+    if (std::max(h->inst[k].nta, h->inst[k].ntt) <= 2 * kWarps) tiny.push_back(k);
+    else local.push_back(k);
   }
+  h->n_wide = (int32_t)local.size();
+  local.insert(local.end(), tiny.begin(), tiny.end());
   h->n_local = (int32_t)local.size();
   h->ntA = (int32_t)ta;
   h->ntT = (int32_t)tt;
@@ -898,6 +924,9 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
   CK(cudaGetDevice(&h->device));
   CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
   CK(cudaStreamCreateWithFlags(&h->setup_stream, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   CK(h->alloc(&h->rpA, sm + 1)); CK(h->alloc(&h->ciA, snz)); CK(h->alloc(&h->valA, snz));
   CK(h->alloc(&h->rpT, sn + 1)); CK(h->alloc(&h->ciT, snz)); CK(h->alloc(&h->valT, snz));
   CK(h->alloc(&h->row_perm, sm)); CK(h->alloc(&h->col_perm, sn));

@@ -145,7 +145,9 @@ struct lp_batch {
   int32_t ntA = 0, ntT = 0;
   std::vector<BInst> inst;
   std::vector<double> eta;
-  int32_t n_local = 0;
+  int32_t n_local = 0, n_wide = 0;  // small instances; the first n_wide of them run on clusters
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int32_t* local_list = nullptr;  // device: the small instances (cluster loop)
   int grid = 1, gridS = 1;
   bool solved = false;
@@ -204,6 +206,9 @@ struct lp_batch {
     if (graph32) cudaGraphDestroy(graph32);
     for (void* p : allocations) cudaFree(p);
     if (setup_stream) cudaStreamDestroy(setup_stream);
+    if (side_stream) cudaStreamDestroy(side_stream);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
   }
 };
 
