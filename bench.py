@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--per-instance", action="store_true",
+                    help="batch workload: also solve every instance alone with lp_solve in FP64")
     ap.add_argument("--tol-run-max-iter", type=int, default=0,
                     help="> 0: one extra untimed solve with this cap to report time to tol")
     return ap.parse_args()
@@ -447,6 +449,45 @@ def batch_cpu_baseline(lps, tol, seconds):
                       f"20k iterations), single-threaded FP64 oracle, {t_used:.1f} s"}
 
 
+def batch_launches(sm, where, precision):
+    """Kernel launches of one lp_batch_solve: kb_init_ctl + kb_init; per stage, one kb_loop
+    launch (16 iterations) per body of the graph's while loop -- as many as the stage's slowest
+    grid instance needs, plus the body that sees every instance done -- and one launch per kind
+    of small instance (cluster, single block); between the stages of precision 1, kb_switch,
+    two kb_spmv and kb_warm (precision 2: kb_switch alone)."""
+    grid = where == 0
+    kinds = int(np.any(where == 1)) + int(np.any(where == 2))
+    it64 = sm["iters"] - sm["iters_fp32"]
+    stages = {0: [sm["iters"]], 1: [sm["iters_fp32"], it64], 2: [sm["iters_fp32"]]}[precision]
+    n = 2 + {0: 0, 1: 4, 2: 1}[precision]
+    for it in stages:
+        if grid.any():
+            n += math.ceil(int(it[grid].max()) / 16) + 1
+        n += kinds
+    return n
+
+
+def batch_per_instance(lps, args, stream):
+    """The same instances solved one after another by the single-instance solver (lp_solve, FP64,
+    same tolerance and iteration cap): the sum of the solves' device times, setup excluded."""
+    import torch
+    import paper_2507_14051_b300 as lpx
+    total_ms, opt, iters = 0.0, 0, 0
+    for lp in lps:
+        with lpx.Solver(lp) as s:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.solve(args.tol, args.max_iter, stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            r = s.result()
+            opt += int(r["status"] == lpx.LP_SOLVE_OPTIMAL)
+            iters += int(r["iters"])
+    return {"solve_s": total_ms / 1e3, "optimal": opt, "iters": iters,
+            "note": "lp_solve on each instance in turn, FP64, CUDA events around each solve (setup excluded)"}
+
+
 def run_batch(args):
     """Batch workload: one lp_batch_solve over every instance = one step."""
     import torch
@@ -471,6 +512,7 @@ def run_batch(args):
     b = lpx.BatchSolver(lps, precision=args.precision, switch_tol=args.switch_tol)
     setup_ms = 1e3 * (time.perf_counter() - t0)
     local_nnz = int(b.params.batch_local_nnz)
+    where = b.schedule()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         b.solve(args.tol, args.max_iter, sp)
@@ -493,10 +535,7 @@ def run_batch(args):
         total_ms += ms
         sm = b.summary()
         total_it += int(sm["iters"].sum())
-        grid_it = [int(i) for i, lp in zip(sm["iters"], lps) if lp.nnz > local_nnz]
-        stages = 2 if args.precision == 1 else 1
-        launches += stages * (2 + (math.ceil(max(grid_it) / 16) + 1 if grid_it else 0) + 1)
-        launches += 4 if args.precision == 1 else (1 if args.precision == 2 else 0)
+        launches += batch_launches(sm, where, args.precision)
         steps_out.append({"ms": ms, "optimal": int((sm["status"] == 1).sum()),
                           "iter_limit": int((sm["status"] == 2).sum()),
                           "iters_max": int(sm["iters"].max()), "iters_median": float(np.median(sm["iters"]))})
@@ -531,6 +570,7 @@ def run_batch(args):
         roof["fp32"]["frac"] = roof["fp32"]["achieved"] / hbm_peak
     roof["peak_source"] = f"HBM {peak_src} copy {hbm_peak} GB/s"
     b.close()
+    per_instance = batch_per_instance(lps, args, stream) if args.per_instance else None
     # end to end through the C ABI from host arrays: create (H2D inside) + solve + summary
     e2e_s, e2e_it = 0.0, 0
     for _ in range(args.e2e_steps):
@@ -559,7 +599,7 @@ def run_batch(args):
                        "batch_local_nnz": local_nnz, "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"independent batches x{world}"},
             "time_to_tol_s": elapsed_s / args.steps, "setup_ms": setup_ms, "steps_detail": steps_out,
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "cpu_baseline": cpu, "per_instance_fp64": per_instance,
             "e2e": {"value": e2e_it / e2e_s if e2e_s > 0 else None, "unit": "instance-iter/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                     "includes": "lp_batch_create from host arrays (validation, transposes, tasks, "

@@ -111,6 +111,15 @@ LP_API lp_status lp_tune_schedule(int32_t m, int32_t n, int64_t nnz, const int64
                                   const int32_t* col_idx, const double* val, const char* cache_path,
                                   int32_t* lane_target, int32_t* tile_rows, double* ms_out);
 
+/*
+ * Where each instance runs, fixed at lp_batch_create: where[k] (HOST int32[count]) is 0 for the
+ * cooperative grid loop (nnz[k] > p->batch_local_nnz), 1 for a cluster of 8 blocks and 2 for a
+ * single block (a small instance with at most two row tiles and two column tiles per warp of a
+ * block).  Small instances of both kinds run in two kernels launched side by side, one launch
+ * per kind present per solve stage.  Errors: LP_ERR_INVALID_ARG (NULL handle or where).
+ */
+LP_API lp_status lp_batch_schedule(lp_batch_handle h, int32_t* where);
+
 /* Frees the batch (waits for its work first).  NULL is a no-op. */
 LP_API void lp_batch_destroy(lp_batch_handle h);
 

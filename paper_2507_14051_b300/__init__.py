@@ -37,7 +37,7 @@ EXPORTED = ("lp_default_params", "lp_create", "lp_set_params", "lp_solve", "lp_g
             "lp_get_info", "lp_get_trace", "lp_destroy", "lp_last_error", "lp_time_kernels",
             "lp_debug_spmv", "lp_debug_layout", "lp_power_norm_noalloc",
             "lp_batch_create", "lp_batch_solve", "lp_batch_get", "lp_batch_get_all",
-            "lp_batch_time_loop", "lp_batch_destroy", "lp_tune_schedule",
+            "lp_batch_time_loop", "lp_batch_schedule", "lp_batch_destroy", "lp_tune_schedule",
             "lp_batch_set_data", "lp_batch_unroll", "lp_batch_unroll_vjp", "lp_batch_get_trace")
 
 
@@ -132,6 +132,7 @@ def load(path: str | None = None) -> C.CDLL:
         L.lp_batch_get.argtypes = [vp, C.c_int32, vp, vp, i32p, dp, i64p]
         L.lp_batch_get_all.argtypes = [vp, vp, vp, vp, vp, vp]
         L.lp_batch_time_loop.argtypes = [vp, C.c_int64, C.c_int32, vp, dp]
+        L.lp_batch_schedule.argtypes = [vp, vp]
         L.lp_batch_destroy.argtypes = [vp]
         L.lp_batch_destroy.restype = None
         for name in EXPORTED:
@@ -361,6 +362,12 @@ class BatchSolver:
         _check(load().lp_batch_get_all(self.h, st.ctypes.data, kkt.ctypes.data, it.ctypes.data,
                                        it32.ctypes.data, eta.ctypes.data), "lp_batch_get_all")
         return dict(status=st, kkt=kkt, iters=it, iters_fp32=it32, eta=eta)
+
+    def schedule(self):
+        """Where each instance runs: 0 grid loop, 1 cluster of 8 blocks, 2 one block."""
+        where = np.zeros(self.count, np.int32)
+        _check(load().lp_batch_schedule(self.h, where.ctypes.data), "lp_batch_schedule")
+        return where
 
     def set_data(self, c=None, l_c=None, u_c=None, l_v=None, u_v=None):
         """Replaces objectives / bounds (concatenated over instances, original order): numpy

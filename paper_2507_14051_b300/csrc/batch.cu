@@ -949,6 +949,7 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
   CK(cudaMemset(h->bc, 0, sizeof(BatchCtl)));
   CK(cudaMemset(h->done, 0, sizeof(int32_t) * K));
   CK(cudaMemcpy(h->d_inst, h->inst.data(), sizeof(BInst) * K, cudaMemcpyHostToDevice));
+  h->local_host = local;
   CK(h->alloc(&h->local_list, local.size()));
   if (!local.empty()) CK(cudaMemcpy(h->local_list, local.data(), sizeof(int32_t) * local.size(), cudaMemcpyHostToDevice));
 
@@ -1439,6 +1440,16 @@ lp_status lp_batch_get_all(lp_batch_handle hh, int32_t* status, double* kkt4, in
     if (iters_fp32) iters_fp32[k] = h->prm.precision == 1 ? c.iters32 : (h->prm.precision == 2 ? c.iters : 0);
     if (eta) eta[k] = h->eta[k];
   }
+  return LP_OK;
+}
+
+lp_status lp_batch_schedule(lp_batch_handle hh, int32_t* where) {
+  pdhg_set_last_error(std::string());
+  lp_batch* h = checked(hh);
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  if (!where) return fail(LP_ERR_INVALID_ARG, "NULL output");
+  for (int32_t k = 0; k < h->count; ++k) where[k] = h->inst[k].local ? 1 : 0;
+  for (int32_t q = h->n_wide; q < h->n_local; ++q) where[h->local_host[q]] = 2;
   return LP_OK;
 }
 

@@ -149,6 +149,7 @@ struct lp_batch {
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int32_t* local_list = nullptr;  // device: the small instances (cluster loop)
+  std::vector<int32_t> local_host;  // host copy of local_list
   int grid = 1, gridS = 1;
   bool solved = false;
   cudaStream_t last_stream = nullptr;

@@ -176,6 +176,7 @@ def test_batch_create_rejects_invalid_arguments():
     assert L.lp_batch_solve(None, 1e-8, 10, None) == lpx.LP_ERR_INVALID_ARG
     assert L.lp_batch_get(None, 0, None, None, None, None, None) == lpx.LP_ERR_INVALID_ARG
     assert L.lp_batch_get_all(None, None, None, None, None, None) == lpx.LP_ERR_INVALID_ARG
+    assert L.lp_batch_schedule(None, None) == lpx.LP_ERR_INVALID_ARG
     L.lp_batch_destroy(None)
 
 
