@@ -82,18 +82,20 @@ def workload_name(name: str, lp) -> str:
     return f"{base}, m={lp.m}, n={lp.n}, nnz={lp.nnz}, FP64"
 
 
-def kernel_work(lp):
-    """Algorithmic bytes and FP64 operations of one launch of each iteration kernel.
-    Bytes (what the method must move, FP64 values, 32-bit indices):
-      row kernel:    12 nnz (A values + columns) + 4 (m+1) row offsets + 8 n gathered xhat
-                     + 56 m (y, y0, l_c, u_c, y read; y, yhat written)
-      column kernel: 12 nnz + 4 (n+1) + 8 m gathered yhat + 56 n (x, x0, c, l_v, u_v read;
-                     x, xhat written)
-    FP64 operations (fma/add/mul issued by the kernel's arithmetic): one fma per nonzero plus
-    17 per row (row kernel) or 12 per column (column kernel)."""
+def kernel_work(lp, vb=8):
+    """Algorithmic bytes and FP64 operations of one launch of each iteration kernel, for values
+    of vb bytes (8: FP64 kernels; 4: the FP32 kernels of precision 1 and 2) and 32-bit indices.
+    Bytes (what the method must move):
+      row kernel:    (4 + vb) nnz (A values + columns) + 4 (m+1) row offsets + vb n gathered
+                     xhat + 7 vb m (y, y0, l_c, u_c, y read; y, yhat written)
+      column kernel: (4 + vb) nnz + 4 (n+1) + vb m gathered yhat + 7 vb n (x, x0, c, l_v, u_v
+                     read; x, xhat written)
+    FP64 operations (fma/add/mul issued by the FP64 kernels' arithmetic): one fma per nonzero
+    plus 17 per row (row kernel) or 12 per column (column kernel); None for the FP32 kernels."""
     m, n, nnz = lp.m, lp.n, lp.nnz
-    return {"k1_rows": (12 * nnz + 4 * (m + 1) + 8 * n + 56 * m, nnz + 17 * m),
-            "k2_cols": (12 * nnz + 4 * (n + 1) + 8 * m + 56 * n, nnz + 12 * n)}
+    f64 = vb == 8
+    return {"k1_rows": ((4 + vb) * nnz + 4 * (m + 1) + vb * n + 7 * vb * m, nnz + 17 * m if f64 else None),
+            "k2_cols": ((4 + vb) * nnz + 4 * (n + 1) + vb * m + 7 * vb * n, nnz + 12 * n if f64 else None)}
 
 
 def source_digest() -> str:
@@ -318,13 +320,16 @@ def run_ours(args):
     info = lpx.lp_get_info(solver.h)
 
     # live kernel durations (same kernels, launched one by one with events) for the roofline
+    # (the kernels of the solve's first stage: FP32 for precision 1 and 2)
     kt = lpx.lp_time_kernels(solver.h, args.kernel_iters, sp)
-    work = kernel_work(lp)
+    vb = 8 if args.precision == 0 else 4
+    work = kernel_work(lp, vb)
     hbm_peak, peak_src = load_peaks()
     if kt[1] == 0.0:  # the cooperative loop kernel runs kt[2] iterations per launch
         per_iter = int(kt[2])
+        ops = work["k1_rows"][1]
         work = {"k_loop": (per_iter * (work["k1_rows"][0] + work["k2_cols"][0]),
-                           per_iter * (work["k1_rows"][1] + work["k2_cols"][1]))}
+                           per_iter * (work["k1_rows"][1] + work["k2_cols"][1]) if ops is not None else None)}
         per = {"k_loop": kt[0]}
     else:
         per = {"k1_rows": kt[0], "k2_cols": kt[1]}
@@ -332,22 +337,25 @@ def run_ours(args):
     bytes_, ops = work[dom]
     ms = per[dom]
     gbs = bytes_ / (ms * 1e-3) / 1e9
-    gops = ops / (ms * 1e-3) / 1e9
-    f_hbm, f_alu = gbs / hbm_peak, gops / FP64_NOMINAL_GOPS
+    f_hbm = gbs / hbm_peak
+    gops = ops / (ms * 1e-3) / 1e9 if ops is not None else None
+    f_alu = gops / FP64_NOMINAL_GOPS if ops is not None else 0.0
     traffic = measured_traffic(dom, wl)
+    kname = dom if vb == 8 else dom + "<float>"
     if f_alu > f_hbm:
         roof = {"bound": "alu", "achieved": gops, "peak": FP64_NOMINAL_GOPS, "unit": "FP64 Gop/s",
-                "frac": f_alu, "traffic": traffic, "kernel": dom}
+                "frac": f_alu, "traffic": traffic, "kernel": kname}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm,
-                "traffic": traffic, "kernel": dom}
+                "traffic": traffic if vb == 8 else None, "kernel": kname}
     roof.update({"peak_source": f"HBM {peak_src} copy {hbm_peak} GB/s; FP64 nominal {FP64_NOMINAL_GOPS} Gop/s "
                                 f"(measured issue rate {FP64_MEASURED_GOPS})",
                  "kernels": {k: {"ms_per_launch": per[k], "iters_per_launch": int(kt[2]),
                                  "alg_bytes_per_launch": work[k][0], "fp64_ops_per_launch": work[k][1],
                                  "GB/s": work[k][0] / (per[k] * 1e-3) / 1e9,
                                  "frac_hbm": work[k][0] / (per[k] * 1e-3) / 1e9 / hbm_peak,
-                                 "frac_fp64": work[k][1] / (per[k] * 1e-3) / 1e9 / FP64_NOMINAL_GOPS}
+                                 "frac_fp64": (work[k][1] / (per[k] * 1e-3) / 1e9 / FP64_NOMINAL_GOPS
+                                               if work[k][1] is not None else None)}
                              for k in per},
                  "timing": f"mean of {int(kt[3])} launches, CUDA events on the solve stream"})
 

@@ -204,7 +204,10 @@ LP_API const char* lp_last_error(void);
 /*
  * Kernel timing for roofline reports: runs at least `iters` iterations of the same solve that
  * lp_solve would (tolerance 0, from the all-zero start), launching the iteration kernels one
- * by one on `stream` with CUDA events around each launch instead of through the graph.
+ * by one on `stream` with CUDA events around each launch instead of through the graph.  The
+ * kernels are those of the solve's first stage: FP64 for precision 0, FP32 for precision 1 and
+ * 2 (after which the handle holds no result: lp_get returns LP_ERR_NOT_SOLVED until the next
+ * lp_solve).
  *   persistent = 0: ms_out[0] / ms_out[1] mean duration of the row kernel (A x, dual step,
  *     restart control) and of the column kernel (A^T y, primal step, KKT test), ms_out[2] = 1;
  *   persistent = 1: ms_out[0] mean duration of one launch of the loop kernel, ms_out[1] = 0,

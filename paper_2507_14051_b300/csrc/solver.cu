@@ -823,31 +823,41 @@ void lp_destroy(lp_handle h) {
 
 const char* lp_last_error(void) { return g_err.c_str(); }
 
-lp_status lp_time_kernels(lp_handle h, int64_t iters, void* stream, double* ms_out) {
-  g_err.clear();
-  if (!h || !ms_out || iters < 1) return fail(LP_ERR_INVALID_ARG, "bad argument");
-  CK(cudaSetDevice(h->device));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace {
+
+// lp_time_kernels in precision V: the iteration kernels of V launched one by one, CUDA events
+// around each launch.
+template <class V>
+lp_status time_kernels(lp_solver* h, int64_t iters, cudaStream_t s, double* ms_out) {
   const bool loop = h->loop_active;
   const int32_t per = loop ? h->prm.unroll : 1;
   const int64_t launches = (iters + per - 1) / per;
-  lp_status st = enqueue_start<double>(h, 0.0, launches * per, s);
+  lp_status st = enqueue_start<V>(h, 0.0, launches * per, s);
   if (st != LP_OK) return st;
-  RowArgs ra{};
-  ColArgs ca{};
+  RowArgsT<V> ra{};
+  ColArgsT<V> ca{};
   fill_args(h, ra, ca);
   const int64_t nev = loop ? launches + 1 : 2 * launches + 1;
-  std::vector<cudaEvent_t> ev(nev);
+  std::vector<cudaEvent_t> ev(nev, nullptr);
+  struct Events {
+    std::vector<cudaEvent_t>& v;
+    ~Events() {
+      for (auto& e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } guard{ev};
   for (auto& e : ev) CK(cudaEventCreate(&e));
   CK(cudaEventRecord(ev[0], s));
   for (int64_t q = 0; q < launches; ++q) {
     if (loop) {
-      CK(launch_loop<double>(h, ra, ca, per, cudaGraphConditionalHandle{}, 0, s));
+      CK(launch_loop<V>(h, ra, ca, per, cudaGraphConditionalHandle{}, 0, s));
       CK(cudaEventRecord(ev[q + 1], s));
     } else {
-      iter_kernels<double>().rows<<<h->gridA, kThreads, 0, s>>>(ra);
+      iter_kernels<V>().rows<<<h->gridA, kThreads, 0, s>>>(ra);
       CK(cudaEventRecord(ev[2 * q + 1], s));
-      iter_kernels<double>().cols<<<h->gridT, kThreads, 0, s>>>(ca);
+      iter_kernels<V>().cols<<<h->gridT, kThreads, 0, s>>>(ca);
       CK(cudaEventRecord(ev[2 * q + 2], s));
     }
   }
@@ -865,12 +875,27 @@ lp_status lp_time_kernels(lp_handle h, int64_t iters, void* stream, double* ms_o
     a += m1;
     b += m2;
   }
-  for (auto& e : ev) cudaEventDestroy(e);
   ms_out[0] = a / (double)launches;
   ms_out[1] = b / (double)launches;
   ms_out[2] = (double)per;
   ms_out[3] = (double)launches;
-  h->solved = true;
+  return LP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lp_status lp_time_kernels(lp_handle h, int64_t iters, void* stream, double* ms_out) {
+  g_err.clear();
+  if (!h || !ms_out || iters < 1) return fail(LP_ERR_INVALID_ARG, "bad argument");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const lp_status st = h->prm.precision == 0 ? time_kernels<double>(h, iters, s, ms_out)
+                                             : time_kernels<float>(h, iters, s, ms_out);
+  if (st != LP_OK) return st;
+  // the FP32 timing leaves its iterate in the FP32 buffers: no result to read
+  h->solved = h->prm.precision == 0;
   h->last_stream = s;
   return LP_OK;
 }

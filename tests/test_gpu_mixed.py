@@ -173,3 +173,25 @@ def test_precision_is_fixed_at_create(cuda_device):
         s.set_params(precision=1)  # ignored: the FP32 buffers are made at create
         r = s.solve(1e-6, 100000).result()
     assert r["iters_fp32"] == 0
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_kernel_timing_in_the_first_stage_precision(cuda_device, precision, persistent):
+    """lp_time_kernels times the kernels of the solve's first stage; after an FP32 timing the
+    handle holds no result until the next solve, which is unchanged by the timing."""
+    lp = gen.small_lp(1)
+    with lpx.Solver(lp, precision=precision, persistent=persistent) as s:
+        ref = s.solve(1e-6, 20000).result()
+        kt = lpx.lp_time_kernels(s.h, 64)
+        assert kt[0] > 0.0 and kt[3] >= 1
+        assert (kt[1] == 0.0) == bool(persistent)
+        if precision == 0:
+            assert lpx.lp_get(s.h)[2] == 64
+        else:
+            with pytest.raises(lpx.LPError) as e:
+                lpx.lp_get(s.h)
+            assert e.value.code == lpx.LP_ERR_NOT_SOLVED
+        again = s.solve(1e-6, 20000).result()
+    assert again["status"] == ref["status"] and again["iters"] == ref["iters"]
+    assert np.array_equal(again["x"], ref["x"]) and np.array_equal(again["y"], ref["y"])
