@@ -22,7 +22,8 @@
 // Every instance advances by one iteration per loop trip; finished instances drop out of the
 // task space.  Results are deterministic (fixed summation orders everywhere).  Instances with
 // at most batch_local_nnz nonzeros skip the grid loop: each runs on a cluster of kLocalCtas CTAs
-// (kb_cluster_loop) with cluster barriers and distributed-shared-memory totals.
+// (kb_cluster_loop) with cluster barriers and distributed-shared-memory totals, or, if it has at
+// most two warp tasks per warp of one CTA in each phase, on a single CTA.
 //
 // The CUDA graph of each precision is a conditional while node around one cooperative launch
 // of kBatchUnroll iterations, so a solve needs no host synchronisation.  Mixed precision runs
@@ -245,9 +246,10 @@ __device__ __forceinline__ void refresh_active(const BatchArgs<V>& a, int32_t* s
 // The batch loop: up to `iters` iterations of every running instance.  Cooperative launch with
 // every block resident.  Block 0 counts the launch and (if use_cond) sets the graph's loop
 // condition: continue while an instance is running, unless the launches outran max_iter.
+// 3 blocks per SM in both precisions (4 for FP32 measured slower: more blocks at each barrier).
 template <class V>
-__global__ void __launch_bounds__(kThreads, 3) kb_loop(BatchArgs<V> a, int32_t iters,
-                                                       cudaGraphConditionalHandle cond, int32_t use_cond) {
+__global__ void __launch_bounds__(kThreads, 3)
+    kb_loop(BatchArgs<V> a, int32_t iters, cudaGraphConditionalHandle cond, int32_t use_cond) {
   cg::grid_group grid = cg::this_grid();
   __shared__ int32_t s_act[kMaxInst];
   __shared__ int32_t s_pa[kMaxInst + 1];
@@ -690,7 +692,7 @@ template <class V>
 cudaError_t launch_batch_loop(const lp_batch* h, const BatchArgs<V>& a, int32_t iters,
                               cudaGraphConditionalHandle cond, int32_t use_cond, cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)h->grid);
+  cfg.gridDim = dim3((unsigned)(sizeof(V) == sizeof(float) ? h->grid32 : h->grid));
   cfg.blockDim = dim3((unsigned)kThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
@@ -1052,9 +1054,8 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
   int occ64 = 0, occ32 = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, kb_loop<double>, kThreads, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, kb_loop<float>, kThreads, 0));
-  int occ = std::min(occ64, occ32);
-  if (occ < 1) occ = 1;
-  h->grid = occ * h->num_sms;
+  h->grid = std::max(1, occ64) * h->num_sms;
+  h->grid32 = std::max(1, occ32) * h->num_sms;
   h->gridS = std::max(1, std::min<int>(K, 8 * h->num_sms));
 
   // ---- step sizes ----

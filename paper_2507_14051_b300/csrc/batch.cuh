@@ -150,7 +150,7 @@ struct lp_batch {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int32_t* local_list = nullptr;  // device: the small instances (cluster loop)
   std::vector<int32_t> local_host;  // host copy of local_list
-  int grid = 1, gridS = 1;
+  int grid = 1, grid32 = 1, gridS = 1;  // loop grids (FP64, FP32), block-per-instance grid
   bool solved = false;
   cudaStream_t last_stream = nullptr;
   cudaStream_t setup_stream = nullptr;

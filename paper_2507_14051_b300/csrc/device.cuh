@@ -70,7 +70,6 @@ struct Ctl {
   double omega_used;     // omega of the last iteration performed
   int64_t iters32;       // mixed precision: iterations of the FP32 phase
   // FP32 phase stall guard: best relative KKT error seen at a check iteration, checks since,
-  // and omega / PID state at that check (restored for the FP64 phase after a stall)
   // and omega / PID state at that check (restored for the FP64 phase after a stall); the
   // check iterations store zhat in slot cand_slot of a two-slot buffer, best_slot holds the best
   int32_t patience, since_best, cand_slot, best_slot;

@@ -105,12 +105,13 @@ __device__ __forceinline__ void store_block_partials(double (&s)[kNumSums], int 
 // identical copy of the scalar state in shared memory: all blocks read the same partials in the
 // same order and run the same control code, so their decisions agree bit for bit and every
 // block leaves the loop at the same barrier.  Block 0 writes the state back, writes the trace,
-// and (if use_cond) sets the device-side loop condition of the enclosing graph.
+// and (if use_cond) sets the device-side loop condition of the enclosing graph.  FP64: 3
+// blocks per SM (80 registers); FP32: 4 (64 registers, no spills), more loads in flight for
+// the memory-bound FP32 phases.
 template <class V>
-__global__ void __launch_bounds__(kThreads, 3) k_loop(RowArgsT<V> ra, ColArgsT<V> ca, double* part_rows,
-                                                      double* part_cols, int32_t iters,
-                                                      cudaGraphConditionalHandle cond,
-                                                      int32_t use_cond) {
+__global__ void __launch_bounds__(kThreads, sizeof(V) == sizeof(float) ? 4 : 3)
+    k_loop(RowArgsT<V> ra, ColArgsT<V> ca, double* part_rows, double* part_cols, int32_t iters,
+           cudaGraphConditionalHandle cond, int32_t use_cond) {
   cg::grid_group grid = cg::this_grid();
   __shared__ Ctl sc;
   __shared__ RowStep rst;

@@ -35,7 +35,7 @@ struct lp_solver {
   lp_params prm{};
   std::vector<int32_t> row_perm, col_perm;  // permuted index -> original index
   BinTable binsA{}, binsT{};
-  int gridA = 1, gridT = 1, gridV = 1, gridL = 1, max_grid = 1;
+  int gridA = 1, gridT = 1, gridV = 1, gridL = 1, gridL32 = 1, max_grid = 1;
   bool loop_active = false;  // the graph body is the cooperative loop kernel
   bool loop_fits = false;    // both phases' grids fit on the device at once
   // device storage
@@ -176,7 +176,7 @@ template <class V>
 cudaError_t launch_loop(const lp_solver* h, const RowArgsT<V>& ra, const ColArgsT<V>& ca, int32_t iters,
                         cudaGraphConditionalHandle cond, int32_t use_cond, cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)h->gridL);
+  cfg.gridDim = dim3((unsigned)(sizeof(V) == sizeof(float) ? h->gridL32 : h->gridL));
   cfg.blockDim = dim3((unsigned)kThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
@@ -383,19 +383,24 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   h->gridT = grid_for_tasks((int64_t)h->binsT.ntasks + h->binsT.nchunks, h->num_sms, occT * h->num_sms);
   int occL = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occL, iter_kernels<double>().loop, kThreads, 0));
-  if (h->prm.precision != 0) {  // one loop grid serves both precisions
-    int occF = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occF, iter_kernels<float>().loop, kThreads, 0));
-    if (occF < occL) occL = occF;
-  }
   if (occL < 1) occL = 1;
   h->gridL = h->gridA > h->gridT ? h->gridA : h->gridT;
   h->loop_fits = h->gridL <= occL * h->num_sms;
   if (h->gridL > occL * h->num_sms) h->gridL = occL * h->num_sms;  // all blocks co-resident
+  if (h->prm.precision != 0) {
+    // the FP32 loop kernel has fewer registers (4 blocks per SM): its own grid, sized the same way
+    int occF = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occF, iter_kernels<float>().loop, kThreads, 0));
+    if (occF < 1) occF = 1;
+    const int gA = grid_for_tasks((int64_t)h->binsA.ntasks + h->binsA.nchunks, h->num_sms, occF * h->num_sms);
+    const int gT = grid_for_tasks((int64_t)h->binsT.ntasks + h->binsT.nchunks, h->num_sms, occF * h->num_sms);
+    h->gridL32 = gA > gT ? gA : gT;
+  }
   h->gridV = grid_for(n > m ? n : m, kThreads, 4 * h->num_sms);
   h->max_grid = h->gridA > h->gridT ? h->gridA : h->gridT;
   if (h->gridV > h->max_grid) h->max_grid = h->gridV;
   if (h->gridL > h->max_grid) h->max_grid = h->gridL;
+  if (h->gridL32 > h->max_grid) h->max_grid = h->gridL32;
 
   // ---- device buffers ----
   CK(h->alloc(&h->rpA, m + 1)); CK(h->alloc(&h->ciA, nnz)); CK(h->alloc(&h->valA, nnz));
@@ -831,7 +836,7 @@ namespace {
 // around each launch.
 template <class V>
 lp_status time_kernels(lp_solver* h, int64_t iters, cudaStream_t s, double* ms_out) {
-  const bool loop = h->loop_active;
+  const bool loop = sizeof(V) == sizeof(float) ? h->loop_active32 : h->loop_active;
   const int32_t per = loop ? h->prm.unroll : 1;
   const int64_t launches = (iters + per - 1) / per;
   lp_status st = enqueue_start<V>(h, 0.0, launches * per, s);
