@@ -641,6 +641,24 @@ __global__ void __launch_bounds__(kThreads) kb_pw_cols(const BInst* __restrict__
   }
 }
 
+// y = A x over the tasks of the instances whose power iteration is still running (a finished
+// instance's vectors are no longer read).
+__global__ void __launch_bounds__(kThreads) kb_pw_spmv(const int4* __restrict__ tasks, int32_t ntasks,
+                                                       const int32_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ ci,
+                                                       const double* __restrict__ val,
+                                                       const double* __restrict__ x, double* __restrict__ y,
+                                                       const BPw* __restrict__ pw) {
+  const LoadPolicy pol = make_policy();
+  const int lane = threadIdx.x & 31;
+  for (int j = blockIdx.x * kWarps + (threadIdx.x >> 5); j < ntasks; j += gridDim.x * kWarps) {
+    const int4 td = tasks[j];
+    if (pw[td.w].done) continue;  // warp-uniform
+    const double v = tile_spmv(rp, ci, val, x, td.x, td.y, task_lanes(td), task_per_lane(td), lane, pol);
+    if (lane < td.y) y[td.x + lane] = v;
+  }
+}
+
 __global__ void kb_pw_count(const BPw* __restrict__ pw, int32_t count, BatchCtl* bc) {
   __shared__ unsigned int left;
   if (threadIdx.x == 0) left = 0;
@@ -807,9 +825,9 @@ lp_status batch_power_iteration(lp_batch* h) {
     const int64_t rest = h->prm.power_max_iter - it;
     const int batch = rest < kPwBatch ? (int)rest : kPwBatch;
     for (int q = 0; q < batch; ++q) {
-      kb_spmv<double><<<gA, kThreads, 0, s>>>(h->tasksA, h->ntA, h->rpA, h->ciA, h->valA, u, w);
+      kb_pw_spmv<<<gA, kThreads, 0, s>>>(h->tasksA, h->ntA, h->rpA, h->ciA, h->valA, u, w, h->pw);
       kb_pw_rows<<<h->gridS, kThreads, 0, s>>>(h->d_inst, h->count, w, h->pw, h->prm.power_tol);
-      kb_spmv<double><<<gT, kThreads, 0, s>>>(h->tasksT, h->ntT, h->rpT, h->ciT, h->valT, w, u);
+      kb_pw_spmv<<<gT, kThreads, 0, s>>>(h->tasksT, h->ntT, h->rpT, h->ciT, h->valT, w, u, h->pw);
       kb_pw_cols<<<h->gridS, kThreads, 0, s>>>(h->d_inst, h->count, u, h->pw);
     }
     kb_pw_count<<<1, kThreads, 0, s>>>(h->pw, h->count, h->bc);
