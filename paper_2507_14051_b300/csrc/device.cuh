@@ -306,27 +306,31 @@ __device__ __forceinline__ void for_each_row(const BinTable& bins, const int32_t
                   [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) { epi(i, v, acc); });
 }
 
-// Sums the first nsums of each thread's v[] over the block in a fixed order (shared-memory
-// halving tree down to one warp, then a warp butterfly); the totals end in thread 0's v[].
-// The whole block must call it.
+// Sums the first nsums (<= kNumSums <= kWarps) of each thread's v[] over the block in a fixed
+// order: warp q adds sum q -- lane L the values of threads L, L + 32, ... as a pairwise tree,
+// then a butterfly over the lanes -- so the sums' FP64 additions run on different warps at once
+// (an FP64 warp instruction occupies the pipe as long as a full one whatever its active lanes,
+// so a serial chain of them is what a block reduction costs).  The totals end in thread 0's
+// v[] (v[q] = 0 for q >= nsums).  The whole block must call it.
 __device__ __forceinline__ void block_reduce(double (&v)[kNumSums], int nsums) {
+  static_assert(kNumSums <= kWarps && kWarps == 8, "one warp per sum, 8 values per lane");
   __shared__ double red[kNumSums][kThreads];
-  const int tid = threadIdx.x;
+  __shared__ double out[kNumSums];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int q = 0; q < kNumSums; ++q) red[q][tid] = v[q];
   __syncthreads();
-#pragma unroll
-  for (int w = kThreads / 2; w >= 32; w >>= 1) {
-    if (tid < w) {
-#pragma unroll
-      for (int q = 0; q < kNumSums; ++q)
-        if (q < nsums) red[q][tid] += red[q][tid + w];
-    }
-    __syncthreads();
+  if (warp < nsums) {
+    const double* r = red[warp];
+    const double a = (r[lane] + r[lane + 32]) + (r[lane + 64] + r[lane + 96]);
+    const double b = (r[lane + 128] + r[lane + 160]) + (r[lane + 192] + r[lane + 224]);
+    const double t = warp_sum(a + b);
+    if (lane == 0) out[warp] = t;
   }
-  if (tid < 32) {
+  __syncthreads();
+  if (tid == 0) {
 #pragma unroll
-    for (int q = 0; q < kNumSums; ++q) v[q] = q < nsums ? warp_sum(red[q][tid]) : 0.0;
+    for (int q = 0; q < kNumSums; ++q) v[q] = q < nsums ? out[q] : 0.0;
   }
   __syncthreads();
 }
@@ -350,26 +354,29 @@ __device__ __forceinline__ bool block_sums_last(double (&s)[kNumSums], int nsums
   return is_last;
 }
 
-// In the last block (all threads): totals over the blocks' partials and, if bins is given, the
-// long rows' epilogue contributions.  Thread t adds blocks t, t + kThreads, ... and long rows
-// t, t + kThreads, ..., then block_reduce; the totals end in thread 0's tot[].
+// Totals over the blocks' partials and, if bins is given, the long rows' epilogue contributions
+// (all threads of the block call it; every thread gets the totals).  Warp q adds sum q: lane L
+// the partials of blocks L, L + 32, ... and then of long rows L, L + 32, ..., in that order,
+// then a butterfly over the lanes.
 __device__ __forceinline__ void block_totals(const double* partials, int nblocks, int nsums,
                                              const BinTable* bins, double (&tot)[kNumSums]) {
-#pragma unroll
-  for (int q = 0; q < kNumSums; ++q) tot[q] = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += kThreads) {
-#pragma unroll
-    for (int q = 0; q < kNumSums; ++q)
-      if (q < nsums) tot[q] += __ldcg(partials + b * kNumSums + q);
-  }
-  if (bins) {
-    for (int r = threadIdx.x; r < bins->long_rows; r += kThreads) {
-#pragma unroll
-      for (int q = 0; q < kNumSums; ++q)
-        if (q < nsums) tot[q] += __ldcg(bins->contrib + r * kNumSums + q);
+  __shared__ double out[kNumSums];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < nsums) {
+    double a = 0.0;
+#pragma unroll 4
+    for (int b = lane; b < nblocks; b += 32) a += __ldcg(partials + b * kNumSums + warp);
+    if (bins) {
+#pragma unroll 4
+      for (int r = lane; r < bins->long_rows; r += 32) a += __ldcg(bins->contrib + r * kNumSums + warp);
     }
+    a = warp_sum(a);
+    if (lane == 0) out[warp] = a;
   }
-  block_reduce(tot, nsums);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kNumSums; ++q) tot[q] = q < nsums ? out[q] : 0.0;
+  __syncthreads();
 }
 
 }  // namespace pdhg
