@@ -620,20 +620,38 @@ def run_batch(args):
     return 0
 
 
-def diff_work(lps, K, C):
-    """Algorithmic bytes of one forward + backward pass of the unrolled layer (FP64 values, 32-bit
-    indices): forward K iterations of two SpMVs (12 nnz + 4 (rows+1) + 8 gathered entries per
-    row side) and the elementwise passes (column: 8 x 9 n, row: 8 x 8 m); backward recomputes
-    the forward once more (from the checkpoints) and runs K adjoint iterations of the same size
-    plus one add pass (8 x 3 m).  Clamp codes: 1 byte per entry per iteration, written and read."""
-    tot = 0
+def diff_iter_bytes(lps):
+    """Algorithmic bytes of one unrolled iteration of each segment kernel over the batch (FP64
+    values, 32-bit indices): both SpMVs (12 nnz + 4 (rows+1) + 8 gathered entries per row side)
+    plus the elementwise work -- forward: column 8 x 9 n, row 8 x 8 m; forward with clamp codes:
+    1 byte more per entry; adjoint: column 8 x 11 n, row 8 x 11 m, codes read (m + n)."""
+    out = {"kd_fwd_loop": 0, "kd_fwd_loop_codes": 0, "kd_bwd_loop": 0}
     for lp in lps:
         m, n, z = lp.m, lp.n, lp.nnz
         spmv = (12 * z + 4 * (n + 1) + 8 * m) + (12 * z + 4 * (m + 1) + 8 * n)
-        fwd = spmv + 8 * 9 * n + 8 * 8 * m
-        bwd = spmv + 8 * 11 * n + 8 * 8 * m + 8 * 3 * m + 2 * (m + n)
-        tot += K * (2 * fwd + bwd)
-    return tot
+        out["kd_fwd_loop"] += spmv + 8 * 9 * n + 8 * 8 * m
+        out["kd_fwd_loop_codes"] += spmv + 8 * 9 * n + 8 * 8 * m + (m + n)
+        out["kd_bwd_loop"] += spmv + 8 * 11 * n + 8 * 11 * m + (m + n)
+    return out
+
+
+def diff_work(lps, K, C):
+    """Algorithmic bytes of one forward + backward pass of the unrolled layer: K forward
+    iterations, K recomputed ones with clamp codes (from the checkpoints) and K adjoint ones."""
+    b = diff_iter_bytes(lps)
+    return K * (b["kd_fwd_loop"] + b["kd_fwd_loop_codes"] + b["kd_bwd_loop"])
+
+
+def diff_launches(K, C, where):
+    """Kernel launches of one layer step (set_data of all five vectors, unroll with x and y out,
+    vjp with dL/dx, dL/dy and three gradients): set_data 5 gathers + 3 scatters + kd_norms;
+    unroll kb_init_ctl + kb_init + one kb_loop per 16 iterations (if any grid instance) + one
+    launch per kind of small instance + kd_sched_table + one kd_fwd_loop per segment + 2
+    scatters; vjp 2 gathers + per segment kd_fwd_loop and kd_bwd_loop + 3 scatters."""
+    nck = -(-K // C)
+    kinds = int(np.any(where == 1)) + int(np.any(where == 2))
+    grid = -(-K // 16) if np.any(where == 0) else 0
+    return 9 + (2 + grid + kinds + 1 + nck + 2) + (2 + 2 * nck + 3)
 
 
 def run_diff(args):
@@ -694,6 +712,14 @@ def run_diff(args):
     hbm_peak, peak_src = load_peaks()
     bytes_step = diff_work(lps, K, C)
     achieved = bytes_step / (elapsed_s / args.steps) / 1e9
+    # the segment kernels, timed live one launch at a time (CUDA events on the stream)
+    sp = torch.cuda.current_stream().cuda_stream
+    ms_f, ms_fc, ms_b, per = layer.batch.time_unroll(3, sp)
+    ib = diff_iter_bytes(lps)
+    kms = {"kd_fwd_loop": ms_f, "kd_fwd_loop_codes": ms_fc, "kd_bwd_loop": ms_b}
+    nseg = -(-K // C)
+    dom = max(kms, key=lambda k: kms[k] * nseg)
+    k_gbs = {k: ib[k] * per / (kms[k] * 1e-3) / 1e9 for k in kms}
     # end to end: objective and bounds from pinned host memory, loss and gradients back to host
     host = {k: v.cpu().numpy() for k, v in base.items()}
     pinned = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in host.items()}
@@ -727,13 +753,17 @@ def run_diff(args):
                        "l2": "working set 61 MB fits L2; not flushed (it is re-read every unrolled step)",
                        "parallelism": f"independent batches x{world}"},
             "unrolled_iters_per_s": value * K, "setup_ms": setup_ms,
-            "roofline": {"bound": "hbm", "kernel": "whole step (forward, recompute, adjoint)", "unit": "GB/s",
-                         "achieved": achieved, "peak": hbm_peak, "frac": achieved / hbm_peak, "traffic": None,
-                         "alg_bytes_per_step": bytes_step, "peak_source": f"HBM {peak_src} copy {hbm_peak} GB/s"},
+            "roofline": {"bound": "hbm", "kernel": dom, "unit": "GB/s", "achieved": k_gbs[dom], "peak": hbm_peak,
+                         "frac": k_gbs[dom] / hbm_peak, "traffic": None,
+                         "kernels": {k: {"ms_per_launch": kms[k], "iters_per_launch": per,
+                                         "alg_bytes_per_iter": ib[k], "GB/s": k_gbs[k]} for k in kms},
+                         "timing": "mean of 3 launches of each segment kernel, CUDA events on the stream",
+                         "whole_step": {"alg_bytes": bytes_step, "GB/s": achieved},
+                         "peak_source": f"HBM {peak_src} copy {hbm_peak} GB/s"},
             "cpu_baseline": cpu,
             "e2e": {"value": args.e2e_steps / e2e_s, "unit": "forward+backward steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
-            "gpu_launches": args.steps * (2 + 2 * 5 * K + 5 * K + 10), "clocks": clocks,
+            "gpu_launches": args.steps * diff_launches(K, C, layer.batch.schedule()), "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     layer.close()

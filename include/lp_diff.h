@@ -67,6 +67,18 @@ LP_API lp_status lp_batch_unroll_vjp(lp_batch_handle h, const double* dl_dx, con
 LP_API lp_status lp_batch_get_trace(lp_batch_handle h, int32_t k, double* out, int64_t cap,
                                     int64_t* rows);
 
+/*
+ * Kernel timing for roofline reports, after an lp_batch_unroll: runs the first segment's kernels
+ * `reps` (>= 1) times each on `stream` with CUDA events around each launch and returns mean
+ * milliseconds per launch in ms_out (HOST double[4]): [0] the forward segment kernel without
+ * clamp codes (as in lp_batch_unroll), [1] with codes (the recomputation of lp_batch_unroll_vjp),
+ * [2] the adjoint segment kernel, [3] iterations per launch (min(K, checkpoint_every)).  The
+ * checkpoints and the schedule are left as they were, so a following lp_batch_unroll_vjp is
+ * unchanged; the adjoint state is overwritten (zeroed first).  Synchronous.
+ * Errors: LP_ERR_INVALID_ARG, LP_ERR_NOT_SOLVED (no forward yet), LP_ERR_CUDA.
+ */
+LP_API lp_status lp_batch_time_unroll(lp_batch_handle h, int32_t reps, void* stream, double* ms_out);
+
 #ifdef __cplusplus
 }
 #endif

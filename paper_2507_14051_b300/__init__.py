@@ -38,7 +38,8 @@ EXPORTED = ("lp_default_params", "lp_create", "lp_set_params", "lp_solve", "lp_g
             "lp_debug_spmv", "lp_debug_layout", "lp_power_norm_noalloc",
             "lp_batch_create", "lp_batch_solve", "lp_batch_get", "lp_batch_get_all",
             "lp_batch_time_loop", "lp_batch_schedule", "lp_batch_destroy", "lp_tune_schedule",
-            "lp_batch_set_data", "lp_batch_unroll", "lp_batch_unroll_vjp", "lp_batch_get_trace")
+            "lp_batch_set_data", "lp_batch_unroll", "lp_batch_unroll_vjp", "lp_batch_get_trace",
+            "lp_batch_time_unroll")
 
 
 class lp_params(C.Structure):
@@ -128,6 +129,7 @@ def load(path: str | None = None) -> C.CDLL:
         L.lp_batch_unroll.argtypes = [vp, C.c_int64, C.c_int64, vp, vp, vp]
         L.lp_batch_unroll_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.lp_batch_get_trace.argtypes = [vp, C.c_int32, dp, C.c_int64, i64p]
+        L.lp_batch_time_unroll.argtypes = [vp, C.c_int32, vp, dp]
         L.lp_batch_solve.argtypes = [vp, C.c_double, C.c_int64, vp]
         L.lp_batch_get.argtypes = [vp, C.c_int32, vp, vp, i32p, dp, i64p]
         L.lp_batch_get_all.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -395,6 +397,14 @@ class BatchSolver:
         _check(load().lp_batch_get_trace(self.h, k, out.ctypes.data_as(C.POINTER(C.c_double)), int(cap),
                                          C.byref(rows)), "lp_batch_get_trace")
         return out[: rows.value]
+
+    def time_unroll(self, reps=3, stream=None):
+        """After unroll(): mean ms per launch of the forward segment kernel without and with clamp
+        codes and of the adjoint segment kernel, and the iterations per launch."""
+        out = np.zeros(4)
+        _check(load().lp_batch_time_unroll(self.h, int(reps), stream, out.ctypes.data_as(C.POINTER(C.c_double))),
+               "lp_batch_time_unroll")
+        return float(out[0]), float(out[1]), float(out[2]), int(out[3])
 
     def time_loop(self, iters, fp64=True, stream=None):
         """(ms per launch of the batch loop kernel, iterations per launch)."""

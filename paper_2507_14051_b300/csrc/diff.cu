@@ -621,4 +621,62 @@ lp_status lp_batch_unroll_vjp(lp_batch_handle h, const double* dl_dx, const doub
   return LP_OK;
 }
 
+lp_status lp_batch_time_unroll(lp_batch_handle h, int32_t reps, void* stream, double* ms_out) {
+  pdhg_set_last_error(std::string());
+  if (!h || !ms_out || reps < 1) return fail(LP_ERR_INVALID_ARG, "bad argument");
+  if (!h->diff || !h->diff->forward_done) return fail(LP_ERR_NOT_SOLVED, "no lp_batch_unroll to time");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Diff* d = h->diff;
+  const int64_t n = h->sum_n, m = h->sum_m;
+  const int32_t len = (int32_t)std::min(d->C, d->K);
+  lp_status st = grow(&d->mx, &d->cap_mask, d->C * std::max<int64_t>(n + m, 1));
+  if (st != LP_OK) return st;
+  uint8_t* cx = d->mx;
+  uint8_t* cy = d->mx + (size_t)len * (size_t)n;
+  for (double* p : {d->lx, d->lx0, d->gc, d->glv, d->guv, d->sx}) {
+    st = zero(p, n, s);
+    if (st != LP_OK) return st;
+  }
+  for (double* p : {d->ly, d->ly0, d->glc, d->guc, d->sy}) {
+    st = zero(p, m, s);
+    if (st != LP_OK) return st;
+  }
+  std::vector<cudaEvent_t> ev(6 * (size_t)reps, nullptr);
+  struct Events {
+    std::vector<cudaEvent_t>& v;
+    ~Events() {
+      for (auto& e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } guard{ev};
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  for (int kind = 0; kind < 3; ++kind) {
+    for (int32_t r = 0; r < reps; ++r) {
+      cudaEvent_t e0 = ev[2 * ((size_t)kind * reps + r)], e1 = ev[2 * ((size_t)kind * reps + r) + 1];
+      if (kind < 2) st = load_ck(h, 0, s);
+      if (st != LP_OK) return st;
+      CK(cudaEventRecord(e0, s));
+      if (kind == 0) st = forward_run(h, 0, len, nullptr, nullptr, s);
+      else if (kind == 1) st = forward_run(h, 0, len, cx, cy, s);
+      else st = backward_run(h, 0, d->K, len, cx, cy, s);
+      if (st != LP_OK) return st;
+      CK(cudaEventRecord(e1, s));
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  for (int kind = 0; kind < 3; ++kind) {
+    double tot = 0.0;
+    for (int32_t r = 0; r < reps; ++r) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev[2 * ((size_t)kind * reps + r)], ev[2 * ((size_t)kind * reps + r) + 1]));
+      tot += ms;
+    }
+    ms_out[kind] = tot / reps;
+  }
+  ms_out[3] = (double)len;
+  h->last_stream = s;
+  return LP_OK;
+}
+
 }  // extern "C"

@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(V) == sizeof(float) ? 4 : 3)
   __shared__ Ctl sc;
   __shared__ RowStep rst;
   __shared__ ColStepT<V> cst;
+  __shared__ Halpern hw;
   if (threadIdx.x == 0) sc = *ra.ctl;
   __syncthreads();
   const LoadPolicy pol = make_policy();
@@ -136,9 +137,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(V) == sizeof(float) ? 4 : 3)
     const int nr = st.check ? 5 : 3;
     store_block_partials(s, nr, part_rows);
     grid.sync();
+    // the last warp is idle while warps 0..nr-1 add the totals: it computes the next Halpern
+    // weights (two FP64 divisions) so that the serial control does not
+    if (threadIdx.x == kThreads - 32) hw = halpern_weights(sc.k, sc.gamma);
     double tot[kNumSums];
     block_totals(part_rows, gridDim.x, nr, &ra.bins, tot);
-    if (threadIdx.x == 0) row_control(sc, tot, st.check, trace);
+    if (threadIdx.x == 0) row_control(sc, tot, st.check, trace, &hw);
     __syncthreads();
     if (sc.done) break;
     // ---- column phase

@@ -167,10 +167,26 @@ __device__ __forceinline__ void row_prefetch(const RowArgsT<V>& a, const RowStep
   prefetch_l1(a.uc + i);
 }
 
+// Reflected Halpern weights of epoch step k + 1 (Section 3): x' = ha xhat + hb x + he x0 with
+// ha = (k+1)/(k+2) (1 + gamma), hb = -(k+1)/(k+2) gamma, he = 1/(k+2).
+struct Halpern {
+  double ha, hb, he;
+};
+__device__ __forceinline__ Halpern halpern_weights(int64_t k, double gamma) {
+  const double kk = (double)k;
+  const double aw = (kk + 1.0) / (kk + 2.0);
+  Halpern h;
+  h.ha = aw * (1.0 + gamma);
+  h.hb = -aw * gamma;
+  h.he = 1.0 / (kk + 2.0);
+  return h;
+}
+
 // Scalar control after the row phase of iteration c.t, on totals tot[0..2] (and tot[3..4] on
-// check iterations).  Writes the trace row if `trace` is given.
+// check iterations).  Writes the trace row if `trace` is given.  `next` (or NULL): the weights
+// halpern_weights(c.k, c.gamma), computed beforehand off this serial path.
 __device__ __forceinline__ void row_control(Ctl& c, const double (&tot)[kNumSums], bool check,
-                                            double* trace) {
+                                            double* trace, const Halpern* next = nullptr) {
   const int64_t t = c.t;
   const double eta = c.eta, om = c.omega;
   const double r2 = fma(c.w_over_eta, c.sxx, fma(c.inv_eta_w, tot[0], 2.0 * tot[1]));
@@ -210,11 +226,10 @@ __device__ __forceinline__ void row_control(Ctl& c, const double (&tot)[kNumSums
     c.restarts += 1;
     if (tr) trace[4 * t + 2] = 1.0;
   } else {
-    const double kk = (double)k;
-    const double aw = (kk + 1.0) / (kk + 2.0);
-    c.ha = aw * (1.0 + c.gamma);
-    c.hb = -aw * c.gamma;
-    c.he = 1.0 / (kk + 2.0);
+    const Halpern h = next ? *next : halpern_weights(k, c.gamma);
+    c.ha = h.ha;
+    c.hb = h.hb;
+    c.he = h.he;
     c.r_prev = r;
     c.k = k + 1;
   }

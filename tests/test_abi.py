@@ -177,6 +177,9 @@ def test_batch_create_rejects_invalid_arguments():
     assert L.lp_batch_get(None, 0, None, None, None, None, None) == lpx.LP_ERR_INVALID_ARG
     assert L.lp_batch_get_all(None, None, None, None, None, None) == lpx.LP_ERR_INVALID_ARG
     assert L.lp_batch_schedule(None, None) == lpx.LP_ERR_INVALID_ARG
+    assert L.lp_batch_unroll(None, 10, 5, None, None, None) == lpx.LP_ERR_INVALID_ARG
+    assert L.lp_batch_unroll_vjp(None, None, None, None, None, None, None, None, None) == lpx.LP_ERR_INVALID_ARG
+    assert L.lp_batch_time_unroll(None, 1, None, None) == lpx.LP_ERR_INVALID_ARG
     L.lp_batch_destroy(None)
 
 

@@ -33,7 +33,7 @@ def offsets(lps, attr):
     return np.concatenate([[0], np.cumsum([getattr(lp, attr) for lp in lps])])
 
 
-def gpu_unroll(lps, K, ckpt, etas, loss_grad_x, loss_grad_y=None, local=16384, **params):
+def gpu_unroll(lps, K, ckpt, etas, loss_grad_x, loss_grad_y=None, local=16384, time_unroll=False, **params):
     import torch
     dev = "cuda"
     with lpx.BatchSolver(lps, eta=etas, batch_local_nnz=local, **params) as b:
@@ -44,6 +44,9 @@ def gpu_unroll(lps, K, ckpt, etas, loss_grad_x, loss_grad_y=None, local=16384, *
         xs, ys = x.cpu().numpy(), y.cpu().numpy()
         gx = torch.tensor(loss_grad_x(xs), device=dev)
         gy = None if loss_grad_y is None else torch.tensor(loss_grad_y(ys), device=dev)
+        if time_unroll:
+            ms_f, ms_fc, ms_b, per = b.time_unroll(2)
+            assert ms_f > 0.0 and ms_fc > 0.0 and ms_b > 0.0 and per == min(K, ckpt)
         g = {k: torch.zeros(nx if k in ("c", "l_v", "u_v") else ny, dtype=torch.float64, device=dev)
              for k in ("c", "l_c", "u_c", "l_v", "u_v")}
         b.unroll_vjp(gx, gy, g["c"], g["l_c"], g["u_c"], g["l_v"], g["u_v"])
@@ -169,6 +172,17 @@ def test_checkpoint_spacing_does_not_change_the_result(cuda_device):
         assert np.array_equal(r[0], runs[0][0])
         for name in r[2]:
             assert np.array_equal(r[2][name], runs[0][2][name])
+
+
+def test_kernel_timing_leaves_the_gradient_unchanged(cuda_device):
+    """lp_batch_time_unroll between the forward and the reverse pass changes neither."""
+    lps = instances()[:2]
+    gxf = lambda x: np.cos(x)
+    a = gpu_unroll(lps, 90, 30, None, gxf)
+    b = gpu_unroll(lps, 90, 30, None, gxf, time_unroll=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for name in a[2]:
+        assert np.array_equal(a[2][name], b[2][name])
 
 
 def test_set_data_equals_a_fresh_batch(cuda_device):
