@@ -214,23 +214,111 @@ __device__ __forceinline__ V strided_dot(const int32_t* __restrict__ ci, const V
   return strided_dot_n<kIlp, V, kCached>(ci, val, xg, first, e, stride, pol);
 }
 
+// Two partial dot products of one lane, over [fa, ea) and [fb, eb) with the same stride, their
+// loads issued together (twice the loads in flight of strided_dot_n); each is accumulated in
+// entry order exactly as strided_dot_n would.
+template <int ILP, class V>
+__device__ __forceinline__ void strided_dot_pair(const int32_t* __restrict__ ci, const V* __restrict__ val,
+                                                 const V* __restrict__ xg, int fa, int ea, int fb, int eb,
+                                                 int stride, const LoadPolicy& pol, V& ra, V& rb) {
+  V acc_a = V(0), acc_b = V(0);
+  for (int k0 = 0; fa + k0 < ea || fb + k0 < eb; k0 += ILP * stride) {
+    V va[ILP], vb[ILP];
+    int ca[ILP], cb[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+      const int ka = fa + k0 + u * stride, kb = fb + k0 + u * stride;
+      if (ka < ea) {
+        va[u] = ld_stream(val + ka, pol.stream);
+        ca[u] = ld_stream(ci + ka, pol.stream);
+      } else {
+        va[u] = V(0);
+        ca[u] = -1;
+      }
+      if (kb < eb) {
+        vb[u] = ld_stream(val + kb, pol.stream);
+        cb[u] = ld_stream(ci + kb, pol.stream);
+      } else {
+        vb[u] = V(0);
+        cb[u] = -1;
+      }
+    }
+    V xa[ILP], xb[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+      xa[u] = ca[u] >= 0 ? ld_gather(xg + ca[u], pol.keep) : V(0);
+      xb[u] = cb[u] >= 0 ? ld_gather(xg + cb[u], pol.keep) : V(0);
+    }
+#pragma unroll
+    for (int u = 0; u < ILP; ++u)
+      if (ca[u] >= 0) acc_a = fma(va[u], xa[u], acc_a);
+#pragma unroll
+    for (int u = 0; u < ILP; ++u)
+      if (cb[u] >= 0) acc_b = fma(vb[u], xb[u], acc_b);
+  }
+  ra = acc_a;
+  rb = acc_b;
+}
+
+// One tile task of a BinTable: its rows, shape, and lane L's row bounds (L < nrows; 0 else).
+struct TileTask {
+  int row0, nrows, lanes, per_lane, b, e;
+};
+
+__device__ __forceinline__ TileTask tile_task(const BinTable& bins, const int32_t* __restrict__ rp, int task,
+                                              int lane) {
+  const Bin B = bins.bin[find_bin(bins, task - bins.nchunks)];
+  TileTask t;
+  t.row0 = B.row0 + (task - bins.nchunks - B.task0) * B.rows_per_tile;
+  t.nrows = min(B.rows_per_tile, B.row1 - t.row0);
+  t.lanes = B.lanes;
+  t.per_lane = B.per_lane;
+  t.b = 0;
+  t.e = 0;
+  if (lane < t.nrows) {
+    t.b = rp[t.row0 + lane];
+    t.e = rp[t.row0 + lane + 1];
+  }
+  return t;
+}
+
+// Largest entries per lane for which two tiles run side by side (tile_spmv_pair).
+constexpr int kPairMaxPerLane = 4;
+
+// Two single-pass tiles with the same lanes per row G (nrows * G <= 32 each, per_lane <=
+// kPairMaxPerLane), their SpMVs interleaved: lane L returns row L's value of each (garbage for
+// L >= nrows).  Each value is summed exactly as tile_spmv sums it.
+template <class V>
+__device__ __forceinline__ void tile_spmv_pair(const int32_t* __restrict__ ci, const V* __restrict__ val,
+                                               const V* __restrict__ xg, const TileTask& a, const TileTask& b,
+                                               int lane, const LoadPolicy& pol, V& va, V& vb) {
+  const int G = a.lanes, g = lane / G, sub = lane - g * G;
+  const int ba = __shfl_sync(kFull, a.b, g), ea = __shfl_sync(kFull, a.e, g);
+  const int bb = __shfl_sync(kFull, b.b, g), eb = __shfl_sync(kFull, b.e, g);
+  V acc_a, acc_b;
+  if (max(a.per_lane, b.per_lane) <= 2)
+    strided_dot_pair<2, V>(ci, val, xg, ba + sub, ea, bb + sub, eb, G, pol, acc_a, acc_b);
+  else
+    strided_dot_pair<kPairMaxPerLane, V>(ci, val, xg, ba + sub, ea, bb + sub, eb, G, pol, acc_a, acc_b);
+  for (int off = G >> 1; off > 0; off >>= 1) {
+    acc_a += __shfl_xor_sync(kFull, acc_a, off);
+    acc_b += __shfl_xor_sync(kFull, acc_b, off);
+  }
+  va = __shfl_sync(kFull, acc_a, (lane % (32 / G)) * G);
+  vb = __shfl_sync(kFull, acc_b, (lane % (32 / G)) * G);
+}
+
 // Dot products of the rows [row0, row0 + nrows) (nrows <= 32) of a CSR matrix with xg.
 // G lanes per row, 32/G rows per pass; lane L returns the value of row L (garbage for
 // L >= nrows).  Summation: each lane accumulates its strided entries in order, then a
 // fixed xor butterfly over the G lanes (deterministic).
 template <class V, bool kCached = false>
-__device__ __forceinline__ V tile_spmv(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                       const V* __restrict__ val, const V* __restrict__ xg, int row0,
-                                       int nrows, int G, int per_lane, int lane, const LoadPolicy& pol) {
+__device__ __forceinline__ V tile_spmv_b(const int32_t* __restrict__ ci, const V* __restrict__ val,
+                                         const V* __restrict__ xg, int my_b, int my_e, int nrows, int G,
+                                         int per_lane, int lane, const LoadPolicy& pol) {
   const int rpp = 32 / G;  // rows per pass
   const int passes = (nrows + rpp - 1) / rpp;
   const int g = lane / G, sub = lane - g * G;
-  // lane L's own row bounds, fetched once (coalesced), then passed around by shuffles
-  int my_b = 0, my_e = 0;
-  if (lane < nrows) {
-    my_b = rp[row0 + lane];
-    my_e = rp[row0 + lane + 1];
-  }
   V mine = V(0);
   for (int p = 0; p < passes; ++p) {
     const int q = p * rpp + g;  // row of this lane's group in this pass
@@ -242,6 +330,19 @@ __device__ __forceinline__ V tile_spmv(const int32_t* __restrict__ rp, const int
     if (lane / rpp == p) mine = v;
   }
   return mine;
+}
+
+// tile_spmv_b with lane L's row bounds (row L of the tile, L < nrows) fetched here, coalesced.
+template <class V, bool kCached = false>
+__device__ __forceinline__ V tile_spmv(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                       const V* __restrict__ val, const V* __restrict__ xg, int row0,
+                                       int nrows, int G, int per_lane, int lane, const LoadPolicy& pol) {
+  int my_b = 0, my_e = 0;
+  if (lane < nrows) {
+    my_b = rp[row0 + lane];
+    my_e = rp[row0 + lane + 1];
+  }
+  return tile_spmv_b<V, kCached>(ci, val, xg, my_b, my_e, nrows, G, per_lane, lane, pol);
 }
 
 // Visits every row of a binned CSR matrix once with its dot product against xg and calls
@@ -283,14 +384,48 @@ __device__ __forceinline__ void for_each_row_pf(const BinTable& bins, const int3
       }
       continue;
     }
-    const Bin B = bins.bin[find_bin(bins, task - bins.nchunks)];
-    const int row0 = B.row0 + (task - bins.nchunks - B.task0) * B.rows_per_tile;
-    const int nrows = min(B.rows_per_tile, B.row1 - row0);
-    const int lc = B.per_lane;
-    In in{};
-    if (lane < nrows) in = pre(row0 + lane);
-    const V v = tile_spmv(rp, ci, val, xg, row0, nrows, B.lanes, lc, lane, pol);
-    if (lane < nrows) epi(row0 + lane, v, in, s);
+    if constexpr (sizeof(V) != sizeof(float)) {
+      // FP64 (bound by the FP64 pipe, not by loads in flight): one tile at a time
+      const TileTask a = tile_task(bins, rp, task, lane);
+      In in{};
+      if (lane < a.nrows) in = pre(a.row0 + lane);
+      const V v = tile_spmv_b(ci, val, xg, a.b, a.e, a.nrows, a.lanes, a.per_lane, lane, pol);
+      if (lane < a.nrows) epi(a.row0 + lane, v, in, s);
+      continue;
+    }
+    // FP32 (bound by loads in flight): tiles two at a time (tasks t and t + nwarps, the same
+    // tasks in the same order as one at a time); two short single-pass tiles of one shape run
+    // their SpMVs side by side.
+    const int task2 = task + nwarps;
+    const TileTask a = tile_task(bins, rp, task, lane);
+    const bool two = task2 < total;
+    TileTask b{};
+    if (two) b = tile_task(bins, rp, task2, lane);
+    const bool pair = two && a.lanes == b.lanes && a.nrows * a.lanes <= 32 && b.nrows * b.lanes <= 32 &&
+                      a.per_lane <= kPairMaxPerLane && b.per_lane <= kPairMaxPerLane;
+    if (pair) {
+      In ia{}, ib{};
+      if (lane < a.nrows) ia = pre(a.row0 + lane);
+      if (lane < b.nrows) ib = pre(b.row0 + lane);
+      V va, vb;
+      tile_spmv_pair(ci, val, xg, a, b, lane, pol, va, vb);
+      if (lane < a.nrows) epi(a.row0 + lane, va, ia, s);
+      if (lane < b.nrows) epi(b.row0 + lane, vb, ib, s);
+    } else {
+      {
+        In in{};
+        if (lane < a.nrows) in = pre(a.row0 + lane);
+        const V v = tile_spmv_b(ci, val, xg, a.b, a.e, a.nrows, a.lanes, a.per_lane, lane, pol);
+        if (lane < a.nrows) epi(a.row0 + lane, v, in, s);
+      }
+      if (two) {
+        In in{};
+        if (lane < b.nrows) in = pre(b.row0 + lane);
+        const V v = tile_spmv_b(ci, val, xg, b.b, b.e, b.nrows, b.lanes, b.per_lane, lane, pol);
+        if (lane < b.nrows) epi(b.row0 + lane, v, in, s);
+      }
+    }
+    task = task2;  // the loop's increment moves on to task2 + nwarps
   }
 }
 
