@@ -340,14 +340,14 @@ def run_ours(args):
     f_hbm = gbs / hbm_peak
     gops = ops / (ms * 1e-3) / 1e9 if ops is not None else None
     f_alu = gops / FP64_NOMINAL_GOPS if ops is not None else 0.0
-    traffic = measured_traffic(dom, wl)
     kname = dom if vb == 8 else dom + "<float>"
+    traffic = measured_traffic(kname, wl)
     if f_alu > f_hbm:
         roof = {"bound": "alu", "achieved": gops, "peak": FP64_NOMINAL_GOPS, "unit": "FP64 Gop/s",
                 "frac": f_alu, "traffic": traffic, "kernel": kname}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm,
-                "traffic": traffic if vb == 8 else None, "kernel": kname}
+                "traffic": traffic, "kernel": kname}
     roof.update({"peak_source": f"HBM {peak_src} copy {hbm_peak} GB/s; FP64 nominal {FP64_NOMINAL_GOPS} Gop/s "
                                 f"(measured issue rate {FP64_MEASURED_GOPS})",
                  "kernels": {k: {"ms_per_launch": per[k], "iters_per_launch": int(kt[2]),
