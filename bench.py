@@ -646,12 +646,14 @@ def diff_launches(K, C, where):
     """Kernel launches of one layer step (set_data of all five vectors, unroll with x and y out,
     vjp with dL/dx, dL/dy and three gradients): set_data 5 gathers + 3 scatters + kd_norms;
     unroll kb_init_ctl + kb_init + one kb_loop per 16 iterations (if any grid instance) + one
-    launch per kind of small instance + kd_sched_table + one kd_fwd_loop per segment + 2
-    scatters; vjp 2 gathers + per segment kd_fwd_loop and kd_bwd_loop + 3 scatters."""
+    launch per kind of small instance + kd_sched_table + per segment the forward kernels
+    (kd_fwd_loop if any grid instance, kd_fwd_cluster if any small one) + 2 scatters; vjp 2
+    gathers + per segment the forward and the adjoint kernels + 3 scatters."""
     nck = -(-K // C)
     kinds = int(np.any(where == 1)) + int(np.any(where == 2))
     grid = -(-K // 16) if np.any(where == 0) else 0
-    return 9 + (2 + grid + kinds + 1 + nck + 2) + (2 + 2 * nck + 3)
+    per = int(np.any(where == 0)) + int(np.any(where != 0))
+    return 9 + (2 + grid + kinds + 1 + nck * per + 2) + (2 + 2 * nck * per + 3)
 
 
 def run_diff(args):
@@ -715,8 +717,12 @@ def run_diff(args):
     # the segment kernels, timed live one launch at a time (CUDA events on the stream)
     sp = torch.cuda.current_stream().cuda_stream
     ms_f, ms_fc, ms_b, per = layer.batch.time_unroll(3, sp)
-    ib = diff_iter_bytes(lps)
-    kms = {"kd_fwd_loop": ms_f, "kd_fwd_loop_codes": ms_fc, "kd_bwd_loop": ms_b}
+    where = layer.batch.schedule()
+    kind = "cluster" if np.all(where != 0) else ("loop" if np.all(where == 0) else "loop+cluster")
+    ib0 = diff_iter_bytes(lps)
+    ib = {f"kd_fwd_{kind}": ib0["kd_fwd_loop"], f"kd_fwd_{kind}_codes": ib0["kd_fwd_loop_codes"],
+          f"kd_bwd_{kind}": ib0["kd_bwd_loop"]}
+    kms = dict(zip(ib, (ms_f, ms_fc, ms_b)))
     nseg = -(-K // C)
     dom = max(kms, key=lambda k: kms[k] * nseg)
     k_gbs = {k: ib[k] * per / (kms[k] * 1e-3) / 1e9 for k in kms}
@@ -763,7 +769,7 @@ def run_diff(args):
             "cpu_baseline": cpu,
             "e2e": {"value": args.e2e_steps / e2e_s, "unit": "forward+backward steps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
-            "gpu_launches": args.steps * diff_launches(K, C, layer.batch.schedule()), "clocks": clocks,
+            "gpu_launches": args.steps * diff_launches(K, C, where), "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     layer.close()

@@ -107,7 +107,7 @@ using namespace pdhg_host;
 
 // Frozen schedule of one instance at one iteration of the differentiable solve (diff.cu).
 struct DiffSched {
-  double tau, sigma, al, be, ep;
+  double tau, sigma, inv_sigma, al, be, ep;
   int rho;
 };
 

@@ -42,6 +42,7 @@ __device__ __forceinline__ Sched sched_from_trace(const double* __restrict__ tra
   Sched s;
   s.tau = e / om;
   s.sigma = e * om;
+  s.inv_sigma = 1.0 / (e * om);
   s.rho = r[2] != 0.0 ? 1 : 0;
   const double kk = r[3];
   const double aw = (kk + 1.0) / (kk + 2.0);
@@ -83,6 +84,8 @@ struct DiffArgs {
   double *lx, *ly, *lx0, *ly0, *lsv, *laty;                 // adjoint state (lsv: adjoint of s = of A xbar)
   const double *sx, *sy;                                     // seeds (at the map's last iteration)
   double *gc, *glv, *guv, *glc, *guc;                        // gradients (scaled, permuted)
+  const BInst* inst;  // per instance: its rows, columns, tasks and whether it is small
+  int32_t skip_local;  // grid kernels: leave the small instances to the cluster kernels
 };
 
 // Forward, column j, iteration t: the x update of iteration t - 1 (deferred to here, where the
@@ -128,7 +131,7 @@ __device__ __forceinline__ void col_upd(const DiffArgs& a, int64_t j, int64_t t)
 __device__ __forceinline__ void row_fwd(const DiffArgs& a, int64_t i, int64_t t, double v, uint8_t* code) {
   const Sched& s = a.sched[(size_t)a.irow[i] * (size_t)a.K + (size_t)t];
   const double yi = a.y[i];
-  const double sv = v - yi / s.sigma;
+  const double sv = fma(-yi, s.inv_sigma, v);  // v - y / sigma, with 1/sigma from the table
   const double lo = a.lc[i], hi = a.uc[i];
   const double h = s.sigma * (clampd(sv, lo, hi) - sv);
   a.yh[i] = h;
@@ -162,7 +165,7 @@ __device__ __forceinline__ void row_bwd(const DiffArgs& a, int64_t i, int64_t t,
   if (cd == 1) a.glc[i] += s.sigma * lyh;
   if (cd == 2) a.guc[i] += s.sigma * lyh;
   a.lsv[i] = ls;
-  a.ly[i] = lyp - ls / s.sigma;
+  a.ly[i] = fma(-ls, s.inv_sigma, lyp);  // lyp - ls / sigma (the adjoint of the same product)
   a.ly0[i] = ly0p;
 }
 
@@ -217,18 +220,24 @@ __global__ void __launch_bounds__(kThreads, 3) kd_fwd_loop(DiffArgs a, int64_t t
     uint8_t* ccy = cy ? cy + (size_t)o * (size_t)a.m : nullptr;
     for (int j = gw; j < a.ntT; j += nw) {
       const int4 td = a.tasksT[j];
+      if (a.skip_local && a.inst[td.w].local) continue;  // warp-uniform
       const double u = tile_spmv(a.rpT, a.ciT, a.valT, a.y, td.x, td.y, dtask_lanes(td), dtask_per_lane(td), lane, pol);
       if (lane < td.y) col_fwd(a, td.x + lane, t, t0, u, ccx);
     }
     grid.sync();
     for (int j = gw; j < a.ntA; j += nw) {
       const int4 td = a.tasksA[j];
+      if (a.skip_local && a.inst[td.w].local) continue;
       const double v = tile_spmv(a.rpA, a.ciA, a.valA, a.xbar, td.x, td.y, dtask_lanes(td), dtask_per_lane(td), lane, pol);
       if (lane < td.y) row_fwd(a, td.x + lane, t, v, ccy);
     }
     grid.sync();
   }
-  if (len > 0) GRID_STRIDE(j, a.n) col_upd(a, j, t0 + len - 1);
+  if (len > 0) {
+    GRID_STRIDE(j, a.n) {
+      if (!a.skip_local || !a.inst[a.icol[j]].local) col_upd(a, j, t0 + len - 1);
+    }
+  }
 }
 
 // Adjoint of iterations t0 + len - 1 down to t0 (codes of iteration t0 + o at cx + o n,
@@ -245,7 +254,9 @@ __global__ void __launch_bounds__(kThreads, 3) kd_bwd_loop(DiffArgs a, int64_t t
   if (len <= 0) return;
   {
     const uint8_t* ccy = cy + (size_t)(len - 1) * (size_t)a.m;
-    GRID_STRIDE(i, a.m) row_bwd(a, i, t0 + len - 1, K, ccy);
+    GRID_STRIDE(i, a.m) {
+      if (!a.skip_local || !a.inst[a.irow[i]].local) row_bwd(a, i, t0 + len - 1, K, ccy);
+    }
   }
   grid.sync();
   for (int32_t o = len - 1; o >= 0; --o) {
@@ -253,6 +264,7 @@ __global__ void __launch_bounds__(kThreads, 3) kd_bwd_loop(DiffArgs a, int64_t t
     const uint8_t* ccx = cx + (size_t)o * (size_t)a.n;
     for (int j = gw; j < a.ntT; j += nw) {
       const int4 td = a.tasksT[j];
+      if (a.skip_local && a.inst[td.w].local) continue;
       const double lb = tile_spmv(a.rpT, a.ciT, a.valT, a.lsv, td.x, td.y, dtask_lanes(td), dtask_per_lane(td), lane, pol);
       if (lane < td.y) col_bwd(a, td.x + lane, t, K, lb, ccx);
     }
@@ -260,6 +272,7 @@ __global__ void __launch_bounds__(kThreads, 3) kd_bwd_loop(DiffArgs a, int64_t t
     const uint8_t* ccy = o > 0 ? cy + (size_t)(o - 1) * (size_t)a.m : nullptr;
     for (int j = gw; j < a.ntA; j += nw) {
       const int4 td = a.tasksA[j];
+      if (a.skip_local && a.inst[td.w].local) continue;
       const double w = tile_spmv(a.rpA, a.ciA, a.valA, a.laty, td.x, td.y, dtask_lanes(td), dtask_per_lane(td), lane, pol);
       if (lane < td.y) {
         const int64_t i = td.x + lane;
@@ -268,6 +281,96 @@ __global__ void __launch_bounds__(kThreads, 3) kd_bwd_loop(DiffArgs a, int64_t t
       }
     }
     grid.sync();
+  }
+}
+
+// The same two segment kernels for the small instances (BInst::local), one instance per cluster
+// of kCtas CTAs at a time: the instance's tasks are spread over the cluster's warps and its two
+// phases per iteration are separated by cluster barriers instead of grid barriers.  The
+// matrix slice is re-read every iteration by the same SMs, so it is loaded through L1.
+template <int kCtas>
+__device__ __forceinline__ void kd_cluster_sync() {
+  if (kCtas > 1) cg::this_cluster().sync();
+  else __syncthreads();
+}
+
+template <int kCtas>
+__global__ void __launch_bounds__(kThreads, 2) kd_fwd_cluster(DiffArgs a, const int32_t* __restrict__ list,
+                                                              int32_t nlist, int64_t t0, int32_t len, uint8_t* cx,
+                                                              uint8_t* cy) {
+  const LoadPolicy pol = make_policy();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rank = (int)(blockIdx.x % kCtas), cid = (int)(blockIdx.x / kCtas), ncl = (int)(gridDim.x / kCtas);
+  const int w0 = rank * kWarps + warp, wstep = kCtas * kWarps;
+  for (int q = cid; q < nlist; q += ncl) {
+    const BInst I = a.inst[list[q]];
+    for (int32_t o = 0; o < len; ++o) {
+      const int64_t t = t0 + o;
+      uint8_t* ccx = cx ? cx + (size_t)o * (size_t)a.n : nullptr;
+      uint8_t* ccy = cy ? cy + (size_t)o * (size_t)a.m : nullptr;
+      for (int j = w0; j < I.ntt; j += wstep) {
+        const int4 td = a.tasksT[I.tt0 + j];
+        const double u = tile_spmv<double, true>(a.rpT, a.ciT, a.valT, a.y, td.x, td.y, dtask_lanes(td),
+                                                 dtask_per_lane(td), lane, pol);
+        if (lane < td.y) col_fwd(a, td.x + lane, t, t0, u, ccx);
+      }
+      kd_cluster_sync<kCtas>();
+      for (int j = w0; j < I.nta; j += wstep) {
+        const int4 td = a.tasksA[I.ta0 + j];
+        const double v = tile_spmv<double, true>(a.rpA, a.ciA, a.valA, a.xbar, td.x, td.y, dtask_lanes(td),
+                                                 dtask_per_lane(td), lane, pol);
+        if (lane < td.y) row_fwd(a, td.x + lane, t, v, ccy);
+      }
+      kd_cluster_sync<kCtas>();
+    }
+    if (len > 0)
+      for (int64_t j = I.col0 + (int64_t)rank * kThreads + threadIdx.x; j < (int64_t)I.col0 + I.n;
+           j += (int64_t)kCtas * kThreads)
+        col_upd(a, j, t0 + len - 1);
+  }
+}
+
+template <int kCtas>
+__global__ void __launch_bounds__(kThreads, 2) kd_bwd_cluster(DiffArgs a, const int32_t* __restrict__ list,
+                                                              int32_t nlist, int64_t t0, int64_t K, int32_t len,
+                                                              const uint8_t* cx, const uint8_t* cy) {
+  const LoadPolicy pol = make_policy();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rank = (int)(blockIdx.x % kCtas), cid = (int)(blockIdx.x / kCtas), ncl = (int)(gridDim.x / kCtas);
+  const int w0 = rank * kWarps + warp, wstep = kCtas * kWarps;
+  if (len <= 0) return;
+  for (int q = cid; q < nlist; q += ncl) {
+    const BInst I = a.inst[list[q]];
+    {
+      const uint8_t* ccy = cy + (size_t)(len - 1) * (size_t)a.m;
+      for (int64_t i = I.row0 + (int64_t)rank * kThreads + threadIdx.x; i < (int64_t)I.row0 + I.m;
+           i += (int64_t)kCtas * kThreads)
+        row_bwd(a, i, t0 + len - 1, K, ccy);
+    }
+    kd_cluster_sync<kCtas>();
+    for (int32_t o = len - 1; o >= 0; --o) {
+      const int64_t t = t0 + o;
+      const uint8_t* ccx = cx + (size_t)o * (size_t)a.n;
+      for (int j = w0; j < I.ntt; j += wstep) {
+        const int4 td = a.tasksT[I.tt0 + j];
+        const double lb = tile_spmv<double, true>(a.rpT, a.ciT, a.valT, a.lsv, td.x, td.y, dtask_lanes(td),
+                                                  dtask_per_lane(td), lane, pol);
+        if (lane < td.y) col_bwd(a, td.x + lane, t, K, lb, ccx);
+      }
+      kd_cluster_sync<kCtas>();
+      const uint8_t* ccy = o > 0 ? cy + (size_t)(o - 1) * (size_t)a.m : nullptr;
+      for (int j = w0; j < I.nta; j += wstep) {
+        const int4 td = a.tasksA[I.ta0 + j];
+        const double w = tile_spmv<double, true>(a.rpA, a.ciA, a.valA, a.laty, td.x, td.y, dtask_lanes(td),
+                                                 dtask_per_lane(td), lane, pol);
+        if (lane < td.y) {
+          const int64_t i = td.x + lane;
+          a.ly[i] += w;
+          if (o > 0) row_bwd(a, i, t - 1, K, ccy);
+        }
+      }
+      kd_cluster_sync<kCtas>();
+    }
   }
 }
 
@@ -390,6 +493,8 @@ DiffArgs diff_args(const lp_batch* h) {
   a.lx = d->lx; a.ly = d->ly; a.lx0 = d->lx0; a.ly0 = d->ly0; a.lsv = d->lv; a.laty = d->laty;
   a.sx = d->sx; a.sy = d->sy;
   a.gc = d->gc; a.glv = d->glv; a.guv = d->guv; a.glc = d->glc; a.guc = d->guc;
+  a.inst = h->d_inst;
+  a.skip_local = h->n_local > 0 ? 1 : 0;
   return a;
 }
 
@@ -401,19 +506,84 @@ lp_status coop_launch(lp_batch* h, const void* fn, void** args, cudaStream_t s) 
   return LP_OK;
 }
 
-// Forward iterations t0 .. t0 + len - 1 (codes stored when cx, cy are given).
+// Cluster launch of a small-instance segment kernel (fn<kCtas>) over the handle's small
+// instances, `clusters` clusters of kCtas CTAs.
+template <int kCtas, class... Args>
+lp_status cluster_launch(void (*fn)(Args...), int clusters, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(clusters * kCtas));
+  cfg.blockDim = dim3((unsigned)kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CK(cudaLaunchKernelEx(&cfg, fn, args...));
+  return LP_OK;
+}
+
+// CTAs per cluster for the small instances: the most (8, 4, 2 or 1) with which every small
+// instance has its own cluster resident at once (an instance's iterations are a chain of
+// barriers, so a second wave of clusters costs a second pass of that chain); 1 when even single
+// CTAs take more than one wave (throughput then decides, and one CTA needs no cluster barrier).
+int diff_cluster_ctas(const lp_batch* h, int* clusters) {
+  int occ = 0, occ_b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kd_fwd_cluster<8>, kThreads, 0) != cudaSuccess) occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, kd_bwd_cluster<8>, kThreads, 0) != cudaSuccess) occ_b = 1;
+  occ = std::max(1, std::min(occ, occ_b));
+  const int64_t slots = (int64_t)occ * h->num_sms;
+  int k = 8;
+  while (k > 1 && (int64_t)h->n_local * k > slots) k >>= 1;
+  *clusters = (int)std::max<int64_t>(1, std::min<int64_t>(h->n_local, slots / k));
+  return k;
+}
+
+// Forward iterations t0 .. t0 + len - 1 (codes stored when cx, cy are given): the grid kernel
+// over the large instances, then the cluster kernel over the small ones.
 lp_status forward_run(lp_batch* h, int64_t t0, int32_t len, uint8_t* cx, uint8_t* cy, cudaStream_t s) {
   DiffArgs a = diff_args(h);
-  void* args[] = {&a, &t0, &len, &cx, &cy};
-  return coop_launch(h, reinterpret_cast<const void*>(kd_fwd_loop), args, s);
+  if (h->n_local < h->count) {
+    void* args[] = {&a, &t0, &len, &cx, &cy};
+    const lp_status st = coop_launch(h, reinterpret_cast<const void*>(kd_fwd_loop), args, s);
+    if (st != LP_OK) return st;
+  }
+  if (h->n_local > 0) {
+    int cl = 1;
+    const int k = diff_cluster_ctas(h, &cl);
+    const int32_t* list = h->local_list;
+    const int32_t nl = h->n_local;
+    if (k == 8) return cluster_launch<8>(kd_fwd_cluster<8>, cl, s, a, list, nl, t0, len, cx, cy);
+    if (k == 4) return cluster_launch<4>(kd_fwd_cluster<4>, cl, s, a, list, nl, t0, len, cx, cy);
+    if (k == 2) return cluster_launch<2>(kd_fwd_cluster<2>, cl, s, a, list, nl, t0, len, cx, cy);
+    return cluster_launch<1>(kd_fwd_cluster<1>, cl, s, a, list, nl, t0, len, cx, cy);
+  }
+  return LP_OK;
 }
 
 // Adjoint of iterations t0 + len - 1 down to t0 of a map of K iterations.
 lp_status backward_run(lp_batch* h, int64_t t0, int64_t K, int32_t len, const uint8_t* cx, const uint8_t* cy,
                        cudaStream_t s) {
   DiffArgs a = diff_args(h);
-  void* args[] = {&a, &t0, &K, &len, &cx, &cy};
-  return coop_launch(h, reinterpret_cast<const void*>(kd_bwd_loop), args, s);
+  if (h->n_local < h->count) {
+    void* args[] = {&a, &t0, &K, &len, &cx, &cy};
+    const lp_status st = coop_launch(h, reinterpret_cast<const void*>(kd_bwd_loop), args, s);
+    if (st != LP_OK) return st;
+  }
+  if (h->n_local > 0) {
+    int cl = 1;
+    const int k = diff_cluster_ctas(h, &cl);
+    const int32_t* list = h->local_list;
+    const int32_t nl = h->n_local;
+    if (k == 8) return cluster_launch<8>(kd_bwd_cluster<8>, cl, s, a, list, nl, t0, K, len, cx, cy);
+    if (k == 4) return cluster_launch<4>(kd_bwd_cluster<4>, cl, s, a, list, nl, t0, K, len, cx, cy);
+    if (k == 2) return cluster_launch<2>(kd_bwd_cluster<2>, cl, s, a, list, nl, t0, K, len, cx, cy);
+    return cluster_launch<1>(kd_bwd_cluster<1>, cl, s, a, list, nl, t0, K, len, cx, cy);
+  }
+  return LP_OK;
 }
 
 // Checkpoint q: (x, y, x0, y0) of the diff state.

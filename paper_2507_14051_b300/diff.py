@@ -19,10 +19,17 @@ from . import BatchSolver
 class UnrolledLPBatch:
     """Holds the batch (its matrices are fixed) and applies the differentiable map to new
     objectives and bounds: ``x, y = layer(c, l_c, u_c, l_v, u_v)`` with CUDA float64 tensors
-    concatenated over the instances in their original order."""
+    concatenated over the instances in their original order.  ``params`` go to the batch
+    (lp_params fields).  Defaults for the layer: instances with at most 65536 nonzeros count as
+    small and run their unrolled iterations (and the traced solve) on clusters of CTAs with
+    cluster barriers, the others on the grid kernels; the tile schedule is lane_target 16,
+    tile_rows 8, the fastest measured for the unrolled kernels."""
 
     def __init__(self, lps, K: int = 2000, checkpoint_every: int = 100, **params):
         params.setdefault("precision", 0)
+        params.setdefault("lane_target", 16)
+        params.setdefault("tile_rows", 8)
+        params.setdefault("batch_local_nnz", 1 << 16)
         self.batch = BatchSolver(lps, **params)
         self.K, self.C = int(K), int(checkpoint_every)
         self.sum_n = int(sum(lp.n for lp in lps))

@@ -22,6 +22,8 @@ def test_diff_launch_count():
     assert bench.diff_launches(K, C, grid) == 9 + (2 + 125 + 0 + 1 + 20 + 2) + (2 + 40 + 3)
     small = np.array([1, 2], np.int32)
     assert bench.diff_launches(K, C, small) == 9 + (2 + 0 + 2 + 1 + 20 + 2) + (2 + 40 + 3)
+    mixed = np.array([0, 1], np.int32)  # both segment kernels per segment and direction
+    assert bench.diff_launches(K, C, mixed) == 9 + (2 + 125 + 1 + 1 + 40 + 2) + (2 + 80 + 3)
 
 
 def test_kernel_work_fp32_moves_fewer_bytes_and_no_fp64_ops():

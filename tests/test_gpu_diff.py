@@ -112,7 +112,9 @@ def test_forward_matches_the_oracle_unrolled_map(cuda_device, K):
 SCHEDULES = [(40, {}), (160, dict(pid_enabled=0)), (160, dict(pid_enabled=0, restart_enabled=0))]
 
 
-@pytest.mark.parametrize("local", [0, 10 ** 9])
+# small-instance threshold: 0 = every instance on the grid kernels, 280 = two of the four on the
+# cluster kernels (297 and 465 nonzeros stay on the grid), 10**9 = all on the cluster kernels
+@pytest.mark.parametrize("local", [0, 280, 10 ** 9])
 @pytest.mark.parametrize("K,params", SCHEDULES)
 def test_gradients_match_oracle_finite_differences(cuda_device, K, params, local):
     lps = instances()
