@@ -98,9 +98,22 @@ def kernel_work(lp, vb=8):
             "k2_cols": ((4 + vb) * nnz + 4 * (n + 1) + vb * m + 7 * vb * n, nnz + 12 * n if f64 else None)}
 
 
-def source_digest() -> str:
+# The sources each profiled kernel is built and launched from: a measured DRAM figure stays valid
+# while these are unchanged.
+_CSRC = os.path.join("paper_2507_14051_b300", "csrc")
+TRAFFIC_SOURCES = {
+    "k_loop": tuple(os.path.join(_CSRC, f) for f in ("iterate.cu", "device.cuh", "step.cuh", "kernels.cuh",
+                                                     "solver.cu", "host_util.h")),
+    "kb_loop": tuple(os.path.join(_CSRC, f) for f in ("batch.cu", "batch.cuh", "device.cuh", "step.cuh",
+                                                      "kernels.cuh", "host_util.h")),
+}
+
+
+def source_digest(kernel: str | None = None) -> str:
+    """sha256 prefix of the kernel's sources (TRAFFIC_SOURCES; every CUDA source if None)."""
+    files = KERNEL_SOURCES if kernel is None else TRAFFIC_SOURCES[kernel.split("<")[0]]
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in files:
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -115,7 +128,7 @@ def measured_traffic(kernel: str, workload: str):
             data = json.load(f)
     except (OSError, ValueError):
         return None
-    if data.get("source_digest") != source_digest():
+    if data.get("source_digests", {}).get(kernel.split("<")[0]) != source_digest(kernel):
         return None
     ent = data.get(kernel, {}).get(workload)
     return None if ent is None else ent.get("dram_bytes_per_launch")
@@ -560,7 +573,7 @@ def run_batch(args):
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             tj = json.load(f)
-        if tj.get("source_digest") == source_digest():
+        if tj.get("source_digests", {}).get("kb_loop") == source_digest("kb_loop"):
             per_nnz_it = tj["kb_loop"]["batch"]["dram_bytes_per_grid_nnz_iteration"]
             traffic = per_nnz_it * sum(lp.nnz for lp in lps if lp.nnz > local_nnz) * 16
     except (OSError, ValueError, KeyError):
