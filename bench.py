@@ -109,6 +109,19 @@ TRAFFIC_SOURCES = {
 }
 
 
+def design_bytes(lp, vb=8):
+    """Bytes the iteration kernels are designed to move per iteration (vb-byte values, 32-bit
+    indices), beyond the algorithmic bytes: the maintained A x and A^T y and their anchors.  Row
+    side: A's values and indices, row offsets, the gathered xhat, and per row y0, yhat, y, A xhat,
+    A x, A x0, l_c, u_c read and y, A x, yhat, A xhat written (12 vectors); column side likewise
+    with per column xhat, x0, x, A^T y, A^T y0, c, l_v, u_v read and x, A^T y, the next xhat
+    written (11 vectors)."""
+    m, n, z = lp.m, lp.n, lp.nnz
+    rows = (4 + vb) * z + 4 * (m + 1) + vb * n + 12 * vb * m
+    cols = (4 + vb) * z + 4 * (n + 1) + vb * m + 11 * vb * n
+    return rows + cols
+
+
 def source_digest(kernel: str | None = None) -> str:
     """sha256 prefix of the kernel's sources (TRAFFIC_SOURCES; every CUDA source if None)."""
     files = KERNEL_SOURCES if kernel is None else TRAFFIC_SOURCES[kernel.split("<")[0]]
@@ -370,7 +383,8 @@ def run_ours(args):
                                  "frac_fp64": (work[k][1] / (per[k] * 1e-3) / 1e9 / FP64_NOMINAL_GOPS
                                                if work[k][1] is not None else None)}
                              for k in per},
-                 "timing": f"mean of {int(kt[3])} launches, CUDA events on the solve stream"})
+                 "timing": f"mean of {int(kt[3])} launches, CUDA events on the solve stream",
+                 "design_bytes_per_launch": design_bytes(lp, vb) * int(kt[2]) if kt[1] == 0.0 else None})
 
     # end to end through the C ABI with host buffers: create (H2D inside) + solve + get (D2H)
     arrs = [np.ascontiguousarray(lp.row_ptr, np.int64), np.ascontiguousarray(lp.col_idx, np.int32),
