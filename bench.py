@@ -82,7 +82,7 @@ def workload_name(name: str, lp) -> str:
     return f"{base}, m={lp.m}, n={lp.n}, nnz={lp.nnz}, FP64"
 
 
-def kernel_work(lp, vb=8):
+def kernel_work(lp, vb=8, loop=True):
     """Algorithmic bytes and FP64 operations of one launch of each iteration kernel, for values
     of vb bytes (8: FP64 kernels; 4: the FP32 kernels of precision 1 and 2) and 32-bit indices.
     Bytes (what the method must move):
@@ -91,11 +91,14 @@ def kernel_work(lp, vb=8):
       column kernel: (4 + vb) nnz + 4 (n+1) + vb m gathered yhat + 7 vb n (x, x0, c, l_v, u_v
                      read; x, xhat written)
     FP64 operations (fma/add/mul issued by the FP64 kernels' arithmetic): one fma per nonzero
-    plus 17 per row (row kernel) or 12 per column (column kernel); None for the FP32 kernels."""
+    plus 17 per row (row kernel) or 12 per column (column kernel); 15 and 10 in the loop kernel
+    (loop=True), whose phases leave the PID norms to a pass at restarts; None for the FP32
+    kernels."""
     m, n, nnz = lp.m, lp.n, lp.nnz
     f64 = vb == 8
-    return {"k1_rows": ((4 + vb) * nnz + 4 * (m + 1) + vb * n + 7 * vb * m, nnz + 17 * m if f64 else None),
-            "k2_cols": ((4 + vb) * nnz + 4 * (n + 1) + vb * m + 7 * vb * n, nnz + 12 * n if f64 else None)}
+    er, ec = (15, 10) if loop else (17, 12)
+    return {"k1_rows": ((4 + vb) * nnz + 4 * (m + 1) + vb * n + 7 * vb * m, nnz + er * m if f64 else None),
+            "k2_cols": ((4 + vb) * nnz + 4 * (n + 1) + vb * m + 7 * vb * n, nnz + ec * n if f64 else None)}
 
 
 # The sources each profiled kernel is built and launched from: a measured DRAM figure stays valid
@@ -349,7 +352,7 @@ def run_ours(args):
     # (the kernels of the solve's first stage: FP32 for precision 1 and 2)
     kt = lpx.lp_time_kernels(solver.h, args.kernel_iters, sp)
     vb = 8 if args.precision == 0 else 4
-    work = kernel_work(lp, vb)
+    work = kernel_work(lp, vb, loop=kt[1] == 0.0)
     hbm_peak, peak_src = load_peaks()
     if kt[1] == 0.0:  # the cooperative loop kernel runs kt[2] iterations per launch
         per_iter = int(kt[2])

@@ -108,15 +108,20 @@ __device__ __forceinline__ void store_block_partials(double (&s)[kNumSums], int 
 // and (if use_cond) sets the device-side loop condition of the enclosing graph.  FP64: 3
 // blocks per SM (80 registers); FP32: 4 (64 registers, no spills), more loads in flight for
 // the memory-bound FP32 phases.
+// The phases do not accumulate the PID's norms |yhat - y0|^2 and |xhat - x0|^2 (two FP64
+// operations per row and per column on the FP64-bound path): at a restart, which the control
+// decides once every many iterations, one extra pass over the four vectors sums them
+// (partials in part_pid) before the PID update.
 template <class V>
 __global__ void __launch_bounds__(kThreads, sizeof(V) == sizeof(float) ? 4 : 3)
-    k_loop(RowArgsT<V> ra, ColArgsT<V> ca, double* part_rows, double* part_cols, int32_t iters,
+    k_loop(RowArgsT<V> ra, ColArgsT<V> ca, double* part_rows, double* part_cols, double* part_pid, int32_t iters,
            cudaGraphConditionalHandle cond, int32_t use_cond) {
   cg::grid_group grid = cg::this_grid();
   __shared__ Ctl sc;
   __shared__ RowStep rst;
   __shared__ ColStepT<V> cst;
   __shared__ Halpern hw;
+  __shared__ int rs;
   if (threadIdx.x == 0) sc = *ra.ctl;
   __syncthreads();
   const LoadPolicy pol = make_policy();
@@ -133,8 +138,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(V) == sizeof(float) ? 4 : 3)
                       row_prefetch(ra, st, i);
                       return NoOperands{};
                     },
-                    [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) { row_epilogue(ra, st, i, v, acc); });
-    const int nr = st.check ? 5 : 3;
+                    [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) {
+                      row_epilogue<V, false>(ra, st, i, v, acc);
+                    });
+    const int nr = st.check ? 5 : 2;
     store_block_partials(s, nr, part_rows);
     grid.sync();
     // the last warp is idle while warps 0..nr-1 add the totals: it computes the next Halpern
@@ -142,8 +149,28 @@ __global__ void __launch_bounds__(kThreads, sizeof(V) == sizeof(float) ? 4 : 3)
     if (threadIdx.x == kThreads - 32) hw = halpern_weights(sc.k, sc.gamma);
     double tot[kNumSums];
     block_totals(part_rows, gridDim.x, nr, &ra.bins, tot);
-    if (threadIdx.x == 0) row_control(sc, tot, st.check, trace, &hw);
+    if (threadIdx.x == 0) rs = row_decide(sc, tot, st.check, trace, &hw);
     __syncthreads();
+    if (rs == 1) {  // the same decision in every block
+      double q[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      if (sc.pid_enabled) {
+        const V* __restrict__ xc = (sc.t & 1) ? ca.xh1 : ca.xh0;  // xhat of this iteration
+        const int stride = gridDim.x * kThreads;
+        for (int j = blockIdx.x * kThreads + threadIdx.x; j < ca.n; j += stride) {
+          const V d = xc[j] - ca.x0[j];
+          acc_fma(q[0], d, d);
+        }
+        for (int i = blockIdx.x * kThreads + threadIdx.x; i < ra.m; i += stride) {
+          const V d = ra.yh[i] - ra.y0[i];
+          acc_fma(q[1], d, d);
+        }
+        store_block_partials(q, 2, part_pid);
+        grid.sync();
+        block_totals(part_pid, gridDim.x, 2, nullptr, q);
+      }
+      if (threadIdx.x == 0) row_restart_weight(sc, q[0], q[1]);
+      __syncthreads();
+    }
     if (sc.done) break;
     // ---- column phase
     if (threadIdx.x == 0) cst = col_step(sc, ca);
@@ -155,8 +182,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(V) == sizeof(float) ? 4 : 3)
                       col_prefetch(ca, cs, j);
                       return NoOperands{};
                     },
-                    [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) { col_epilogue(ca, cs, j, u, acc); });
-    const int nc = cs.check ? 5 : 2;
+                    [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) {
+                      col_epilogue<V, false>(ca, cs, j, u, acc);
+                    });
+    const int nc = cs.check ? 5 : 1;
     store_block_partials(s2, nc, part_cols);
     grid.sync();
     double tot2[kNumSums];

@@ -23,6 +23,7 @@ struct RowArgsT {
   double* partials;
   double* trace;
   BinTable bins;
+  int32_t m;  // rows
 };
 
 template <class V>
@@ -38,6 +39,7 @@ struct ColArgsT {
   Ctl* ctl;
   double* partials;
   BinTable bins;
+  int32_t n;  // columns
 };
 
 using RowArgs = RowArgsT<double>;
@@ -57,7 +59,7 @@ template <class V>
 struct IterKernels {
   void (*rows)(RowArgsT<V>);
   void (*cols)(ColArgsT<V>);
-  void (*loop)(RowArgsT<V>, ColArgsT<V>, double*, double*, int32_t, cudaGraphConditionalHandle, int32_t);
+  void (*loop)(RowArgsT<V>, ColArgsT<V>, double*, double*, double*, int32_t, cudaGraphConditionalHandle, int32_t);
   void (*init_cols)(int32_t, const V*, const V*, const V*, V*, V*, V*, V*, V*, Ctl*, double*);
   void (*init_rows)(int32_t, V*, V*, V*, V*, V*, V*);
 };

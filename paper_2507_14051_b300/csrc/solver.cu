@@ -61,6 +61,7 @@ struct lp_solver {
   double* out_buf = nullptr;
   double* partials = nullptr;
   double* partials2 = nullptr;  // column-phase partials of the loop kernel
+  double* partials3 = nullptr;  // the loop kernel's restart-time PID norms
   double* trace = nullptr;
   int64_t trace_cap = 0;
   Ctl* ctl = nullptr;
@@ -145,12 +146,14 @@ void fill_args(const lp_solver* h, RowArgs& ra, ColArgs& ca) {
   ra.lc = h->lc; ra.uc = h->uc; ra.inv_dr = h->inv_dr;
   ra.ctl = h->ctl; ra.partials = h->partials; ra.trace = h->trace_cap > 0 ? h->trace : nullptr;
   ra.bins = h->binsA;
+  ra.m = h->m;
   ca = ColArgs{};
   ca.rp = h->rpT; ca.ci = h->ciT; ca.val = h->valT; ca.yh = h->yh;
   ca.xh0 = h->xh0; ca.xh1 = h->xh1;
   ca.x = h->x; ca.x0 = h->x0; ca.aty = h->aty; ca.aty0 = h->aty0;
   ca.c = h->c; ca.lv = h->lv; ca.uv = h->uv; ca.inv_dc = h->inv_dc;
   ca.ctl = h->ctl; ca.partials = h->partials; ca.bins = h->binsT;
+  ca.n = h->n;
 }
 
 void fill_args(const lp_solver* h, RowArgsT<float>& ra, ColArgsT<float>& ca) {
@@ -163,6 +166,7 @@ void fill_args(const lp_solver* h, RowArgsT<float>& ra, ColArgsT<float>& ca) {
   ra.yb0 = f.yb0; ra.yb1 = f.yb1;
   ra.ctl = h->ctl; ra.partials = h->partials; ra.trace = h->trace_cap > 0 ? h->trace : nullptr;
   ra.bins = h->binsA;
+  ra.m = h->m;
   ca = ColArgsT<float>{};
   ca.rp = h->rpT; ca.ci = h->ciT; ca.val = f.valT; ca.yh = f.yh;
   ca.xh0 = f.xh0; ca.xh1 = f.xh1;
@@ -170,6 +174,7 @@ void fill_args(const lp_solver* h, RowArgsT<float>& ra, ColArgsT<float>& ca) {
   ca.c = f.c; ca.lv = f.lv; ca.uv = f.uv; ca.inv_dc = f.inv_dc;
   ca.xb0 = f.xb0; ca.xb1 = f.xb1;
   ca.ctl = h->ctl; ca.partials = h->partials; ca.bins = h->binsT;
+  ca.n = h->n;
 }
 
 template <class V>
@@ -185,7 +190,8 @@ cudaError_t launch_loop(const lp_solver* h, const RowArgsT<V>& ra, const ColArgs
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, iter_kernels<V>().loop, ra, ca, h->partials, h->partials2, iters, cond, use_cond);
+  return cudaLaunchKernelEx(&cfg, iter_kernels<V>().loop, ra, ca, h->partials, h->partials2, h->partials3, iters,
+                            cond, use_cond);
 }
 
 // Captures the solve loop of one precision: a graph whose conditional while node runs the body
@@ -418,6 +424,7 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   }
   CK(h->alloc(&h->partials, (size_t)h->max_grid * kNumSums));
   CK(h->alloc(&h->partials2, (size_t)h->max_grid * kNumSums));
+  CK(h->alloc(&h->partials3, (size_t)h->max_grid * kNumSums));
   CK(h->alloc(&h->ctl, 1));
   CK(h->alloc(&h->pw, 1));
   CK(cudaMemset(h->ctl, 0, sizeof(Ctl)));

@@ -99,7 +99,9 @@ __device__ __forceinline__ RowIn<V> row_load(const RowArgsT<V>& a, const RowStep
   return in;
 }
 
-template <class V>
+// kPidSums: also accumulate |yhat - y0|^2 (slot 2), which only the PID update at a restart
+// reads; a driver that evaluates it only when a restart happens passes false (slot 2 stays 0).
+template <class V, bool kPidSums = true>
 __device__ __forceinline__ void row_finish(const RowArgsT<V>& a, const RowStep& st, int i, V v,
                                            const RowIn<V>& in, double (&acc)[kNumSums]) {
   const V ha = (V)st.ha, hb = (V)st.hb, he = (V)st.he;
@@ -127,8 +129,10 @@ __device__ __forceinline__ void row_finish(const RowArgsT<V>& a, const RowStep& 
   const V dy = yi - yn;
   acc_fma(acc[0], dy, dy);
   acc_fma(acc[1], dy, axi - v);
-  const V d0 = yn - y0i;
-  acc_fma(acc[2], d0, d0);
+  if (kPidSums) {
+    const V d0 = yn - y0i;
+    acc_fma(acc[2], d0, d0);
+  }
   if (st.check) {
     const V pr = (v - clampd(v, lo, hi)) * a.inv_dr[i];
     acc_fma(acc[3], pr, pr);
@@ -143,10 +147,10 @@ __device__ __forceinline__ void row_finish(const RowArgsT<V>& a, const RowStep& 
   a.axh[i] = v;
 }
 
-template <class V>
+template <class V, bool kPidSums = true>
 __device__ __forceinline__ void row_epilogue(const RowArgsT<V>& a, const RowStep& st, int i, V v,
                                              double (&acc)[kNumSums]) {
-  row_finish(a, st, i, v, row_load(a, st, i), acc);
+  row_finish<V, kPidSums>(a, st, i, v, row_load(a, st, i), acc);
 }
 
 // Issued before the row's SpMV: brings the row epilogue's operands to L1 while the SpMV runs,
@@ -185,10 +189,13 @@ __device__ __forceinline__ Halpern halpern_weights(int64_t k, double gamma) {
 // Scalar control after the row phase of iteration c.t, on totals tot[0..2] (and tot[3..4] on
 // check iterations).  Writes the trace row if `trace` is given.  `next` (or NULL): the weights
 // halpern_weights(c.k, c.gamma), computed beforehand off this serial path.
-__device__ __forceinline__ void row_control(Ctl& c, const double (&tot)[kNumSums], bool check,
-                                            double* trace, const Halpern* next = nullptr) {
+// row_decide does all of it but the new primal weight of a restart, and returns the restart flag
+// (1), 0, or -1 once the solve has ended (NUMERICAL); row_restart_weight then applies the PID
+// update (Section 3) from the squared norms |xhat - x0|^2 and |yhat - y0|^2 of the epoch.
+__device__ __forceinline__ int row_decide(Ctl& c, const double (&tot)[kNumSums], bool check, double* trace,
+                                          const Halpern* next = nullptr) {
   const int64_t t = c.t;
-  const double eta = c.eta, om = c.omega;
+  const double om = c.omega;
   const double r2 = fma(c.w_over_eta, c.sxx, fma(c.inv_eta_w, tot[0], 2.0 * tot[1]));
   const double r = sqrt(r2 > 0.0 ? r2 : 0.0);
   const int64_t k = c.k;
@@ -210,18 +217,10 @@ __device__ __forceinline__ void row_control(Ctl& c, const double (&tot)[kNumSums
     c.status = kNumerical;
     c.iters = t + 1;
     c.done = 1;
-    return;
+    return -1;
   }
   const int rs = c.restart_enabled && (t + 1 < c.max_iter) ? restart_test(c, k, t, r) : 0;
   if (rs) {
-    double omn = om;
-    if (c.pid_enabled) omn = pid_update(c, om, sqrt(c.sx0), sqrt(tot[2]));
-    c.omega = omn;
-    c.tau = eta / omn;
-    c.sigma = eta * omn;
-    c.inv_sigma = 1.0 / (eta * omn);
-    c.w_over_eta = omn / eta;
-    c.inv_eta_w = 1.0 / (eta * omn);
     c.k = 0;
     c.restarts += 1;
     if (tr) trace[4 * t + 2] = 1.0;
@@ -234,6 +233,26 @@ __device__ __forceinline__ void row_control(Ctl& c, const double (&tot)[kNumSums
     c.k = k + 1;
   }
   c.restart = rs;
+  return rs;
+}
+
+__device__ __forceinline__ void row_restart_weight(Ctl& c, double dx2, double dy2) {
+  const double eta = c.eta, om = c.omega;
+  double omn = om;
+  if (c.pid_enabled) omn = pid_update(c, om, sqrt(dx2), sqrt(dy2));
+  c.omega = omn;
+  c.tau = eta / omn;
+  c.sigma = eta * omn;
+  c.inv_sigma = 1.0 / (eta * omn);
+  c.w_over_eta = omn / eta;
+  c.inv_eta_w = 1.0 / (eta * omn);
+}
+
+// Scalar control after the row phase with the PID norms accumulated in the phase (c.sx0 from the
+// last column phase, tot[2] from this row phase).
+__device__ __forceinline__ void row_control(Ctl& c, const double (&tot)[kNumSums], bool check,
+                                            double* trace, const Halpern* next = nullptr) {
+  if (row_decide(c, tot, check, trace, next) == 1) row_restart_weight(c, c.sx0, tot[2]);
 }
 
 // --------------------------------------------------------------- column phase
@@ -286,7 +305,9 @@ __device__ __forceinline__ ColIn<V> col_load(const ColArgsT<V>& a, const ColStep
   return in;
 }
 
-template <class V>
+// kPidSums: also accumulate |xhat' - x0|^2 (slot 1), which only the PID update at a restart reads
+// (as c.sx0); with false slot 1 stays 0.
+template <class V, bool kPidSums = true>
 __device__ __forceinline__ void col_finish(const ColArgsT<V>& a, const ColStepT<V>& st, int j, V u,
                                            const ColIn<V>& in, double (&acc)[kNumSums]) {
   const V ha = (V)st.ha, hb = (V)st.hb, he = (V)st.he, tau = (V)st.tau;
@@ -307,8 +328,10 @@ __device__ __forceinline__ void col_finish(const ColArgsT<V>& a, const ColStepT<
   const V xn = clampd(fmav(-tau, cj - atyj, xj), lo, hi);
   const V dx = xj - xn;
   acc_fma(acc[0], dx, dx);
-  const V d0 = xn - x0j;
-  acc_fma(acc[1], d0, d0);
+  if (kPidSums) {
+    const V d0 = xn - x0j;
+    acc_fma(acc[1], d0, d0);
+  }
   if (st.check) {
     acc_fma(acc[2], cj, xc);
     const V rc = cj - u;
@@ -324,10 +347,10 @@ __device__ __forceinline__ void col_finish(const ColArgsT<V>& a, const ColStepT<
   st.xn[j] = xn;
 }
 
-template <class V>
+template <class V, bool kPidSums = true>
 __device__ __forceinline__ void col_epilogue(const ColArgsT<V>& a, const ColStepT<V>& st, int j, V u,
                                              double (&acc)[kNumSums]) {
-  col_finish(a, st, j, u, col_load(a, st, j), acc);
+  col_finish<V, kPidSums>(a, st, j, u, col_load(a, st, j), acc);
 }
 
 template <class V>

@@ -33,3 +33,4 @@ def test_kernel_work_fp32_moves_fewer_bytes_and_no_fp64_ops():
     for k in ("k1_rows", "k2_cols"):
         assert b32[k][0] < b64[k][0] and b32[k][1] is None and b64[k][1] > 0
     assert b64["k1_rows"][0] == 12 * 50 + 4 * 11 + 8 * 20 + 56 * 10
+    assert b64["k1_rows"][1] == 50 + 15 * 10 and bench.kernel_work(LP(), 8, loop=False)["k1_rows"][1] == 50 + 17 * 10
