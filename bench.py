@@ -135,9 +135,10 @@ def source_digest(kernel: str | None = None) -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
-    kernel sources (digest) and on this workload; None otherwise."""
+def measured_traffic(kernel: str, workload: str, iters_per_launch: int):
+    """DRAM bytes of one launch of `iters_per_launch` iterations, from the committed ncu summary
+    (bytes per iteration of the captured launch), if it was taken on the current kernel sources
+    (digest) and on this workload; None otherwise."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -147,7 +148,9 @@ def measured_traffic(kernel: str, workload: str):
     if data.get("source_digests", {}).get(kernel.split("<")[0]) != source_digest(kernel):
         return None
     ent = data.get(kernel, {}).get(workload)
-    return None if ent is None else ent.get("dram_bytes_per_launch")
+    if ent is None:
+        return None
+    return ent["dram_bytes_per_launch"] / ent["iters_per_launch"] * iters_per_launch
 
 
 def load_peaks():
@@ -370,7 +373,7 @@ def run_ours(args):
     gops = ops / (ms * 1e-3) / 1e9 if ops is not None else None
     f_alu = gops / FP64_NOMINAL_GOPS if ops is not None else 0.0
     kname = dom if vb == 8 else dom + "<float>"
-    traffic = measured_traffic(kname, wl)
+    traffic = measured_traffic(kname, wl, int(kt[2]))
     if f_alu > f_hbm:
         roof = {"bound": "alu", "achieved": gops, "peak": FP64_NOMINAL_GOPS, "unit": "FP64 Gop/s",
                 "frac": f_alu, "traffic": traffic, "kernel": kname}

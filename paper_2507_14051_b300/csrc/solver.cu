@@ -557,7 +557,7 @@ lp_status lp_default_params(lp_params* p) {
   p->pc_enabled = 1;
   p->pc_alpha = 1.0;
   p->trace_cap = 0;
-  p->unroll = 8;
+  p->unroll = 32;
   p->lane_target = 8;
   p->persistent = -1;
   p->precision = 0;

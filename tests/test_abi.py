@@ -63,7 +63,7 @@ def test_default_params_match_documentation_and_oracle():
     p = lpx.lp_default_params()
     assert (p.gamma, p.beta_sufficient, p.beta_necessary, p.beta_artificial) == (1.0, 0.2, 0.8, 0.36)
     assert p.eta == 0.0 and p.omega0 == 1.0 and p.check_every == 64
-    assert p.unroll == 8 and p.lane_target == 8 and p.trace_cap == 0 and p.persistent == -1
+    assert p.unroll == 32 and p.lane_target == 8 and p.trace_cap == 0 and p.persistent == -1
     for k, v in oracle.DEFAULTS.items():
         assert getattr(p, k) == v, k
 
