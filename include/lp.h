@@ -84,7 +84,9 @@ typedef struct {
   double pc_alpha;
   int64_t trace_cap;       /* > 0: record (r_t, omega_t, restart_t, k_t) for t < trace_cap */
   int32_t unroll;          /* iterations per body of the device-side loop (1..64) */
-  int32_t lane_target;     /* SpMV schedule: at most this many nonzeros per lane and task (1..64) */
+  int32_t lane_target;     /* SpMV schedule: at most this many nonzeros per lane and task (1..64);
+                              0: automatic (8 for lp_solve; 32 for the batch, whose long rows
+                              then take fewer FP64 butterfly additions per row) */
   int32_t persistent;      /* 1: one cooperative kernel runs `unroll` iterations per launch with
                               grid-wide barriers between phases; 0: one kernel per phase;
                               -1: the first when every block of both phases fits on the GPU at
@@ -109,7 +111,7 @@ typedef struct {
   int32_t tile_rows;       /* rows per warp tile (1..32, rounded down to a power of two): a tile
                               of R rows, each read by G lanes (G from lane_target), takes R G / 32
                               passes and runs its R row epilogues in R lanes at once; 0: automatic
-                              (1 for lp_solve, whose latency-bound sizes want short tasks; 32 for
+                              (1 for lp_solve, whose latency-bound sizes want short tasks; 8 for
                               the batch, whose long rows would otherwise spend one warp's FP64
                               issue on each row's epilogue) */
   int64_t batch_local_nnz; /* lp_batch_* only: instances with at most this many nonzeros are
@@ -121,7 +123,7 @@ typedef struct {
 /* Fills p with the defaults: gamma 1, betas 0.2 / 0.8 / 0.36, K_P 0.5, K_I 0.001, K_D 0,
  * eta 0 (power iteration), omega0 1, check_every 64, restarts and PID on, power_tol 1e-7,
  * power_max_iter 10000, seed 0, Ruiz 10 + Pock-Chambolle alpha 1, no trace, unroll 32,
- * lane_target 8, persistent -1, precision 0, switch_tol 1e-5, fp32_patience 32, rescale 0,
+ * lane_target 0 (automatic), persistent -1, precision 0, switch_tol 1e-5, fp32_patience 32, rescale 0,
  * tile_rows 0, batch_local_nnz 16384.  Returns LP_ERR_INVALID_ARG if p is NULL. */
 LP_API lp_status lp_default_params(lp_params* p);
 

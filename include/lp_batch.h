@@ -33,7 +33,8 @@ typedef struct lp_batch* lp_batch_handle;
  *   eta   NULL: instance k uses p->eta if > 0, else 0.998 / ||A~_k||_2 from a power iteration
  *         on its own preconditioned matrix (Section 3, "Stepsize"); or double[count], each > 0,
  *         the step size of each instance.
- *   tiles NULL: p->lane_target and p->tile_rows for every instance; or int32[2 * count], the
+ *   tiles NULL: p->lane_target and p->tile_rows for every instance (0, the default: lane_target
+ *         32 and tile_rows 8); or int32[2 * count], the
  *         tile schedule of each instance as (lane_target in [1, 64], tile_rows in [1, 32]),
  *         e.g. from lp_tune_schedule.
  *   p     shared parameters (NULL: lp_default_params).  precision 0, 1 and 2 as for lp_solve;

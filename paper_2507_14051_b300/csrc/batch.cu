@@ -906,7 +906,7 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
     for (int32_t i = 0; i < mk; ++i) rpl[i + 1] = rpl[i] + (int32_t)rlen[b.row_perm[i]];
     cpl[0] = 0;
     for (int32_t j = 0; j < nk; ++j) cpl[j + 1] = cpl[j] + (int32_t)clen[b.col_perm[j]];
-    const int lt = tiles ? tiles[2 * k] : h->prm.lane_target;
+    const int lt = tiles ? tiles[2 * k] : (h->prm.lane_target > 0 ? h->prm.lane_target : kBatchLaneTarget);
     const int tr = tiles ? tiles[2 * k + 1] : (h->prm.tile_rows > 0 ? h->prm.tile_rows : kBatchTileRows);
     make_tasks(rpl, lt, tr, h->inst[k].row0, k, b.tA);
     make_tasks(cpl, lt, tr, h->inst[k].col0, k, b.tT);

@@ -13,7 +13,10 @@
 namespace pdhg {
 
 constexpr int kBatchUnroll = 16;  // iterations per launch of the batch loop kernel
-constexpr int kBatchTileRows = 32;  // rows per tile of the batch when lp_params.tile_rows is 0
+// The batch's tile schedule when lp_params.lane_target / tile_rows are 0 (measured on 512 uneven
+// LPs: 4.74 ms per FP64 iteration of the grid loop, against 5.08 ms with (8, 32)).
+constexpr int kBatchLaneTarget = 32;
+constexpr int kBatchTileRows = 8;
 constexpr int kLocalCtas = 8;       // CTAs (SMs) of the cluster that runs one small instance
 constexpr int kMaxInst = LP_BATCH_MAX_INSTANCES;
 

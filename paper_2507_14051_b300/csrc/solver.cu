@@ -377,8 +377,9 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
       valT[pos] = valA[q];
     }
   std::vector<int4> chunksA, chunksT;
-  h->binsA = make_bins(rpA, h->prm.lane_target, h->prm.tile_rows > 0 ? h->prm.tile_rows : 1, chunksA);
-  h->binsT = make_bins(rpT, h->prm.lane_target, h->prm.tile_rows > 0 ? h->prm.tile_rows : 1, chunksT);
+  const int lt = h->prm.lane_target > 0 ? h->prm.lane_target : 8;  // automatic: 8
+  h->binsA = make_bins(rpA, lt, h->prm.tile_rows > 0 ? h->prm.tile_rows : 1, chunksA);
+  h->binsT = make_bins(rpT, lt, h->prm.tile_rows > 0 ? h->prm.tile_rows : 1, chunksT);
 
   int occA = 0, occT = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, iter_kernels<double>().rows, kThreads, 0));
@@ -558,7 +559,7 @@ lp_status lp_default_params(lp_params* p) {
   p->pc_alpha = 1.0;
   p->trace_cap = 0;
   p->unroll = 32;
-  p->lane_target = 8;
+  p->lane_target = 0;
   p->persistent = -1;
   p->precision = 0;
   p->switch_tol = 1e-5;

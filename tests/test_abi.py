@@ -63,7 +63,7 @@ def test_default_params_match_documentation_and_oracle():
     p = lpx.lp_default_params()
     assert (p.gamma, p.beta_sufficient, p.beta_necessary, p.beta_artificial) == (1.0, 0.2, 0.8, 0.36)
     assert p.eta == 0.0 and p.omega0 == 1.0 and p.check_every == 64
-    assert p.unroll == 32 and p.lane_target == 8 and p.trace_cap == 0 and p.persistent == -1
+    assert p.unroll == 32 and p.lane_target == 0 and p.trace_cap == 0 and p.persistent == -1
     for k, v in oracle.DEFAULTS.items():
         assert getattr(p, k) == v, k
 
@@ -118,7 +118,7 @@ def test_create_rejects_invalid_arguments():
     assert L.lp_create(lp.m, lp.n, lp.nnz, None, *ptrs[1:], 0, None, C.byref(h)) == lpx.LP_ERR_INVALID_ARG
     assert L.lp_create(lp.m, lp.n, 1 << 31, *ptrs, 0, None, C.byref(h)) == lpx.LP_ERR_TOO_LARGE
     for field, value in (("gamma", 1.5), ("check_every", 0), ("unroll", 0), ("omega0", -1.0),
-                         ("lane_target", 0), ("pc_alpha", 3.0), ("persistent", 2)):
+                         ("lane_target", -1), ("lane_target", 65), ("pc_alpha", 3.0), ("persistent", 2)):
         p = lpx.lp_default_params(**{field: value})
         with pytest.raises(lpx.LPError) as e:
             _create(lp, arrs, params=p)
