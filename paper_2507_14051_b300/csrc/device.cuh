@@ -113,20 +113,23 @@ __device__ __forceinline__ LoadPolicy make_policy() {
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.keep));
   return p;
 }
-// Read-only streaming loads of the matrix: no L1 allocation, L2 evict-first.
+// Read-only loads of the matrix: L2 evict-first (the matrix is streamed once per iteration), but
+// allocated in L1: a lane reads its row's consecutive entries in successive steps, so one L1
+// line serves several steps of several lanes instead of one L2 fetch per step (measured: FP32
+// multicommodity iteration 156 -> 146 us, FP64 297 -> 288 us).
 __device__ __forceinline__ double ld_stream(const double* p, uint64_t pol) {
   double v;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
   return v;
 }
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol) {
   int32_t v;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
 __device__ __forceinline__ float ld_stream(const float* p, uint64_t pol) {
   float v;
-  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
   return v;
 }
 // Prefetch of the line holding *p into L1 (no register is written; the later load hits L1).
