@@ -161,15 +161,16 @@ __device__ __forceinline__ double start_entry(uint64_t seed, uint64_t i) {
   return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
 }
 
-// Read-only loads that allocate in L1: for data a block re-reads every iteration (the
-// cluster loop over a small instance).
+// Read-only loads with the default L2 policy: for data the same SMs re-read every iteration (the
+// cluster loops over a small instance), which should stay in L1 and L2.
 __device__ __forceinline__ double ld_cached(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float ld_cached(const float* p) { return __ldg(p); }
 __device__ __forceinline__ int32_t ld_cached(const int32_t* p) { return __ldg(p); }
 
 // Partial dot product of one lane: entries b+first, b+first+stride, ... < e, loaded ILP at a
 // time (all loads of a batch issued before any is used) and accumulated in entry order.
-// kCached: matrix loads through L1 (ld_cached) instead of streaming past it.
+// kCached: matrix loads without the L2 evict-first hint (ld_cached), for a matrix slice that the
+// same SMs re-read every iteration.
 template <int ILP, class V, bool kCached = false>
 __device__ __forceinline__ V strided_dot_n(const int32_t* __restrict__ ci, const V* __restrict__ val,
                                            const V* __restrict__ xg, int first, int e, int stride,

@@ -27,8 +27,8 @@ def o_eta(lp):
     return o_solve(lp, 0.0, 1)["eta"]
 
 
-# instances with at most this many nonzeros run on one block each: 0 = all on the grid loop,
-# 4000 = some of each, 10**9 = all block-local
+# instances with at most this many nonzeros are small (cluster or single-CTA loop): 0 = all on
+# the grid loop, 4000 = some of each, 10**9 = all on the small-instance loops
 LOCAL = [0, 4000, 10 ** 9]
 
 
