@@ -7,9 +7,14 @@ if the library cannot be loaded, the first call raises.
 
 Low level (same names and arguments as the C ABI):
     lp_default_params, lp_create, lp_set_params, lp_solve, lp_get, lp_get_info,
-    lp_get_trace, lp_destroy, lp_last_error, lp_time_kernels, lp_debug_spmv, lp_debug_layout
+    lp_get_trace, lp_destroy, lp_last_error, lp_time_kernels, lp_debug_spmv, lp_debug_layout,
+    lp_power_norm_noalloc, lp_tune_schedule
 High level:
-    Solver(lp_or_arrays, **params) -> .solve(tol, max_iter, stream) -> .result()
+    Solver(lp, **params) -> .solve(tol, max_iter, stream) -> .result()
+    BatchSolver(lps, eta=None, tiles=None, **params): many LPs in one persistent loop
+        (include/lp_batch.h), plus the differentiable unrolled map (include/lp_diff.h) that
+        paper_2507_14051_b300.diff.UnrolledLPBatch wraps as a torch.autograd.Function
+    tune_batch(lps): per-instance tile schedules from lp_tune_schedule
 """
 from __future__ import annotations
 
