@@ -10,6 +10,8 @@ Low level (same names and arguments as the C ABI):
     lp_get_trace, lp_destroy, lp_last_error, lp_time_kernels, lp_debug_spmv, lp_debug_layout,
     lp_power_norm_noalloc, lp_tune_schedule
 High level:
+    solve(A, c, l_c, u_c, l_v, u_v, tol, max_iter, stream, **params): one call, scipy CSR on the
+        host or torch sparse CSR on the device
     Solver(lp, **params) -> .solve(tol, max_iter, stream) -> .result()
     BatchSolver(lps, eta=None, tiles=None, **params): many LPs in one persistent loop
         (include/lp_batch.h), plus the differentiable unrolled map (include/lp_diff.h) that
@@ -263,6 +265,49 @@ def lp_power_norm_noalloc(m, n, nnz, row_ptr, col_idx, val, tol=1e-7, max_iter=1
                                         int(max_iter), seed, stream, C.byref(out), C.byref(it)),
            "lp_power_norm_noalloc")
     return out.value, it.value
+
+
+def solve(A, c, l_c, u_c, l_v, u_v, tol=1e-8, max_iter=1_000_000, stream=None, **params):
+    """Solves one LP (Section 2.1: min c^T x, l_c <= A x <= u_c, l_v <= x <= u_v) in one call.
+
+    A is a scipy.sparse matrix with numpy vectors (host input), or a torch sparse CSR tensor on
+    a CUDA device with CUDA tensors (device input; passed by pointer).  The data are copied by
+    lp_create, solved on `stream` (a cudaStream_t as an int; None: the legacy default stream)
+    and the handle is destroyed.  Returns a dict with x and y in the original variables (numpy
+    for host input, CUDA float64 tensors for device input), status, kkt (relative gap, primal
+    and dual residuals, their maximum) and iters.  ``params`` are lp_params fields."""
+    prm = lp_default_params(**params)
+    if hasattr(A, "is_cuda") and A.is_cuda:
+        import torch
+        if A.layout != torch.sparse_csr:
+            A = A.to_sparse_csr()
+        m, n = int(A.shape[0]), int(A.shape[1])
+        rp = A.crow_indices().to(torch.int64).contiguous()
+        ci = A.col_indices().to(torch.int32).contiguous()
+        val = A.values().to(torch.float64).contiguous()
+        vecs = [torch.as_tensor(v, dtype=torch.float64, device=A.device).contiguous()
+                for v in (c, l_c, u_c, l_v, u_v)]
+        where = LP_DEVICE
+        x = torch.zeros(n, dtype=torch.float64, device=A.device)
+        y = torch.zeros(m, dtype=torch.float64, device=A.device)
+    else:
+        import scipy.sparse as sp
+        A = sp.csr_matrix(A)
+        A.sum_duplicates()
+        m, n = int(A.shape[0]), int(A.shape[1])
+        rp = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+        val = np.ascontiguousarray(A.data, dtype=np.float64)
+        vecs = [np.ascontiguousarray(v, dtype=np.float64) for v in (c, l_c, u_c, l_v, u_v)]
+        where = LP_HOST
+        x, y = np.zeros(n), np.zeros(m)
+    h = lp_create(m, n, int(rp[-1]), rp, ci, val, *vecs, where=where, params=prm)
+    try:
+        lp_solve(h, tol, max_iter, stream)
+        st, kkt, it = lp_get(h, x, y)
+    finally:
+        lp_destroy(h)
+    return dict(x=x, y=y, status=st, kkt=kkt, iters=it)
 
 
 class Solver:

@@ -346,3 +346,23 @@ def test_rescaled_solve_to_tolerance(cuda_device):
     if first_near_tie(o["trace"]) is None:
         assert g["iters"] == o["iters"]
     assert oracle.kkt(lp, g["x"], g["y"])[3] <= 1e-8
+
+
+def test_one_call_solve_from_scipy_and_torch_csr(cuda_device):
+    """lpx.solve takes a scipy CSR matrix with numpy vectors (host) or a torch sparse CSR tensor
+    with CUDA vectors (device); both equal the Solver's result bit for bit."""
+    import scipy.sparse as sp
+    import torch
+    lp = gen.small_lp(3)
+    A = sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n))
+    vecs = [getattr(lp, k) for k in ("c", "l_c", "u_c", "l_v", "u_v")]
+    with lpx.Solver(lp) as s:
+        ref = s.solve(1e-8, 100000).result()
+    host = lpx.solve(A, *vecs, tol=1e-8, max_iter=100000)
+    At = torch.sparse_csr_tensor(torch.tensor(lp.row_ptr), torch.tensor(lp.col_idx, dtype=torch.int64),
+                                 torch.tensor(lp.val), size=(lp.m, lp.n), device="cuda")
+    dev = lpx.solve(At, *[torch.tensor(v, device="cuda") for v in vecs], tol=1e-8, max_iter=100000)
+    assert host["status"] == dev["status"] == ref["status"] == oracle.OPTIMAL
+    assert host["iters"] == dev["iters"] == ref["iters"]
+    assert np.array_equal(host["x"], ref["x"]) and np.array_equal(host["y"], ref["y"])
+    assert np.array_equal(dev["x"].cpu().numpy(), ref["x"]) and np.array_equal(dev["y"].cpu().numpy(), ref["y"])
