@@ -744,20 +744,36 @@ cudaError_t launch_cluster_loop(const lp_batch* h, const BatchArgs<V>& a, const 
   return cudaLaunchKernelEx(&cfg, kb_cluster_loop<V, kCtas>, a, list, n, cap);
 }
 
+// The clustered small instances on clusters of k CTAs (8, 4 or 2).
 template <class V>
-cudaError_t launch_local(const lp_batch* h, const BatchArgs<V>& a, int64_t cap, cudaStream_t s) {
+cudaError_t launch_wide(const lp_batch* h, const BatchArgs<V>& a, int k, int64_t cap, cudaStream_t s) {
+  if (k == 4) return launch_cluster_loop<V, 4>(h, a, h->local_list, h->n_wide, cap, s);
+  if (k == 2) return launch_cluster_loop<V, 2>(h, a, h->local_list, h->n_wide, cap, s);
+  return launch_cluster_loop<V, kLocalCtas>(h, a, h->local_list, h->n_wide, cap, s);
+}
+
+// one_wave: clusters of the most CTAs (8, 4, 2) with which every clustered instance has its own
+// cluster at once.  A solve to tolerance keeps 8 (its small stragglers run longest, so each
+// instance's own speed decides); the schedule solve of the differentiable map runs exactly K
+// iterations of every instance, so a second wave of clusters would cost a second pass.
+template <class V>
+cudaError_t launch_local(const lp_batch* h, const BatchArgs<V>& a, int64_t cap, cudaStream_t s,
+                         bool one_wave = false) {
   const int32_t n_tiny = h->n_local - h->n_wide;
+  int k = kLocalCtas;
+  if (one_wave)
+    while (k > 2 && (int64_t)h->n_wide * k > 2 * (int64_t)h->num_sms) k >>= 1;
   cudaError_t e = cudaSuccess;
   if (h->n_wide > 0 && n_tiny > 0) {
     e = cudaEventRecord(h->ev_fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side_stream, h->ev_fork, 0);
     if (e == cudaSuccess) e = launch_cluster_loop<V, 1>(h, a, h->local_list + h->n_wide, n_tiny, cap, h->side_stream);
-    if (e == cudaSuccess) e = launch_cluster_loop<V, kLocalCtas>(h, a, h->local_list, h->n_wide, cap, s);
+    if (e == cudaSuccess) e = launch_wide<V>(h, a, k, cap, s);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_join, 0);
     return e;
   }
-  if (h->n_wide > 0) return launch_cluster_loop<V, kLocalCtas>(h, a, h->local_list, h->n_wide, cap, s);
+  if (h->n_wide > 0) return launch_wide<V>(h, a, k, cap, s);
   return launch_cluster_loop<V, 1>(h, a, h->local_list, n_tiny, cap, s);
 }
 
@@ -1216,7 +1232,7 @@ lp_status batch_schedule_solve(lp_batch* h, int64_t K, cudaStream_t s) {
     for (int64_t q = 0; q < launches; ++q)
       CK(launch_batch_loop<double>(h, a, kBatchUnroll, cudaGraphConditionalHandle{}, 0, s));
   }
-  if (h->n_local > 0) CK(launch_local<double>(h, a, K + 2, s));
+  if (h->n_local > 0) CK(launch_local<double>(h, a, K + 2, s, true));
   h->solved = true;
   h->last_stream = s;
   return LP_OK;
