@@ -1,0 +1,107 @@
+"""Parity at the benchmark workloads' full sizes, in the launch configurations bench.py times.
+
+The oracle cannot run these workloads whole in seconds, so each test checks sampled outputs that
+it can compute one by one: a few iterations of the multicommodity LP, sampled instances of the
+512-LP batch, sampled instances of the differentiable layer's batch.  Where the oracle's own
+power iteration on millions of nonzeros would dominate, both sides use the GPU's step size (the
+step size itself is compared with the oracle's at smaller sizes in test_gpu_parity.py and
+test_gpu_batch.py); for the layer, the oracle's unrolled map runs on the GPU's recorded
+schedule (schedule agreement is tested in test_gpu_diff.py).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import diff as od
+import paper_2507_14051_b300 as lpx
+from paper_2507_14051_b300 import gen
+
+from .test_gpu_diff import compare_grad, offsets
+from .test_gpu_parity import assert_iterates_close, compare_fixed, first_near_tie
+
+pytestmark = pytest.mark.gpu
+
+
+def test_full_size_multicommodity_iterates(cuda_device):
+    """The multicommodity benchmark LP (m = 1.8M, n = 4.0M, nnz = 12M), default parameters: 10
+    iterations against the oracle element by element, with the GPU's step size on both sides."""
+    lp = gen.multicommodity(0)
+    with lpx.Solver(lp) as s:
+        eta = s.solve(0.0, 1).result()["eta"]
+    compare_fixed(lp, 10, eta=eta)
+
+
+def test_full_size_batch_sampled_instances(cuda_device):
+    """The 512-instance benchmark batch with the default schedule: after 30 iterations, a
+    single-CTA instance, a clustered one, a mid-size grid-loop one and the largest one equal the
+    oracle's 30 iterations (with the batch's own step sizes) element by element."""
+    lps = gen.batch_uneven(0, count=512)
+    T = 30
+    with lpx.BatchSolver(lps) as b:
+        where = b.schedule()
+        b.solve(0.0, T)
+        summ = b.summary()
+        nnz = np.array([lp.nnz for lp in lps])
+        grid = np.nonzero(where == 0)[0]
+        picks = [int(np.nonzero(where == 2)[0][0]), int(np.nonzero(where == 1)[0][0]),
+                 int(grid[np.argsort(nnz[grid])[len(grid) // 2]]), int(np.argmax(nnz))]
+        got = {k: b.get(k) for k in picks}
+    assert np.all(summ["status"] == oracle.ITER_LIMIT) and np.all(summ["iters"] == T)
+    compared = 0
+    for k in picks:
+        o = oracle.solve(lps[k], tol=0.0, max_iter=T, trace=True, eta=float(summ["eta"][k]))
+        tie = first_near_tie(o["trace"])
+        if tie is not None and tie < T - 1:
+            continue
+        assert o["status"] == oracle.ITER_LIMIT and o["iters"] == T
+        assert_iterates_close(got[k]["x"], o["x"])
+        assert_iterates_close(got[k]["y"], o["y"])
+        compared += 1
+    assert compared >= 3
+
+
+def test_full_size_layer_sampled_instances(cuda_device):
+    """The differentiable layer's benchmark batch (64 LPs of 1000 x 2000, K = 2000, checkpoints
+    every 100, the layer's default schedule): for two instances the forward output equals the
+    oracle's unrolled map on the GPU's schedule, and sampled gradient entries equal central
+    differences of that map where it is affine on the difference interval."""
+    import torch
+    from paper_2507_14051_b300.diff import UnrolledLPBatch
+    K, C = 2000, 100
+    lps = [gen.small_lp(k, m=1000, n=2000, density=0.01) for k in range(64)]
+    dev = torch.device("cuda")
+    cat = lambda name: torch.tensor(np.concatenate([getattr(lp, name) for lp in lps]), device=dev)
+    c, lc, uc, lv, uv = (cat(k) for k in ("c", "l_c", "u_c", "l_v", "u_v"))
+    rng = np.random.default_rng(0)
+    xt = rng.uniform(0.0, 1.0, c.shape[0])
+    layer = UnrolledLPBatch(lps, K=K, checkpoint_every=C)
+    try:
+        cg = c.clone().requires_grad_(True)
+        ucg = uc.clone().requires_grad_(True)
+        x, y = layer(cg, lc, ucg, lv, uv)
+        ((x - torch.tensor(xt, device=dev)) ** 2).sum().backward()
+        xs = x.detach().cpu().numpy()
+        ys = y.detach().cpu().numpy()
+        gc = cg.grad.cpu().numpy()
+        guc = ucg.grad.cpu().numpy()
+        eta = layer.batch.summary()["eta"]
+        picks = [0, 37]
+        traces = {k: layer.batch.trace(k, K) for k in picks}
+    finally:
+        layer.close()
+    ox, oy = offsets(lps, "n"), offsets(lps, "m")
+    compared = 0
+    for k in picks:
+        lp, tr = lps[k], traces[k]
+        assert tr.shape[0] == K
+        xo, yo = od.unrolled(lp, tr, float(eta[k]), K)
+        np.testing.assert_allclose(xs[ox[k]:ox[k + 1]], xo, rtol=0, atol=1e-10 * max(1, np.abs(xo).max()))
+        np.testing.assert_allclose(ys[oy[k]:oy[k + 1]], yo, rtol=0, atol=1e-10 * max(1, np.abs(yo).max()))
+        xtk = xt[ox[k]:ox[k + 1]]
+        loss = lambda xx, yy, xtk=xtk: float(np.sum((xx - xtk) ** 2))
+        idx = rng.choice(lp.n, size=4, replace=False)
+        compared += compare_grad(lp, tr, float(eta[k]), K, loss, "c", idx, gc[ox[k]:ox[k + 1]][idx])
+        fin = np.nonzero(np.isfinite(lp.u_c) & (lp.l_c != lp.u_c))[0]
+        idx = rng.choice(fin, size=min(4, len(fin)), replace=False)
+        compared += compare_grad(lp, tr, float(eta[k]), K, loss, "u_c", idx, guc[oy[k]:oy[k + 1]][idx])
+    assert compared >= 4
