@@ -22,20 +22,62 @@ from .test_gpu_parity import assert_iterates_close, compare_fixed, first_near_ti
 pytestmark = pytest.mark.gpu
 
 
-def test_full_size_multicommodity_iterates(cuda_device):
+@pytest.fixture(scope="module")
+def batch512():
+    return gen.batch_uneven(0, count=512)
+
+
+@pytest.fixture(scope="module")
+def mcf():
+    return gen.multicommodity(0)
+
+
+def test_full_size_multicommodity_iterates(cuda_device, mcf):
     """The multicommodity benchmark LP (m = 1.8M, n = 4.0M, nnz = 12M), default parameters: 10
     iterations against the oracle element by element, with the GPU's step size on both sides."""
-    lp = gen.multicommodity(0)
+    lp = mcf
     with lpx.Solver(lp) as s:
         eta = s.solve(0.0, 1).result()["eta"]
     compare_fixed(lp, 10, eta=eta)
 
 
-def test_full_size_batch_sampled_instances(cuda_device):
+def test_full_size_mixed_multicommodity(cuda_device, mcf):
+    """The multicommodity LP in mixed precision (FP32 phase, then FP64) to 1e-4: the oracle's
+    FP64 KKT evaluation of the returned point meets the tolerance and agrees with the reported
+    values."""
+    with lpx.Solver(mcf, precision=1) as s:
+        r = s.solve(1e-4, 100000).result()
+    assert r["status"] == oracle.OPTIMAL and r["iters_fp32"] > 0
+    kk = oracle.kkt(mcf, r["x"], r["y"])
+    assert kk[3] <= 1e-4
+    np.testing.assert_allclose(r["kkt"], kk[:4], rtol=1e-7, atol=1e-13)
+
+
+def test_full_size_batch_mixed_to_tolerance(cuda_device, batch512):
+    """The 512-LP batch in mixed precision to 1e-8: every instance that stops OPTIMAL reports a
+    KKT error <= 1e-8, and for sampled instances the oracle's FP64 KKT evaluation of the returned
+    point agrees and meets the tolerance."""
+    lps = batch512
+    with lpx.BatchSolver(lps, precision=1) as b:
+        b.solve(1e-8, 100000)
+        summ = b.summary()
+        opt = np.nonzero(summ["status"] == oracle.OPTIMAL)[0]
+        assert len(opt) >= 510
+        assert np.all(summ["kkt"][opt, 3] <= 1e-8)
+        nnz = np.array([lp.nnz for lp in lps])
+        picks = [int(opt[np.argmin(nnz[opt])]), int(opt[len(opt) // 2]), int(opt[np.argmax(nnz[opt])])]
+        got = {k: b.get(k) for k in picks}
+    for k in picks:
+        kk = oracle.kkt(lps[k], got[k]["x"], got[k]["y"])
+        assert kk[3] <= 1e-8, k
+        np.testing.assert_allclose(got[k]["kkt"], kk[:4], rtol=1e-7, atol=1e-13)
+
+
+def test_full_size_batch_sampled_instances(cuda_device, batch512):
     """The 512-instance benchmark batch with the default schedule: after 30 iterations, a
     single-CTA instance, a clustered one, a mid-size grid-loop one and the largest one equal the
     oracle's 30 iterations (with the batch's own step sizes) element by element."""
-    lps = gen.batch_uneven(0, count=512)
+    lps = batch512
     T = 30
     with lpx.BatchSolver(lps) as b:
         where = b.schedule()
