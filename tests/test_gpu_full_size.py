@@ -147,3 +147,27 @@ def test_full_size_layer_sampled_instances(cuda_device):
         idx = rng.choice(fin, size=min(4, len(fin)), replace=False)
         compared += compare_grad(lp, tr, float(eta[k]), K, loss, "u_c", idx, guc[oy[k]:oy[k + 1]][idx])
     assert compared >= 4
+
+
+def test_full_size_miplib_like_to_tolerance(cuda_device):
+    """The MIPLIB-shaped benchmark LP solved to 1e-8 with the default parameters (as the
+    benchmark's tolerance run does, about a minute): the oracle's FP64 KKT evaluation of the
+    returned point meets the tolerance and agrees with the reported values, and the objective is
+    the planted optimum's."""
+    lp = gen.miplib_like(0)
+    with lpx.Solver(lp) as s:
+        r = s.solve(1e-8, 3_000_000).result()
+    assert r["status"] == oracle.OPTIMAL and r["iters"] % 64 == 0
+    kk = oracle.kkt(lp, r["x"], r["y"])
+    assert kk[3] <= 1e-8
+    # the relative gap |pobj - dobj| / (1 + |pobj| + |dobj|) cancels two nearly equal sums of
+    # ~10^5 terms; its rounding is absolute, about u times the sum of the terms' magnitudes
+    # over the denominator (1e-11 here), not relative to the tiny gap
+    np.testing.assert_allclose(r["kkt"][0], kk[0], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(r["kkt"][1:], kk[1:4], rtol=1e-7, atol=1e-13)
+    # the planted optimum p* lies between the objectives up to the residuals weighted by the
+    # optimal multipliers (weak duality for a point that violates the constraints by pres and the
+    # dual constraints by dres): |pobj - p*| <= |pobj - dobj| + |y*| pres + |x*| dres
+    pstar = float(lp.c @ lp.x_star)
+    bound = abs(kk[4] - kk[5]) + np.linalg.norm(lp.y_star) * kk[6] + np.linalg.norm(lp.x_star) * kk[7]
+    assert abs(kk[4] - pstar) <= bound + 1e-9 * (1 + abs(pstar))
