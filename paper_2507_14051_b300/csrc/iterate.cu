@@ -260,16 +260,6 @@ __global__ void k_to_float(int64_t len, const double* __restrict__ src, float* _
     dst[i] = (float)src[i];
 }
 
-// dst[i] = dst2[i] = (double)src[i] (dst2 may be null).
-__global__ void k_to_double(int64_t len, const float* __restrict__ src, double* __restrict__ dst,
-                            double* __restrict__ dst2) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)src[i];
-    dst[i] = v;
-    if (dst2) dst2[i] = v;
-  }
-}
-
 // Hand-over kernel of the single-instance solve (switch_ctl in step.cuh).
 __global__ void k_switch_ctl(Ctl* ctl, double tol, int64_t max_iter_fp64) {
   switch_ctl(*ctl, tol, max_iter_fp64);

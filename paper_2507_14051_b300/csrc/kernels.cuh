@@ -73,7 +73,6 @@ __global__ void k_spmv(const int32_t* rp, const int32_t* ci, const double* val, 
                        double* y, BinTable bins);
 // mixed precision: conversions and the hand-over from the FP32 phase to the FP64 phase
 __global__ void k_to_float(int64_t len, const double* src, float* dst);
-__global__ void k_to_double(int64_t len, const float* src, double* dst, double* dst2);
 __global__ void k_switch_ctl(Ctl* ctl, double tol, int64_t max_iter_fp64);
 __global__ void k_switch_vectors(int32_t n, int32_t m, Ctl* ctl, const float* xh0f,
                                  const float* xh1f, const float* yhf, const float* xb0,
