@@ -204,3 +204,22 @@ def test_tune_rejects_invalid_input_before_any_cuda_call():
                               C.byref(lt), C.byref(tr), None) == lpx.LP_ERR_INVALID_INPUT
     assert L.lp_tune_schedule(lp.m, lp.n, lp.nnz, rp.ctypes.data, bad.ctypes.data, v.ctypes.data, None,
                               None, None, None) == lpx.LP_ERR_INVALID_ARG
+
+
+def test_one_call_solve_refuses_invalid_input_before_any_cuda_call():
+    """lpx.solve marshals a scipy CSR matrix into lp_create, whose validation runs before the
+    first CUDA call: a crossed variable bound and a NaN objective entry are refused on a host
+    without a GPU."""
+    import scipy.sparse as sp
+    lp = gen.small_lp(1)
+    A = sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n))
+    lv, uv = lp.l_v.copy(), lp.u_v.copy()
+    lv[3], uv[3] = 2.0, 1.0
+    with pytest.raises(lpx.LPError) as e:
+        lpx.solve(A, lp.c, lp.l_c, lp.u_c, lv, uv)
+    assert e.value.code == lpx.LP_ERR_INVALID_INPUT
+    c = lp.c.copy()
+    c[0] = np.nan
+    with pytest.raises(lpx.LPError) as e:
+        lpx.solve(A, c, lp.l_c, lp.u_c, lp.l_v, lp.u_v)
+    assert e.value.code == lpx.LP_ERR_INVALID_INPUT
