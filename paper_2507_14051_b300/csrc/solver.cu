@@ -348,7 +348,34 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   for (int32_t i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
   for (int64_t p = 0; p < nnz; ++p) clen[ci[p]]++;
   order_by_class(rlen, h->row_perm);
-  order_by_class(clen, h->col_perm);
+  {
+    // columns grouped by length class like the rows, and inside a class in the order the
+    // permuted rows first reference them (unreferenced columns last): the entries of one row
+    // tile then gather nearby columns, fewer L2 sectors per tile (multicommodity FP64 iteration
+    // 286 -> 276 us)
+    std::vector<int32_t> seq;
+    seq.reserve(n);
+    std::vector<char> seen(n, 0);
+    for (int32_t i = 0; i < m; ++i) {
+      const int32_t o = h->row_perm[i];
+      for (int64_t p = rp[o]; p < rp[o + 1]; ++p)
+        if (!seen[ci[p]]) {
+          seen[ci[p]] = 1;
+          seq.push_back(ci[p]);
+        }
+    }
+    for (int32_t j = 0; j < n; ++j)
+      if (!seen[j]) seq.push_back(j);
+    std::vector<int64_t> count(33, 0), start(33, 0);
+    for (int32_t j = 0; j < n; ++j) count[length_class(clen[j])]++;
+    int64_t acc = 0;
+    for (int c = 32; c >= 0; --c) {
+      start[c] = acc;
+      acc += count[c];
+    }
+    h->col_perm.assign(n, 0);
+    for (int32_t q = 0; q < n; ++q) h->col_perm[start[length_class(clen[seq[q]])]++] = seq[q];
+  }
   std::vector<int32_t> col_inv(n);
   for (int32_t j = 0; j < n; ++j) col_inv[h->col_perm[j]] = j;
 
