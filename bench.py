@@ -8,11 +8,18 @@ update, KKT test) as one CUDA graph.  Setup (S0: validation, transpose, binning,
 preconditioning, power iteration) runs once in lp_create and is reported as `setup_ms`
 and inside `time_to_tol_s` and the end-to-end number.
 
-Workload (default): the MIPLIB-relaxation-shaped LP, m = 50k, n = 100k, nnz ~ 600k, seeded
-synthetic data with a planted optimum (paper_2507_14051_b300.gen.miplib_like, seed = rank).
+Workload (default): the multicommodity-flow LP (200k nodes, 1M arcs, 4 commodities: m = 1.8M,
+n = 4.0M, nnz = 12M), FP64, solved to relative KKT 1e-8 in every step; seeded synthetic data
+(paper_2507_14051_b300.gen.multicommodity, seed = rank).  Its working set (about 0.9 GB per
+iteration) is far larger than L2.
 Timing: W untimed warm-up solves, then K solves each bracketed by CUDA events on the solve
 stream, L2 flushed (256 MiB write) between solves outside the events, barrier +
 synchronize around the timed region, MAX over ranks.  value = total PDHG iterations / time.
+
+Secondary records (one GPU, after the timed region; `--secondary none` skips them): the
+MIPLIB-relaxation-shaped LP solved once to 1e-8 (untimed by the headline, timed by events),
+the 512-LP uneven batch to 1e-8 in FP64 and in mixed precision, and one forward + backward
+step of the differentiable layer (64 LPs, K = 2000).
 
 --impl reference times the FP64 CPU oracle (the method's plain reference implementation) on
 a bounded sample of the same workload.
@@ -47,11 +54,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="miplib", choices=["miplib", "mcf", "small", "batch", "diff"])
+    ap.add_argument("--workload", default="mcf", choices=["miplib", "mcf", "small", "batch", "diff"])
     ap.add_argument("--unroll", type=int, default=2000, help="diff workload: unrolled iterations K")
     ap.add_argument("--batch-count", type=int, default=512, help="instances of the batch workload")
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--max-iter", type=int, default=100000)
+    ap.add_argument("--max-iter", type=int, default=400000)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="0 FP64; 1 FP32 phase then FP64 refinement; 2 FP32 only")
     ap.add_argument("--switch-tol", type=float, default=1e-5)
@@ -63,6 +70,10 @@ def parse():
                     help="batch workload: also solve every instance alone with lp_solve in FP64")
     ap.add_argument("--tol-run-max-iter", type=int, default=0,
                     help="> 0: one extra untimed solve with this cap to report time to tol")
+    ap.add_argument("--secondary", default="miplib,batch,diff",
+                    help="comma list of secondary records after the timed region (miplib, batch, diff) or none")
+    ap.add_argument("--miplib-max-iter", type=int, default=2000000,
+                    help="iteration cap of the secondary MIPLIB-shaped solve to --tol")
     return ap.parse_args()
 
 
@@ -84,12 +95,14 @@ def workload_name(name: str, lp) -> str:
 
 def kernel_work(lp, vb=8, loop=True):
     """Algorithmic bytes and FP64 operations of one launch of each iteration kernel, for values
-    of vb bytes (8: FP64 kernels; 4: the FP32 kernels of precision 1 and 2) and 32-bit indices.
-    Bytes (what the method must move):
-      row kernel:    (4 + vb) nnz (A values + columns) + 4 (m+1) row offsets + vb n gathered
+    of vb bytes (8: FP64 kernels; 4: the FP32 kernels of precision 1 and 2).
+    Bytes (what the method must move, as the hot-path scope counts them: 4-byte column indices
+    and 8-byte row offsets; the device stores 4-byte offsets, so it moves 4 (m + n) bytes less):
+      row kernel:    (4 + vb) nnz (A values + columns) + 8 (m+1) row offsets + vb n gathered
                      xhat + 7 vb m (y, y0, l_c, u_c, y read; y, yhat written)
-      column kernel: (4 + vb) nnz + 4 (n+1) + vb m gathered yhat + 7 vb n (x, x0, c, l_v, u_v
+      column kernel: (4 + vb) nnz + 8 (n+1) + vb m gathered yhat + 7 vb n (x, x0, c, l_v, u_v
                      read; x, xhat written)
+    For vb = 8 the sum is 24 nnz + 72 (m + n) + 16 bytes per iteration.
     FP64 operations (fma/add/mul issued by the FP64 kernels' arithmetic): one fma per nonzero
     plus 17 per row (row kernel) or 12 per column (column kernel); 15 and 10 in the loop kernel
     (loop=True), whose phases leave the PID norms to a pass at restarts; None for the FP32
@@ -97,8 +110,29 @@ def kernel_work(lp, vb=8, loop=True):
     m, n, nnz = lp.m, lp.n, lp.nnz
     f64 = vb == 8
     er, ec = (15, 10) if loop else (17, 12)
-    return {"k1_rows": ((4 + vb) * nnz + 4 * (m + 1) + vb * n + 7 * vb * m, nnz + er * m if f64 else None),
-            "k2_cols": ((4 + vb) * nnz + 4 * (n + 1) + vb * m + 7 * vb * n, nnz + ec * n if f64 else None)}
+    return {"k1_rows": ((4 + vb) * nnz + 8 * (m + 1) + vb * n + 7 * vb * m, nnz + er * m if f64 else None),
+            "k2_cols": ((4 + vb) * nnz + 8 * (n + 1) + vb * m + 7 * vb * n, nnz + ec * n if f64 else None)}
+
+
+def cpu_info():
+    """Host CPU model and logical core count (the oracle's baseline is single-threaded)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def sgm10(times, shift=10.0):
+    """Shifted geometric mean with shift 10 (Section 4's summary of solve times in seconds):
+    exp(mean(log(t + 10))) - 10."""
+    t = np.asarray(times, dtype=float)
+    return float(np.exp(np.mean(np.log(t + shift))) - shift) if t.size else None
 
 
 # The sources each profiled kernel is built and launched from: a measured DRAM figure stays valid
@@ -222,7 +256,7 @@ def cpu_baseline(lp, eta, seconds, workload):
     t0 = time.perf_counter()
     out = oracle.solve(lp, tol=0.0, max_iter=iters, eta=eta)
     dt = time.perf_counter() - t0
-    return {"value": out["iters"] / dt, "unit": "iter/s", "cores": 1, "kind": "oracle",
+    return {"value": out["iters"] / dt, "unit": "iter/s", "cores": 1, "kind": "oracle", **cpu_info(),
             "sample": f"first {out['iters']} iterations from zero of the {workload} "
                       f"(tolerance off, oracle's own preconditioning included), {dt:.1f} s"}
 
@@ -272,7 +306,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl, "tol": args.tol, "step_iters": step_iters},
-            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "iter/s", "cores": 1, "kind": "oracle", **cpu_info(),
+                             "sample": sample},
             "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -321,7 +356,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     total_ms, total_iters, launches = 0.0, 0, 0
-    statuses, kkts = [], []
+    statuses, kkts, step_s = [], [], []
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
@@ -331,6 +366,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
+        step_s.append(e0.elapsed_time(e1) / 1e3)
         st, kkt, it = lpx.lp_get(solver.h)
         statuses.append(st)
         kkts.append(kkt.tolist())
@@ -371,22 +407,30 @@ def run_ours(args):
     gbs = bytes_ / (ms * 1e-3) / 1e9
     f_hbm = gbs / hbm_peak
     gops = ops / (ms * 1e-3) / 1e9 if ops is not None else None
-    f_alu = gops / FP64_NOMINAL_GOPS if ops is not None else 0.0
+    f_alu = gops / FP64_MEASURED_GOPS if ops is not None else 0.0
     kname = dom if vb == 8 else dom + "<float>"
     traffic = measured_traffic(kname, wl, int(kt[2]))
     if f_alu > f_hbm:
-        roof = {"bound": "alu", "achieved": gops, "peak": FP64_NOMINAL_GOPS, "unit": "FP64 Gop/s",
+        roof = {"bound": "alu", "achieved": gops, "peak": FP64_MEASURED_GOPS, "unit": "FP64 Gop/s",
                 "frac": f_alu, "traffic": traffic, "kernel": kname}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm,
                 "traffic": traffic, "kernel": kname}
-    roof.update({"peak_source": f"HBM {peak_src} copy {hbm_peak} GB/s; FP64 nominal {FP64_NOMINAL_GOPS} Gop/s "
-                                f"(measured issue rate {FP64_MEASURED_GOPS})",
+    roof.update({"hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": f_hbm,
+                         "peak_source": f"{peak_src} copy"},
+                 "fp64": ({"achieved": gops, "peak": FP64_MEASURED_GOPS, "unit": "Gop/s", "frac": f_alu,
+                           "frac_of_nominal": gops / FP64_NOMINAL_GOPS,
+                           "peak_source": f"measured issue rate {FP64_MEASURED_GOPS} G/s "
+                                          f"(nominal {FP64_NOMINAL_GOPS})"} if ops is not None else None),
+                 "peak_source": f"HBM {peak_src} copy {hbm_peak} GB/s; FP64 measured issue rate "
+                                f"{FP64_MEASURED_GOPS} Gop/s (nominal {FP64_NOMINAL_GOPS})",
+                 "bytes_model": "24 nnz + 72 (m + n) + 16 per FP64 iteration (4-byte indices, 8-byte row "
+                                "offsets); the device stores 4-byte offsets",
                  "kernels": {k: {"ms_per_launch": per[k], "iters_per_launch": int(kt[2]),
                                  "alg_bytes_per_launch": work[k][0], "fp64_ops_per_launch": work[k][1],
                                  "GB/s": work[k][0] / (per[k] * 1e-3) / 1e9,
                                  "frac_hbm": work[k][0] / (per[k] * 1e-3) / 1e9 / hbm_peak,
-                                 "frac_fp64": (work[k][1] / (per[k] * 1e-3) / 1e9 / FP64_NOMINAL_GOPS
+                                 "frac_fp64": (work[k][1] / (per[k] * 1e-3) / 1e9 / FP64_MEASURED_GOPS
                                                if work[k][1] is not None else None)}
                              for k in per},
                  "timing": f"mean of {int(kt[3])} launches, CUDA events on the solve stream",
@@ -430,6 +474,21 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(lp, float(info[0]), args.cpu_seconds, wl)
 
+    secondary = {}
+    wanted = [w for w in args.secondary.split(",") if w and w != "none"]
+    if world == 1 and wanted:
+        solver.close()
+        del flush
+        torch.cuda.empty_cache()
+        runners = {"miplib": lambda: secondary_miplib(args, stream), "batch": lambda: secondary_batch(args, stream),
+                   "diff": lambda: secondary_diff(args)}
+        for w in wanted:
+            try:
+                secondary[w] = runners[w]()
+            except Exception as exc:  # reported, not hidden: the headline record stands without it
+                secondary[w] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
+
     if rank == 0:
         solved = all(s == 1 for s in statuses)
         line = {
@@ -452,12 +511,128 @@ def run_ours(args):
                     "includes": "lp_create from pinned host arrays (validation, transpose, binning, "
                                 "preconditioning, power iteration, H2D) + lp_solve + lp_get to host"},
             "gpu_launches": launches, "clocks": clocks, "tol_run": tol_run,
+            "sgm10_time_to_tol_s": sgm10([setup_ms / 1e3 + t for t in step_s]) if solved else None,
+            "secondary": secondary or None,
         }
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def secondary_miplib(args, stream):
+    """The MIPLIB-relaxation-shaped LP (m = 50k, n = 100k, nnz ~ 600k, seed 0), FP64: one solve to
+    --tol capped at --miplib-max-iter (CUDA events on the solve stream), and its loop kernel's
+    live roofline.  Its working set (~25 MB) stays in L2."""
+    import torch
+    import paper_2507_14051_b300 as lpx
+    lp = make_workload("miplib", 0)
+    sp = stream.cuda_stream
+    t0 = time.perf_counter()
+    solver = lpx.Solver(lp)
+    setup_s = time.perf_counter() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.solve(args.tol, args.miplib_max_iter, sp)
+    e1.record(stream)
+    e1.synchronize()
+    solve_s = e0.elapsed_time(e1) / 1e3
+    st, kkt, it = lpx.lp_get(solver.h)
+    kt = lpx.lp_time_kernels(solver.h, 64, sp)
+    solver.close()
+    w = kernel_work(lp, 8, loop=kt[1] == 0.0)
+    per_iter = int(kt[2]) if kt[1] == 0.0 else 1
+    ms = kt[0] if kt[1] == 0.0 else kt[0] + kt[1]
+    byt = per_iter * (w["k1_rows"][0] + w["k2_cols"][0])
+    ops = per_iter * (w["k1_rows"][1] + w["k2_cols"][1])
+    hbm_peak, _ = load_peaks()
+    return {"workload": workload_name("miplib", lp), "status": int(st), "iters": int(it), "solve_s": solve_s,
+            "setup_s": setup_s, "time_to_tol_s": setup_s + solve_s if st == 1 else None,
+            "iters_per_s": it / solve_s, "rel_kkt": kkt.tolist(), "tol": args.tol, "max_iter": args.miplib_max_iter,
+            "kernel": {"name": "k_loop" if kt[1] == 0.0 else "k1_rows+k2_cols", "us_per_iter": 1e3 * ms / per_iter,
+                       "frac_hbm": byt / (ms * 1e-3) / 1e9 / hbm_peak,
+                       "frac_fp64": ops / (ms * 1e-3) / 1e9 / FP64_MEASURED_GOPS,
+                       "note": "L2-resident working set: the HBM fraction is not a DRAM test here"}}
+
+
+def secondary_batch(args, stream):
+    """The 512-LP uneven batch (m log-uniform in [100, 20000], n = 2m, 1 % density, seed 0) to
+    --tol in one persistent launch per stage, FP64 and mixed precision (FP32 phase, FP64
+    refinement): setup (lp_batch_create), device solve time (CUDA events), statuses, and the
+    grid loop kernel's live HBM fraction in FP64."""
+    import torch
+    import paper_2507_14051_b300 as lpx
+    from paper_2507_14051_b300 import gen
+    lps = gen.batch_uneven(0, count=args.batch_count)
+    sp = stream.cuda_stream
+    out = {"workload": f"{len(lps)} uneven LPs, m log-uniform in [100, 20000], n = 2m, 1 % density, "
+                       f"sum nnz = {sum(lp.nnz for lp in lps)}", "tol": args.tol}
+    hbm_peak, _ = load_peaks()
+    for prec, key in ((0, "fp64"), (1, "mixed")):
+        t0 = time.perf_counter()
+        b = lpx.BatchSolver(lps, precision=prec)
+        setup_s = time.perf_counter() - t0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.solve(args.tol, 100000, sp)
+        e1.record(stream)
+        e1.synchronize()
+        sm = b.summary()
+        rec = {"setup_s": setup_s, "solve_s": e0.elapsed_time(e1) / 1e3,
+               "optimal": int((sm["status"] == 1).sum()), "iter_limit": int((sm["status"] == 2).sum()),
+               "instance_iters": int(sm["iters"].sum()), "iters_median": float(np.median(sm["iters"])),
+               "iters_max": int(sm["iters"].max())}
+        rec["time_to_tol_s"] = rec["setup_s"] + rec["solve_s"]
+        if prec == 0:
+            local_nnz = int(b.params.batch_local_nnz)
+            ms64, per = b.time_loop(64, fp64=True, stream=sp)
+            gbs = batch_work(lps, local_nnz, 8) * per / (ms64 * 1e-3) / 1e9
+            rec["grid_loop"] = {"kernel": "kb_loop<double>", "ms_per_launch": ms64, "iters_per_launch": per,
+                                "GB/s": gbs, "frac_hbm": gbs / hbm_peak}
+        out[key] = rec
+        b.close()
+    return out
+
+
+def secondary_diff(args):
+    """The differentiable layer (64 LPs, m = 1000, n = 2000, 1 % density; K = 2000 unrolled
+    iterations, checkpoints every 100; L = |x - x_target|^2): one warm-up and three timed
+    forward + backward steps (CUDA events)."""
+    import torch
+    from paper_2507_14051_b300 import gen
+    from paper_2507_14051_b300.diff import UnrolledLPBatch
+    count, K, C = 64, 2000, 100
+    lps = [gen.small_lp(k, m=1000, n=2000, density=0.01) for k in range(count)]
+    t0 = time.perf_counter()
+    layer = UnrolledLPBatch(lps, K=K, checkpoint_every=C)
+    setup_s = time.perf_counter() - t0
+    dev = torch.device("cuda")
+    cat = lambda name: torch.tensor(np.concatenate([getattr(lp, name) for lp in lps]), device=dev)
+    base = {k: cat(k) for k in ("c", "l_c", "u_c", "l_v", "u_v")}
+    xt = torch.rand(base["c"].shape[0], dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(0))
+
+    def step():
+        c = base["c"].clone().requires_grad_(True)
+        uc = base["u_c"].clone().requires_grad_(True)
+        x, y = layer(c, base["l_c"], uc, base["l_v"], base["u_v"])
+        L = ((x - xt) ** 2).sum()
+        L.backward()
+        return L
+
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        step()
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / 3
+    layer.close()
+    return {"workload": f"{count} LPs m=1000 n=2000 1 % density, K={K} unrolled steps, checkpoints every {C}",
+            "setup_s": setup_s, "ms_per_fwd_bwd_step": ms, "unrolled_iters_per_s": K / (ms * 1e-3),
+            "grads": "c, u_c"}
 
 
 def batch_work(lps, local_nnz, vb):
@@ -485,7 +660,7 @@ def batch_cpu_baseline(lps, tol, seconds):
         t_used += time.perf_counter() - t0
         it += out["iters"]
         k += 1
-    return {"value": it / t_used, "unit": "instance-iter/s", "cores": 1, "kind": "oracle",
+    return {"value": it / t_used, "unit": "instance-iter/s", "cores": 1, "kind": "oracle", **cpu_info(),
             "sample": f"instances 0..{k - 1} of the batch, each solved to {tol:g} from zero (at most "
                       f"20k iterations), single-threaded FP64 oracle, {t_used:.1f} s"}
 
@@ -780,6 +955,7 @@ def run_diff(args):
         od.unrolled(lps[0], tr, eta, ks)
         dt = time.perf_counter() - t0
         cpu = {"value": 1.0 / (dt * (K / ks) * count), "unit": "forward steps/s (no backward)", "cores": 1,
+               **cpu_info(),
                "kind": "oracle",
                "sample": f"oracle solve + unrolled map, {ks} iterations of instance 0 ({dt:.1f} s), "
                          f"scaled to {count} instances x {K} iterations"}

@@ -250,16 +250,22 @@ LP_API lp_status lp_debug_layout(lp_handle h, int32_t* row_perm, int32_t* col_pe
  * library holds on every device that loads it until the process exits.
  *   m, n       at most 262144 each; larger sizes return LP_ERR_TOO_LARGE.
  *   row_ptr, col_idx, val   CSR of A in device memory of the current device (int64 offsets,
- *              0-based int32 column indices, doubles); not validated.
+ *              0-based int32 column indices, doubles; row_ptr has m + 1 entries, col_idx and
+ *              val nnz).  The kernels check every offset and column index as they read it:
+ *              an offset outside [0, nnz], decreasing offsets or a column index outside
+ *              [0, n) is never dereferenced, and the call returns LP_ERR_INVALID_INPUT.
  *   tol, max_iter, seed     stopping rule and start vector as in lp_params.
- *   stream     cudaStream_t (NULL: legacy default stream); the call is synchronous.
+ *   stream     cudaStream_t (NULL: legacy default stream); the call is synchronous.  Steps are
+ *              queued 16 at a time with one host synchronisation per 16 steps.
  *   norm_out   receives the estimate (0 for an empty matrix); iters_out (may be NULL) the steps.
- * The first call on a device looks up the device address of the static scratch with that
- * device current; make that first call before any stream capture.  Every call on a device
- * shares the same scratch: calls that overlap on the GPU (other threads, other streams) race
- * and give wrong results.  The transposed product uses atomic adds, so the last bits of the
- * estimate can differ from run to run.
- * Errors: LP_ERR_INVALID_ARG, LP_ERR_TOO_LARGE, LP_ERR_CUDA.
+ * Every call looks up the device address of the static scratch in the current device's
+ * context (cudaGetSymbolAddress, which allocates nothing), so the address stays valid across a
+ * cudaDeviceReset.  The first call on a device may load the library's device code; make that
+ * first call before any stream capture.  Every call on a device shares the same scratch:
+ * calls that overlap on the GPU (other threads, other streams) race and give wrong results.
+ * The transposed product uses atomic adds, so the last bits of the estimate can differ from
+ * run to run.
+ * Errors: LP_ERR_INVALID_ARG, LP_ERR_INVALID_INPUT, LP_ERR_TOO_LARGE, LP_ERR_CUDA.
  */
 LP_API lp_status lp_power_norm_noalloc(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
                                        const int32_t* col_idx, const double* val, double tol,

@@ -258,7 +258,28 @@ def lp_debug_layout(h, m: int, n: int):
 def lp_power_norm_noalloc(m, n, nnz, row_ptr, col_idx, val, tol=1e-7, max_iter=10000, seed=0,
                           stream: int | None = None):
     """||A||_2 estimate for a device CSR (torch CUDA tensors) without device allocation;
-    returns (norm, steps).  See include/lp.h for the limits and the shared scratch."""
+    returns (norm, steps).  See include/lp.h for the limits and the shared scratch.
+
+    The arrays must be contiguous torch tensors on the current CUDA device with dtypes int64
+    (row_ptr, m + 1 entries), int32 (col_idx, nnz) and float64 (val, nnz); anything else is
+    refused here (ValueError) before the library reads a byte of it."""
+    if nnz > 0:
+        import torch
+        want = ((row_ptr, torch.int64, m + 1, "row_ptr"), (col_idx, torch.int32, nnz, "col_idx"),
+                (val, torch.float64, nnz, "val"))
+        for t, dt, length, name in want:
+            if not isinstance(t, torch.Tensor):
+                raise ValueError(f"{name} must be a torch tensor on the current CUDA device")
+            if t.dtype != dt:
+                raise ValueError(f"{name} must have dtype {dt}, got {t.dtype}")
+        for t, dt, length, name in want:
+            if not t.is_contiguous():
+                raise ValueError(f"{name} must be contiguous")
+            if t.numel() < length:
+                raise ValueError(f"{name} has {t.numel()} entries, needs {length}")
+        for t, dt, length, name in want:
+            if not t.is_cuda or t.device.index != torch.cuda.current_device():
+                raise ValueError(f"{name} must live on the current CUDA device")
     out = C.c_double(0.0)
     it = C.c_int64(0)
     _check(load().lp_power_norm_noalloc(m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val), tol,

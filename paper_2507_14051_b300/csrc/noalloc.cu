@@ -2,12 +2,15 @@
 //
 // This is the power iteration that lp_create runs, for callers that cannot allocate device
 // memory: all of its scratch -- the two iterate vectors, the product A u, the per-block
-// partial sums and the scalars -- lives in one file-scope static device array that the
-// library reserves on every device that loads it, for the life of the process.  The matrix
-// is the caller's CSR of A as given (no transpose, no binning): A u is a warp per row, and
-// A^T w is a scatter with atomic adds, so its last bits depend on the order of those adds.
+// partial sums, the scalars and a short history of the estimates -- lives in one file-scope
+// static device array that the library reserves on every device that loads it, for the life
+// of the process.  The matrix is the caller's CSR of A as given (no transpose, no binning):
+// A u is a warp per row, and A^T w is a scatter with atomic adds, so its last bits depend on
+// the order of those adds.  The caller's CSR is checked inside the kernels as it is read: an
+// entry outside [0, nnz) or a column index outside [0, n) is skipped and raises a flag, which
+// the host turns into LP_ERR_INVALID_INPUT.
 #include <cmath>
-#include <mutex>
+#include <cstring>
 #include <string>
 
 #include "lp.h"
@@ -19,14 +22,18 @@ namespace {
 constexpr int64_t kNaMaxDim = int64_t(1) << 18;  // m and n at most 262144
 constexpr int kNaThreads = 256;
 constexpr int kNaMaxBlocks = 1024;
-// layout (doubles): u[kNaMaxDim] | v[kNaMaxDim] | w[kNaMaxDim] | partials[kNaMaxBlocks] | ctl[32]
+constexpr int kNaBatch = 16;  // power steps per host synchronisation
+// layout (doubles): u[kNaMaxDim] | v[kNaMaxDim] | w[kNaMaxDim] | partials[kNaMaxBlocks] |
+// ctl[16] | hist[kNaBatch] (the estimate of each step of the current batch)
 constexpr int64_t kNaOffU = 0, kNaOffV = kNaMaxDim, kNaOffW = 2 * kNaMaxDim;
 constexpr int64_t kNaOffPart = 3 * kNaMaxDim, kNaOffCtl = 3 * kNaMaxDim + kNaMaxBlocks;
-constexpr int64_t kNaTotal = kNaOffCtl + 32;
+constexpr int64_t kNaOffHist = kNaOffCtl + 16;
+constexpr int64_t kNaTotal = kNaOffHist + kNaBatch;
 
 static __device__ __align__(256) double g_na_scratch[kNaTotal];
 
-// ctl slots: 0 lambda, 1 s (= 1/|u|); slot 2 holds an unsigned arrival counter
+// ctl slots: 0 lambda of the last step, 1 s (= 1/|u|); slot 2 holds an unsigned arrival
+// counter, slot 3 an unsigned flag (nonzero: the CSR had an entry out of range)
 struct NaPtrs {
   double* base;
   __host__ __device__ double* u() const { return base + kNaOffU; }
@@ -34,7 +41,9 @@ struct NaPtrs {
   __host__ __device__ double* w() const { return base + kNaOffW; }
   __host__ __device__ double* part() const { return base + kNaOffPart; }
   __host__ __device__ double* ctl() const { return base + kNaOffCtl; }
+  __host__ __device__ double* hist() const { return base + kNaOffHist; }
   __host__ __device__ unsigned* counter() const { return reinterpret_cast<unsigned*>(base + kNaOffCtl + 2); }
+  __host__ __device__ unsigned* bad() const { return reinterpret_cast<unsigned*>(base + kNaOffCtl + 3); }
 };
 
 // Block sum of one value per thread (fixed-order tree); the last block to arrive writes
@@ -79,8 +88,22 @@ __device__ __forceinline__ double na_start_entry(uint64_t seed, uint64_t i) {
   return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
 }
 
-// u = start vector (original column order), s = 1/|u|.
+// Row i's entry range [b, e), clipped to [0, nnz); raises the flag if the offsets are out of
+// range or decreasing (the row is then read as clipped, or skipped).
+__device__ __forceinline__ void na_row_range(const int64_t* __restrict__ rp, int64_t i, int64_t nnz, NaPtrs p,
+                                             int lane, int64_t& b, int64_t& e) {
+  b = rp[i];
+  e = rp[i + 1];
+  if (b < 0 || e > nnz || b > e) {
+    if (lane == 0) atomicOr(p.bad(), 1u);
+    b = b < 0 ? 0 : (b > nnz ? nnz : b);
+    e = e < b ? b : (e > nnz ? nnz : e);
+  }
+}
+
+// u = start vector (original column order), s = 1/|u|; clears the flag.
 __global__ void __launch_bounds__(kNaThreads) na_start(int32_t n, uint64_t seed, NaPtrs p) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *p.bad() = 0u;
   double acc = 0.0;
   for (int64_t j = blockIdx.x * (int64_t)kNaThreads + threadIdx.x; j < n; j += (int64_t)gridDim.x * kNaThreads) {
     const double e = na_start_entry(seed, (uint64_t)j);
@@ -90,11 +113,14 @@ __global__ void __launch_bounds__(kNaThreads) na_start(int32_t n, uint64_t seed,
   na_block_total(acc, p, p.ctl() + 1, [](double t) { return t > 0.0 ? 1.0 / sqrt(t) : 0.0; });
 }
 
-// w = s * (A u) (warp per row), lambda = |w|^2; v <- 0 for the scatter that follows.
-__global__ void __launch_bounds__(kNaThreads) na_rows(int32_t m, int32_t n, const int64_t* __restrict__ rp,
+// w = s * (A u) (warp per row), lambda = |w|^2 (also stored as hist[q]); v <- 0 for the
+// scatter that follows.  Entries with a column index outside [0, n) are skipped.
+__global__ void __launch_bounds__(kNaThreads) na_rows(int32_t m, int32_t n, int64_t nnz,
+                                                      const int64_t* __restrict__ rp,
                                                       const int32_t* __restrict__ ci,
                                                       const double* __restrict__ val, NaPtrs p,
-                                                      const double* __restrict__ u, double* __restrict__ v) {
+                                                      const double* __restrict__ u, double* __restrict__ v,
+                                                      int32_t q) {
   const double sc = p.ctl()[1];
   for (int64_t j = blockIdx.x * (int64_t)kNaThreads + threadIdx.x; j < n; j += (int64_t)gridDim.x * kNaThreads)
     v[j] = 0.0;
@@ -102,19 +128,30 @@ __global__ void __launch_bounds__(kNaThreads) na_rows(int32_t m, int32_t n, cons
   const int64_t nw = (int64_t)gridDim.x * (kNaThreads / 32);
   double acc = 0.0;
   for (int64_t i = (blockIdx.x * (int64_t)kNaThreads + threadIdx.x) >> 5; i < m; i += nw) {
+    int64_t b, e;
+    na_row_range(rp, i, nnz, p, lane, b, e);
     double d = 0.0;
-    for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) d = fma(val[k], u[ci[k]], d);
+    for (int64_t k = b + lane; k < e; k += 32) {
+      const int32_t j = ci[k];
+      if (j >= 0 && j < n) d = fma(val[k], u[j], d);
+      else atomicOr(p.bad(), 1u);
+    }
     d = warp_sum(d) * sc;
     if (lane == 0) {
       p.w()[i] = d;
       acc = fma(d, d, acc);
     }
   }
-  na_block_total(acc, p, p.ctl() + 0, [](double t) { return t; });
+  double* hq = p.hist() + q;
+  na_block_total(acc, p, p.ctl() + 0, [hq](double t) {
+    *hq = t;
+    return t;
+  });
 }
 
-// v += A^T w (scatter, warp per row).
-__global__ void __launch_bounds__(kNaThreads) na_scatter(int32_t m, const int64_t* __restrict__ rp,
+// v += A^T w (scatter, warp per row; out-of-range entries skipped).
+__global__ void __launch_bounds__(kNaThreads) na_scatter(int32_t m, int32_t n, int64_t nnz,
+                                                         const int64_t* __restrict__ rp,
                                                          const int32_t* __restrict__ ci,
                                                          const double* __restrict__ val, NaPtrs p,
                                                          double* __restrict__ v) {
@@ -122,7 +159,12 @@ __global__ void __launch_bounds__(kNaThreads) na_scatter(int32_t m, const int64_
   const int64_t nw = (int64_t)gridDim.x * (kNaThreads / 32);
   for (int64_t i = (blockIdx.x * (int64_t)kNaThreads + threadIdx.x) >> 5; i < m; i += nw) {
     const double wi = p.w()[i];
-    for (int64_t k = rp[i] + lane; k < rp[i + 1]; k += 32) atomicAdd(v + ci[k], val[k] * wi);
+    int64_t b, e;
+    na_row_range(rp, i, nnz, p, lane, b, e);
+    for (int64_t k = b + lane; k < e; k += 32) {
+      const int32_t j = ci[k];
+      if (j >= 0 && j < n) atomicAdd(v + j, val[k] * wi);
+    }
   }
 }
 
@@ -133,10 +175,6 @@ __global__ void __launch_bounds__(kNaThreads) na_norm(int32_t n, NaPtrs p, const
     acc = fma(v[j], v[j], acc);
   na_block_total(acc, p, p.ctl() + 1, [](double t) { return t > 0.0 ? 1.0 / sqrt(t) : 0.0; });
 }
-
-// Device address of the static scratch, looked up once per device (with that device current).
-std::mutex g_na_mutex;
-double* g_na_addr[64] = {};
 
 lp_status na_fail(lp_status code, std::string* err, const std::string& msg) {
   *err = msg;
@@ -173,21 +211,17 @@ extern "C" lp_status lp_power_norm_noalloc(int32_t m, int32_t n, int64_t nnz, co
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= 64)
+  if (e != cudaSuccess)
     return done(na_fail(LP_ERR_CUDA, &err, std::string("cudaGetDevice: ") + cudaGetErrorString(e)));
-  double* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_addr[dev]) {
-      void* ptr = nullptr;
-      e = cudaGetSymbolAddress(&ptr, g_na_scratch);
-      if (e != cudaSuccess)
-        return done(na_fail(LP_ERR_CUDA, &err, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)));
-      g_na_addr[dev] = static_cast<double*>(ptr);
-    }
-    base = g_na_addr[dev];
-  }
-  NaPtrs p{base};
+  // The device address of the static scratch in the current device's context, looked up on
+  // every call (a host-side lookup once the module is loaded): a cached address would dangle
+  // after the context is torn down and re-created (cudaDeviceReset).  The first call on a
+  // device may load the module, which is why it must not happen inside a stream capture.
+  void* ptr = nullptr;
+  e = cudaGetSymbolAddress(&ptr, g_na_scratch);
+  if (e != cudaSuccess)
+    return done(na_fail(LP_ERR_CUDA, &err, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)));
+  NaPtrs p{static_cast<double*>(ptr)};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -207,26 +241,44 @@ extern "C" lp_status lp_power_norm_noalloc(int32_t m, int32_t n, int64_t nnz, co
   na_start<<<gv, kNaThreads, 0, s>>>(n, seed, p);
   double* u = p.u();
   double* v = p.v();
+  // Steps run kNaBatch at a time; each records its estimate in hist[q], and the host applies
+  // the stopping rule to the batch in step order after one synchronisation (steps past the
+  // stopping one change only the scratch).
+  double got[kNaBatch + 1];
   double lam = 0.0, prev = 0.0;
-  int64_t it;
-  for (it = 1; it <= max_iter; ++it) {
-    na_rows<<<gr, kNaThreads, 0, s>>>(m, n, row_ptr, col_idx, val, p, u, v);
-    e = cudaMemcpyAsync(&lam, p.ctl() + 0, sizeof(double), cudaMemcpyDeviceToHost, s);
+  int64_t it = 0;
+  bool stop = false;
+  while (!stop && it < max_iter) {
+    const int64_t left = max_iter - it;
+    const int batch = left < kNaBatch ? (int)left : kNaBatch;
+    for (int q = 0; q < batch; ++q) {
+      na_rows<<<gr, kNaThreads, 0, s>>>(m, n, nnz, row_ptr, col_idx, val, p, u, v, q);
+      na_scatter<<<gr, kNaThreads, 0, s>>>(m, n, nnz, row_ptr, col_idx, val, p, v);
+      na_norm<<<gv, kNaThreads, 0, s>>>(n, p, v);
+      double* t = u;
+      u = v;
+      v = t;
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(got, p.hist(), sizeof(double) * batch, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(got + kNaBatch, p.ctl() + 3, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return done(na_fail(LP_ERR_CUDA, &err, std::string("power iteration: ") + cudaGetErrorString(e)));
-    if (lam == 0.0) break;
-    na_scatter<<<gr, kNaThreads, 0, s>>>(m, row_ptr, col_idx, val, p, v);
-    na_norm<<<gv, kNaThreads, 0, s>>>(n, p, v);
-    double* t = u;
-    u = v;
-    v = t;
-    if (it > 1 && std::fabs(lam - prev) <= tol * lam) break;
-    prev = lam;
+    unsigned bad = 0;
+    std::memcpy(&bad, got + kNaBatch, sizeof(unsigned));
+    if (bad)
+      return done(na_fail(LP_ERR_INVALID_INPUT, &err,
+                          "lp_power_norm_noalloc: CSR entry out of range (row_ptr outside [0, nnz] or "
+                          "decreasing, or a column index outside [0, n))"));
+    for (int q = 0; q < batch && !stop; ++q) {
+      ++it;
+      lam = got[q];
+      if (lam == 0.0) stop = true;
+      else if (it > 1 && std::fabs(lam - prev) <= tol * lam) stop = true;
+      else prev = lam;
+    }
   }
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return done(na_fail(LP_ERR_CUDA, &err, std::string("power iteration: ") + cudaGetErrorString(e)));
   *norm_out = std::sqrt(lam);
-  if (iters_out) *iters_out = it > max_iter ? max_iter : it;
+  if (iters_out) *iters_out = it;
   return done(LP_OK);
 }

@@ -16,12 +16,20 @@
 #include "lp.h"
 #include "kernels.cuh"
 #include "host_util.h"
+#include <nvtx3/nvToolsExt.h>
 
 using namespace pdhg;
 using namespace pdhg_host;
 
 namespace {
 thread_local std::string g_err;
+
+// NVTX range around an entry point (visible in a profiler's timeline; the header-only NVTX API
+// does nothing unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 }  // namespace
 
 // Sets the calling thread's lp_last_error message (used by entry points in other files).
@@ -601,6 +609,7 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr,
                     const int32_t* col_idx, const double* val, const double* c,
                     const double* l_c, const double* u_c, const double* l_v, const double* u_v,
                     int32_t where, const lp_params* p, lp_handle* out) {
+  NvtxRange nvtx("lp_create");
   g_err.clear();
   if (!out) return fail(LP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -752,6 +761,7 @@ lp_status enqueue_switch(lp_solver* h, double tol, int64_t max_iter, cudaStream_
 extern "C" {
 
 lp_status lp_solve(lp_handle h, double tol, int64_t max_iter, void* stream) {
+  NvtxRange nvtx("lp_solve");
   g_err.clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "handle is NULL");
   if (!(tol >= 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be >= 0");
@@ -788,6 +798,7 @@ lp_status lp_solve(lp_handle h, double tol, int64_t max_iter, void* stream) {
 
 lp_status lp_get(lp_handle h, double* x, double* y, int32_t* solve_status, double* kkt,
                  int64_t* iters) {
+  NvtxRange nvtx("lp_get");
   g_err.clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "handle is NULL");
   if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "lp_get before lp_solve");

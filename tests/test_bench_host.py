@@ -1,4 +1,5 @@
-"""Host-side bookkeeping of bench.py (no GPU): the kernel-launch counts it reports."""
+"""Host-side bookkeeping of bench.py (no GPU): the kernel-launch counts, byte model and summary
+statistics it reports."""
 import numpy as np
 
 import bench
@@ -32,5 +33,20 @@ def test_kernel_work_fp32_moves_fewer_bytes_and_no_fp64_ops():
     b64, b32 = bench.kernel_work(LP(), 8), bench.kernel_work(LP(), 4)
     for k in ("k1_rows", "k2_cols"):
         assert b32[k][0] < b64[k][0] and b32[k][1] is None and b64[k][1] > 0
-    assert b64["k1_rows"][0] == 12 * 50 + 4 * 11 + 8 * 20 + 56 * 10
+    assert b64["k1_rows"][0] == 12 * 50 + 8 * 11 + 8 * 20 + 56 * 10
+    # the scope table's per-iteration figure: 24 nnz + 72 (m + n) + 16
+    assert b64["k1_rows"][0] + b64["k2_cols"][0] == 24 * 50 + 72 * 30 + 16
     assert b64["k1_rows"][1] == 50 + 15 * 10 and bench.kernel_work(LP(), 8, loop=False)["k1_rows"][1] == 50 + 17 * 10
+
+
+def test_sgm10_is_the_shifted_geometric_mean():
+    """Section 4 summarises solve times by the shifted geometric mean with shift 10."""
+    assert bench.sgm10([5.0]) == 5.0
+    # (t + 10) = 10 and 40: geometric mean 20, minus the shift
+    assert abs(bench.sgm10([0.0, 30.0]) - 10.0) < 1e-12
+    assert bench.sgm10([]) is None
+
+
+def test_cpu_info_reports_model_and_core_count():
+    info = bench.cpu_info()
+    assert info["nproc"] >= 1 and "cpu_model" in info

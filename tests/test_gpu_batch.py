@@ -13,7 +13,7 @@ import oracle
 import paper_2507_14051_b300 as lpx
 from paper_2507_14051_b300 import gen
 
-from .test_gpu_parity import SHARED, assert_iterates_close, first_near_tie
+from .test_gpu_parity import SHARED, assert_iterates_close, first_near_tie, tie_is_late
 
 pytestmark = pytest.mark.gpu
 
@@ -57,6 +57,8 @@ def test_batch_fixed_iterations_match_oracle(cuda_device, make, iters, local):
     for lp, e in zip(lps, etas):
         o = o_solve(lp, 0.0, iters, trace=True, eta=e)
         tie = first_near_tie(o["trace"])
+        if tie is not None and tie < iters - 1:  # the harness's floor on a cut comparison
+            assert tie + 1 >= 0.9 * iters or tie_is_late(o["trace"], tie), (tie, iters)
         cut.append(iters if tie is None or tie >= iters - 1 else tie + 1)
         traces.append(o)
     with lpx.BatchSolver(lps, eta=etas, batch_local_nnz=local) as b:
@@ -93,6 +95,9 @@ def test_batch_to_tolerance(cuda_device, seed, local):
         tie = first_near_tie(o["trace"])
         if tie is None or tie >= o["iters"] - 1:
             assert g["iters"] == o["iters"], k
+        else:  # only a converged-regime tie may move the stopping check, by one period at most
+            assert tie_is_late(o["trace"], tie), (k, tie, o["iters"])
+            assert abs(g["iters"] - o["iters"]) <= 64, (k, g["iters"], o["iters"])
         kk = oracle.kkt(lp, g["x"], g["y"])
         assert kk[3] <= 1e-8, k
         np.testing.assert_allclose(g["kkt"], kk[:4], rtol=1e-7, atol=1e-13)
@@ -114,10 +119,13 @@ def test_batch_matches_single_instance_solver(cuda_device, local):
             s.solve(0.0, 300)
             r = s.result()
         o = o_solve(lp, 0.0, 300, trace=True, eta=e)
-        if first_near_tie(o["trace"]) is not None:
-            continue
-        assert_iterates_close(g["x"], r["x"])
-        assert_iterates_close(g["y"], r["y"])
+        tie = first_near_tie(o["trace"])
+        rtol = 1e-10
+        if tie is not None:  # a converged-regime tie may part the two sums' orders by about r_tie
+            assert tie_is_late(o["trace"], tie), tie
+            rtol = 1e-6
+        assert_iterates_close(g["x"], r["x"], rtol=rtol)
+        assert_iterates_close(g["y"], r["y"], rtol=rtol)
 
 
 def test_batch_power_iteration_step_sizes(cuda_device):
@@ -220,10 +228,13 @@ def test_batch_with_per_instance_schedules_matches_oracle(cuda_device, local):
         res = [b.get(k) for k in range(len(lps))]
     for lp, e, g in zip(lps, etas, res):
         o = o_solve(lp, 0.0, 200, trace=True, eta=e)
-        if first_near_tie(o["trace"]) is not None:
-            continue
-        assert_iterates_close(g["x"], o["x"])
-        assert_iterates_close(g["y"], o["y"])
+        tie = first_near_tie(o["trace"])
+        rtol = 1e-10
+        if tie is not None:
+            assert tie_is_late(o["trace"], tie), tie
+            rtol = 1e-6
+        assert_iterates_close(g["x"], o["x"], rtol=rtol)
+        assert_iterates_close(g["y"], o["y"], rtol=rtol)
 
 
 def test_batch_schedule_classes(cuda_device):

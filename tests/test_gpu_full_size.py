@@ -33,12 +33,27 @@ def mcf():
 
 
 def test_full_size_multicommodity_iterates(cuda_device, mcf):
-    """The multicommodity benchmark LP (m = 1.8M, n = 4.0M, nnz = 12M), default parameters: 10
-    iterations against the oracle element by element, with the GPU's step size on both sides."""
+    """The multicommodity benchmark LP (m = 1.8M, n = 4.0M, nnz = 12M), default parameters: 200
+    iterations against the oracle element by element (three termination checks, at 64, 128 and
+    192, and the restarts of the first epochs), with the GPU's step size on both sides."""
     lp = mcf
     with lpx.Solver(lp) as s:
         eta = s.solve(0.0, 1).result()["eta"]
-    compare_fixed(lp, 10, eta=eta)
+    g, o = compare_fixed(lp, 200, eta=eta)
+    assert int(np.sum(o["trace"][:, 2])) >= 5  # restarts compared
+    assert o["iters"] >= 193
+
+
+def test_full_size_multicommodity_fp64_to_1e4(cuda_device, mcf):
+    """The plain FP64 solve of the multicommodity LP to 1e-4 (Section 4) with default parameters:
+    OPTIMAL, and the oracle's FP64 KKT evaluation of the returned point meets the tolerance and
+    agrees with the reported values."""
+    with lpx.Solver(mcf) as s:
+        r = s.solve(1e-4, 100000).result()
+    assert r["status"] == oracle.OPTIMAL and r["iters_fp32"] == 0
+    kk = oracle.kkt(mcf, r["x"], r["y"])
+    assert kk[3] <= 1e-4
+    np.testing.assert_allclose(r["kkt"], kk[:4], rtol=1e-7, atol=1e-13)
 
 
 def test_full_size_mixed_multicommodity(cuda_device, mcf):

@@ -15,7 +15,13 @@ Restart decisions compare r against beta * r0 and against the previous r.  When 
 is inside the rounding error of r (a floating-point tie), either outcome is a correct
 evaluation of the paper's rule, and after a differing decision the trajectories part.  The
 harness therefore finds the oracle's first near-tie decision and compares both sides over the
-iterations before it (the run is cut so that the tied decision is never taken).
+iterations before it (the run is cut so that the tied decision is never taken).  A cut must not
+hide the comparison: it is accepted only when it leaves at least 90 % of the requested
+iterations, or when the tie comes after the run has converged to the rounding floor
+(r_tie <= 1e-9 max_t r_t, where every later decision compares residuals of ~1e-16 relative
+differences); the uncut runs are then still compared at the requested count, both sides within
+1e-6 of each other (a decision taken differently that late moves the iterates by about r_tie).
+Any other cut fails the test with its position.
 """
 import numpy as np
 import pytest
@@ -76,14 +82,35 @@ def first_near_tie(trace, beta_s=0.2, beta_n=0.8, rel=1e-9, floor=1e-12):
     return None
 
 
+TIE_CONVERGED = 1e-9  # a restart near-tie is tolerated once r_t <= this * max r
+
+
+def tie_is_late(trace, tie):
+    """True if the near-tie decision at `tie` comes after the run converged to the rounding floor."""
+    r = trace[:, 0]
+    return bool(r[tie] <= TIE_CONVERGED * float(np.max(r)))
+
+
 def compare_fixed(lp, iters, **params):
     """Both sides run `iters` iterations (tol = 0) with the same explicit step size, cut
-    before the first near-tie restart decision if there is one."""
+    before the first near-tie restart decision if there is one; a cut that leaves less than
+    90 % of the iterations is accepted only after convergence (module docstring), and then the
+    full runs are also compared at 1e-6."""
     params = dict(params)
     params.setdefault("eta", oracle_eta(lp, **params))
+    requested = iters
     o = oracle_solve(lp, 0.0, iters, trace=True, **params)
     tie = first_near_tie(o["trace"], params.get("beta_sufficient", 0.2), params.get("beta_necessary", 0.8))
     if tie is not None and tie < iters - 1:
+        late = tie_is_late(o["trace"], tie)
+        assert tie + 1 >= 0.9 * requested or late, (
+            f"restart near-tie at iteration {tie} (r/max r = {o['trace'][tie, 0] / np.max(o['trace'][:, 0]):.2e}) "
+            f"would cut the comparison to {tie + 1} of {requested} iterations")
+        if late:
+            full_g = gpu_solve(lp, 0.0, requested, **params)
+            assert full_g["iters"] == o["iters"] == requested
+            assert_iterates_close(full_g["x"], o["x"], rtol=1e-6)
+            assert_iterates_close(full_g["y"], o["y"], rtol=1e-6)
         iters = tie + 1
         o = oracle_solve(lp, 0.0, iters, trace=True, **params)
     g = gpu_solve(lp, 0.0, iters, trace=True, **params)
@@ -209,6 +236,9 @@ def test_small_lp_to_tolerance(cuda_device, seed):
     tie = first_near_tie(o["trace"])
     if tie is None or tie >= o["iters"] - 1:
         assert g["iters"] == o["iters"]
+    else:  # only a converged-regime tie may move the stopping check, and by one period at most
+        assert tie_is_late(o["trace"], tie), (tie, o["iters"])
+        assert abs(g["iters"] - o["iters"]) <= 64, (g["iters"], o["iters"])
     k = oracle.kkt(lp, g["x"], g["y"])
     assert k[3] <= 1e-8
     np.testing.assert_allclose(g["kkt"], k[:4], rtol=1e-7, atol=1e-13)

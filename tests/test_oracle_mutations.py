@@ -1,6 +1,11 @@
 """Planted mistakes: each test compiles a copy of the oracle with one plausible error (a flipped
 sign, a dropped term, a swapped bound) and checks that a pin of tests/test_oracle_pins.py
-rejects it.  This shows the pins constrain every part of the oracle they are meant to."""
+rejects it.  This shows the pins constrain every part of the oracle they are meant to.
+
+One plausible slip in the restart bookkeeping is deliberately absent: also setting r_prev = r on
+a restart step.  It cannot change any result, because the step after a restart has k = 0,
+which never restarts and always sets r_prev = r before the next test reads it (Section 3's
+r(z^{n,k-1}) at k = 1 is r(z^{n,0})); no test can tell it apart from the oracle."""
 import os
 
 import numpy as np
@@ -54,6 +59,19 @@ MUTATIONS = {
     "restart_artificial": ("if ((double)k >= beta_a * (double)(t + 1)) return 1;",
                            "if ((double)k >= beta_a * (double)(k + 1)) return 1;",
                            ["restart"]),
+    # restart point: the anchor set to the pre-step iterate z instead of the PDHG output z^
+    # (Section 3, "restart ... at the current solution", read as z^ = T(z))
+    "restart_anchor_at_z": ("for (int32_t j = 0; j < n; ++j) x[j] = x0[j] = xh[j];",
+                            "for (int32_t j = 0; j < n; ++j) { x0[j] = x[j]; x[j] = xh[j]; }",
+                            ["restart_trace"]),
+    # r0 never refreshed after the first epoch (Section 3: r0 = r(z^{n,0}) of the current epoch)
+    "restart_r0_first_epoch_only": ("if (k == 0) r0 = r;", "if (t == 0) r0 = r;",
+                                    ["restart_epochs"]),
+    # r0 taken from the step that decided the restart instead of the new epoch's first step
+    "restart_r0_at_restart_step": ([("if (k == 0) r0 = r;", "if (t == 0) r0 = r;"),
+                                    ("      k = 0;\n      if (trace && t < trace_cap) trace[4 * t + 2] = 1.0;",
+                                     "      k = 0;\n      r0 = r;\n      if (trace && t < trace_cap) trace[4 * t + 2] = 1.0;")],
+                                   ["restart_epochs"]),
     # Ruiz: factor 1/max instead of 1/sqrt(max)
     "ruiz_sqrt": ("for (int32_t i = 0; i < m; ++i) fr[i] = fr[i] > 0.0 ? 1.0 / sqrt(fr[i]) : 1.0;",
                   "for (int32_t i = 0; i < m; ++i) fr[i] = fr[i] > 0.0 ? 1.0 / fr[i] : 1.0;",
@@ -71,6 +89,8 @@ CHECKS = {
     "solve": lambda: ([pins.test_solve_reaches_planted_optimum(s) for s in range(2)],
                       [pins.test_solve_matches_vertex_enumeration(s) for s in range(3)]),
     "scale": lambda: (pins.test_ruiz_equilibrates_rows_and_columns(), pins.test_pock_chambolle_pass()),
+    "restart_trace": lambda: pins.test_restart_trace_hand_worked(),
+    "restart_epochs": lambda: [pins.test_restart_decisions_follow_the_epoch_definitions(s) for s in range(3)],
 }
 
 
@@ -81,10 +101,13 @@ def test_unmutated_oracle_passes_every_check():
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(name, tmp_path):
-    old, new, checks = MUTATIONS[name]
+    sites, checks = MUTATIONS[name][:-1], MUTATIONS[name][-1]
+    pairs = sites[0] if len(sites) == 1 else [sites]
     src = oracle.source()
-    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
-    path = oracle.compile_variant(src.replace(old, new), os.path.join(tmp_path, f"lib_{name}.so"))
+    for old, new in pairs:
+        assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+        src = src.replace(old, new)
+    path = oracle.compile_variant(src, os.path.join(tmp_path, f"lib_{name}.so"))
     with oracle.using_library(path):
         for chk in checks:
             with pytest.raises(AssertionError):

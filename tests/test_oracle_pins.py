@@ -233,6 +233,64 @@ def test_restart_decisions_hand_labelled():
         assert got == cs["restart"], cs
 
 
+def _frac(v):
+    num, _, den = v.partition("/")
+    return float(num) / float(den or 1)
+
+
+def test_restart_trace_hand_worked():
+    """Section 3, the restart bookkeeping inside the solve: nine iterations of a 1x1 LP worked by
+    hand with exact fractions (tests/golden/restart_trace_1x1.json), spanning two artificial
+    restarts.  Each step's PDHG output (x^, y^), residual r_t, primal weight, epoch step k and
+    restart flag follow from r0 = r at the epoch's first step, r_prev = the previous step's r,
+    the restart point and anchor = the PDHG output z^ (not the pre-step iterate z), and the PID
+    update at each restart (K_P = 1 gives omega' = |dy| / |dx|)."""
+    g = _load("restart_trace_1x1.json")
+    lp = _lp_from_dense(g["lp"])
+    prm = dict(g["params"])
+    steps = g["steps"]
+    T = len(steps)
+    out = oracle.solve(lp, tol=0.0, max_iter=T, trace=True, **prm)
+    tr = out["trace"]
+    assert tr.shape[0] == T
+    for st, row in zip(steps, tr):
+        assert row[0] == pytest.approx(math.sqrt(_frac(st["r2"])), rel=1e-12), st["t"]
+        assert row[1] == pytest.approx(_frac(st["omega"]), rel=1e-12), st["t"]
+        assert row[2] == st["restart"], st["t"]
+        assert row[3] == st["k"], st["t"]
+    for st in steps:  # the solve stopped after t + 1 iterations returns z^_t
+        o = oracle.solve(lp, tol=0.0, max_iter=st["t"] + 1, **prm)
+        assert o["x"][0] == pytest.approx(_frac(st["xhat"]), rel=1e-12, abs=1e-14), st["t"]
+        assert o["y"][0] == pytest.approx(_frac(st["yhat"]), rel=1e-12, abs=1e-14), st["t"]
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_restart_decisions_follow_the_epoch_definitions(seed):
+    """Section 3: at every step with k >= 1 of a long solve, the oracle restarts exactly when the
+    (separately pinned) decision rule says so for r0 = the residual of the epoch's first step
+    (k = 0) and r_prev = the residual of the step before; after a restart the next step has
+    k = 0, otherwise k + 1; the primal weight changes only right after a restart."""
+    lp = gen.free_and_boxed_mix(seed, 40, 70) if seed == 2 else gen.small_lp(seed, 60, 140, 0.05)
+    out = oracle.solve(lp, tol=0.0, max_iter=4000, trace=True, check_every=10 ** 6)
+    tr = out["trace"]
+    restarts = 0
+    r0 = None
+    for t in range(tr.shape[0]):
+        r, om, flag, k = tr[t]
+        if k == 0:
+            r0 = r
+            assert flag == 0.0
+        else:
+            want = oracle.restart_decide(int(k), t, r, r0, tr[t - 1, 0])
+            assert bool(flag) == want, (t, r, r0, tr[t - 1, 0], k)
+        if t + 1 < tr.shape[0]:
+            assert tr[t + 1, 3] == (0.0 if flag else k + 1), t
+            if not flag:
+                assert tr[t + 1, 1] == om, t
+        restarts += int(flag)
+    assert restarts >= 5
+
+
 def test_pid_three_restarts_hand_worked():
     g = _load("pid_three_restarts.json")
     pid = oracle.PID(g["gains"]["k_p"], g["gains"]["k_i"], g["gains"]["k_d"])
