@@ -93,7 +93,7 @@ def workload_name(name: str, lp) -> str:
     return f"{base}, m={lp.m}, n={lp.n}, nnz={lp.nnz}, FP64"
 
 
-def kernel_work(lp, vb=8, loop=True):
+def kernel_work(lp, vb=8, loop=True, refl=False):
     """Algorithmic bytes and FP64 operations of one launch of each iteration kernel, for values
     of vb bytes (8: FP64 kernels; 4: the FP32 kernels of precision 1 and 2).
     Bytes (what the method must move, as the hot-path scope counts them: 4-byte column indices
@@ -105,11 +105,11 @@ def kernel_work(lp, vb=8, loop=True):
     For vb = 8 the sum is 24 nnz + 72 (m + n) + 16 bytes per iteration.
     FP64 operations (fma/add/mul issued by the FP64 kernels' arithmetic): one fma per nonzero
     plus 17 per row (row kernel) or 12 per column (column kernel); 15 and 10 in the loop kernel
-    (loop=True), whose phases leave the PID norms to a pass at restarts; None for the FP32
-    kernels."""
+    (loop=True), whose phases leave the PID norms to a pass at restarts; 12 and 9 in its
+    reflected form (refl=True, gamma = 1); None for the FP32 kernels."""
     m, n, nnz = lp.m, lp.n, lp.nnz
     f64 = vb == 8
-    er, ec = (15, 10) if loop else (17, 12)
+    er, ec = ((12, 9) if refl else (15, 10)) if loop else (17, 12)
     return {"k1_rows": ((4 + vb) * nnz + 8 * (m + 1) + vb * n + 7 * vb * m, nnz + er * m if f64 else None),
             "k2_cols": ((4 + vb) * nnz + 8 * (n + 1) + vb * m + 7 * vb * n, nnz + ec * n if f64 else None)}
 
@@ -146,16 +146,18 @@ TRAFFIC_SOURCES = {
 }
 
 
-def design_bytes(lp, vb=8):
+def design_bytes(lp, vb=8, refl=False):
     """Bytes the iteration kernels are designed to move per iteration (vb-byte values, 32-bit
-    indices), beyond the algorithmic bytes: the maintained A x and A^T y and their anchors.  Row
-    side: A's values and indices, row offsets, the gathered xhat, and per row y0, yhat, y, A xhat,
-    A x, A x0, l_c, u_c read and y, A x, yhat, A xhat written (12 vectors); column side likewise
-    with per column xhat, x0, x, A^T y, A^T y0, c, l_v, u_v read and x, A^T y, the next xhat
-    written (11 vectors)."""
+    indices and offsets).  Plain form: the maintained A x and A^T y and their anchors -- per row
+    y0, yhat, y, A xhat, A x, A x0, l_c, u_c read and y, A x, yhat, A xhat written (12 vectors),
+    per column xhat, x0, x, A^T y, A^T y0, c, l_v, u_v read and x, A^T y, the next xhat written
+    (11).  Reflected form (refl=True): per row qy, y0, w, A x0, l_c, u_c read and qy, yhat, w
+    written (9), per column xbar, x0, A^T y0, c, l_v, u_v read and xbar, the next xhat written
+    (8).  Both add A's values and indices, the row offsets and the gathered vector per side."""
     m, n, z = lp.m, lp.n, lp.nnz
-    rows = (4 + vb) * z + 4 * (m + 1) + vb * n + 12 * vb * m
-    cols = (4 + vb) * z + 4 * (n + 1) + vb * m + 11 * vb * n
+    vr, vc = (9, 8) if refl else (12, 11)
+    rows = (4 + vb) * z + 4 * (m + 1) + vb * n + vr * vb * m
+    cols = (4 + vb) * z + 4 * (n + 1) + vb * m + vc * vb * n
     return rows + cols
 
 
@@ -391,7 +393,8 @@ def run_ours(args):
     # (the kernels of the solve's first stage: FP32 for precision 1 and 2)
     kt = lpx.lp_time_kernels(solver.h, args.kernel_iters, sp)
     vb = 8 if args.precision == 0 else 4
-    work = kernel_work(lp, vb, loop=kt[1] == 0.0)
+    refl = kt[1] == 0.0 and float(prm.gamma) == 1.0  # the loop kernel's reflected form
+    work = kernel_work(lp, vb, loop=kt[1] == 0.0, refl=refl)
     hbm_peak, peak_src = load_peaks()
     if kt[1] == 0.0:  # the cooperative loop kernel runs kt[2] iterations per launch
         per_iter = int(kt[2])
@@ -434,7 +437,8 @@ def run_ours(args):
                                                if work[k][1] is not None else None)}
                              for k in per},
                  "timing": f"mean of {int(kt[3])} launches, CUDA events on the solve stream",
-                 "design_bytes_per_launch": design_bytes(lp, vb) * int(kt[2]) if kt[1] == 0.0 else None})
+                 "form": "reflected" if refl else "plain",
+                 "design_bytes_per_launch": design_bytes(lp, vb, refl) * int(kt[2]) if kt[1] == 0.0 else None})
 
     # end to end through the C ABI with host buffers: create (H2D inside) + solve + get (D2H)
     arrs = [np.ascontiguousarray(lp.row_ptr, np.int64), np.ascontiguousarray(lp.col_idx, np.int32),
@@ -541,7 +545,7 @@ def secondary_miplib(args, stream):
     st, kkt, it = lpx.lp_get(solver.h)
     kt = lpx.lp_time_kernels(solver.h, 64, sp)
     solver.close()
-    w = kernel_work(lp, 8, loop=kt[1] == 0.0)
+    w = kernel_work(lp, 8, loop=kt[1] == 0.0, refl=kt[1] == 0.0)
     per_iter = int(kt[2]) if kt[1] == 0.0 else 1
     ms = kt[0] if kt[1] == 0.0 else kt[0] + kt[1]
     byt = per_iter * (w["k1_rows"][0] + w["k2_cols"][0])

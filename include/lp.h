@@ -88,9 +88,11 @@ typedef struct {
                               0: automatic (8 for lp_solve; 32 for the batch, whose long rows
                               then take fewer FP64 butterfly additions per row) */
   int32_t persistent;      /* 1: one cooperative kernel runs `unroll` iterations per launch with
-                              grid-wide barriers between phases; 0: one kernel per phase;
-                              -1: the first when every block of both phases fits on the GPU at
-                              once (latency-bound sizes), else the second */
+                              grid-wide barriers between phases; 2: the same loop as one block
+                              (block barriers only; for LPs of a few dozen tiles per phase);
+                              0: one kernel per phase; -1: 2 when each phase has at most
+                              4 tiles per warp of one block, else 1 when every block of both
+                              phases fits on the GPU at once, else 0 */
   int32_t precision;       /* 0: FP64 throughout.  1: mixed -- matrix and iterates in FP32 with
                               FP32 SpMV accumulation (reductions, restart test, PID and KKT test in
                               FP64) until the relative KKT error is <= max(tol, switch_tol) or
@@ -111,9 +113,10 @@ typedef struct {
   int32_t tile_rows;       /* rows per warp tile (1..32, rounded down to a power of two): a tile
                               of R rows, each read by G lanes (G from lane_target), takes R G / 32
                               passes and runs its R row epilogues in R lanes at once; 0: automatic
-                              (1 for lp_solve, whose latency-bound sizes want short tasks; 8 for
-                              the batch, whose long rows would otherwise spend one warp's FP64
-                              issue on each row's epilogue) */
+                              (lp_solve: 32 when A and A^T each give at least 8 tiles of 32 rows
+                              per resident warp of the loop kernel, else 1, since latency-bound
+                              sizes want short tasks; the batch: 8, since its long rows would
+                              otherwise spend one warp's FP64 issue on each row's epilogue) */
   int64_t batch_local_nnz; /* lp_batch_* only: instances with at most this many nonzeros are
                               solved by one cluster of 8 CTAs each (cluster barriers only)
                               instead of by the grid-wide loop; 0 puts every instance on the grid
@@ -188,7 +191,8 @@ LP_API lp_status lp_get(lp_handle h, double* x, double* y, int32_t* solve_status
 /* Extra scalars of the last solve (host doubles): out[0] eta, out[1] final omega,
  * out[2] restarts, out[3] ||A~||_2 from the power iteration (0 if eta was given),
  * out[4] power-iteration steps, out[5] primal objective c^T x, out[6] dual objective,
- * out[7] 1 if the cooperative loop kernel runs the solve, 0 if one kernel per phase does,
+ * out[7] 1 if the cooperative loop kernel runs the solve (2 if as one block), 0 if one kernel
+ * per phase does,
  * out[8] iterations done in FP32 (precision 1 or 2; 0 for FP64).
  * Waits like lp_get.  Errors: LP_ERR_INVALID_ARG, LP_ERR_NOT_SOLVED, LP_ERR_CUDA. */
 LP_API lp_status lp_get_info(lp_handle h, double* out9);

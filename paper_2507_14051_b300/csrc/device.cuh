@@ -218,6 +218,64 @@ __device__ __forceinline__ V strided_dot(const int32_t* __restrict__ ci, const V
   return strided_dot_n<kIlp, V, kCached>(ci, val, xg, first, e, stride, pol);
 }
 
+// One batch of N entries of a lane's strided slice (k0, k0 + stride, ...; entries at or past e
+// are absent), all loads issued before any is used, accumulated into acc in entry order.
+template <int N, class V, bool kCached>
+__device__ __forceinline__ void dot_batch(const int32_t* __restrict__ ci, const V* __restrict__ val,
+                                          const V* __restrict__ xg, int k0, int e, int stride,
+                                          const LoadPolicy& pol, V& acc) {
+  V v[N];
+  int c[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    const int k = k0 + u * stride;
+    if (k < e) {
+      if (kCached) {
+        v[u] = ld_cached(val + k);
+        c[u] = ld_cached(ci + k);
+      } else {
+        v[u] = ld_stream(val + k, pol.stream);
+        c[u] = ld_stream(ci + k, pol.stream);
+      }
+    } else {
+      v[u] = V(0);
+      c[u] = -1;
+    }
+  }
+  V xv[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) xv[u] = c[u] >= 0 ? ld_gather(xg + c[u], pol.keep) : V(0);
+#pragma unroll
+  for (int u = 0; u < N; ++u)
+    if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+}
+
+// Partial dot product of one lane over exactly `slots` strided entries (warp-uniform: the most
+// entries any lane of the warp has in this pass), in batches of 8 and one exact remainder
+// batch: the warp issues one fma instruction per slot and none for slots no lane has (on this
+// GPU an FP64 warp instruction costs the same pipe time whatever its active lanes).  The lane's
+// entries are accumulated in entry order, as strided_dot does.
+template <class V, bool kCached = false>
+__device__ __forceinline__ V strided_dot_slots(const int32_t* __restrict__ ci, const V* __restrict__ val,
+                                               const V* __restrict__ xg, int first, int e, int stride,
+                                               int slots, const LoadPolicy& pol) {
+  V acc = V(0);
+  int k0 = first;
+  for (; slots >= kIlp; slots -= kIlp, k0 += kIlp * stride)
+    dot_batch<kIlp, V, kCached>(ci, val, xg, k0, e, stride, pol, acc);
+  switch (slots) {
+    case 1: dot_batch<1, V, kCached>(ci, val, xg, k0, e, stride, pol, acc); break;
+    case 2: dot_batch<2, V, kCached>(ci, val, xg, k0, e, stride, pol, acc); break;
+    case 3: dot_batch<3, V, kCached>(ci, val, xg, k0, e, stride, pol, acc); break;
+    case 4: dot_batch<4, V, kCached>(ci, val, xg, k0, e, stride, pol, acc); break;
+    case 5: dot_batch<5, V, kCached>(ci, val, xg, k0, e, stride, pol, acc); break;
+    case 6: dot_batch<6, V, kCached>(ci, val, xg, k0, e, stride, pol, acc); break;
+    case 7: dot_batch<7, V, kCached>(ci, val, xg, k0, e, stride, pol, acc); break;
+    default: break;
+  }
+  return acc;
+}
+
 // Two partial dot products of one lane, over [fa, ea) and [fb, eb) with the same stride, their
 // loads issued together (twice the loads in flight of strided_dot_n); each is accumulated in
 // entry order exactly as strided_dot_n would.
@@ -314,12 +372,15 @@ __device__ __forceinline__ void tile_spmv_pair(const int32_t* __restrict__ ci, c
 
 // Dot products of the rows [row0, row0 + nrows) (nrows <= 32) of a CSR matrix with xg.
 // G lanes per row, 32/G rows per pass; lane L returns the value of row L (garbage for
-// L >= nrows).  Summation: each lane accumulates its strided entries in order, then a
-// fixed xor butterfly over the G lanes (deterministic).
+// L >= nrows).  Each pass runs as many entry slots as its longest row needs (a warp maximum of
+// the rows' own lengths; `per_lane`, the length class's bound, is not needed).  Summation: each
+// lane accumulates its strided entries in order, then a fixed xor butterfly over the G lanes
+// (deterministic).
 template <class V, bool kCached = false>
 __device__ __forceinline__ V tile_spmv_b(const int32_t* __restrict__ ci, const V* __restrict__ val,
                                          const V* __restrict__ xg, int my_b, int my_e, int nrows, int G,
                                          int per_lane, int lane, const LoadPolicy& pol) {
+  (void)per_lane;
   const int rpp = 32 / G;  // rows per pass
   const int passes = (nrows + rpp - 1) / rpp;
   const int g = lane / G, sub = lane - g * G;
@@ -328,7 +389,9 @@ __device__ __forceinline__ V tile_spmv_b(const int32_t* __restrict__ ci, const V
     const int q = p * rpp + g;  // row of this lane's group in this pass
     const int b = __shfl_sync(kFull, my_b, q & 31);
     const int e = __shfl_sync(kFull, my_e, q & 31);
-    V acc = q < nrows ? strided_dot<V, kCached>(ci, val, xg, b + sub, e, G, per_lane, pol) : V(0);
+    const int mine_slots = q < nrows && e > b + sub ? (e - b - sub + G - 1) / G : 0;
+    const int slots = (int)__reduce_max_sync(kFull, (unsigned)mine_slots);
+    V acc = q < nrows ? strided_dot_slots<V, kCached>(ci, val, xg, b + sub, e, G, slots, pol) : V(0);
     for (int off = G >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
     const V v = __shfl_sync(kFull, acc, (lane % rpp) * G);
     if (lane / rpp == p) mine = v;

@@ -121,6 +121,20 @@ inline TileShape tile_shape(int64_t Lc, int lane_target, int tile_rows) {
   return t;
 }
 
+// Stable order of indices by decreasing length (counting sort over the distinct lengths).  A
+// length class is then a contiguous run, and inside it the rows of one tile pass have nearly
+// equal lengths, so a pass issues few entry slots that only some of its rows use.
+inline void order_by_length(const std::vector<int64_t>& len, std::vector<int32_t>& perm) {
+  const int32_t N = (int32_t)len.size();
+  int64_t maxlen = 0;
+  for (int32_t i = 0; i < N; ++i) maxlen = len[i] > maxlen ? len[i] : maxlen;
+  std::vector<int64_t> start(maxlen + 2, 0);
+  for (int32_t i = 0; i < N; ++i) start[maxlen - len[i] + 1]++;
+  for (int64_t L = 1; L <= maxlen + 1; ++L) start[L] += start[L - 1];
+  perm.assign(N, 0);
+  for (int32_t i = 0; i < N; ++i) perm[start[maxlen - len[i]]++] = i;
+}
+
 // Range checks of lp_params (shared by lp_create, lp_set_params and lp_batch_create).
 inline lp_status check_params(const lp_params& p) {
   if (!(p.gamma >= 0.0 && p.gamma <= 1.0)) return fail(LP_ERR_INVALID_ARG, "gamma must be in [0, 1]");
@@ -137,7 +151,7 @@ inline lp_status check_params(const lp_params& p) {
   if (p.trace_cap < 0) return fail(LP_ERR_INVALID_ARG, "trace_cap must be >= 0");
   if (p.unroll < 1 || p.unroll > 64) return fail(LP_ERR_INVALID_ARG, "unroll must be in [1, 64]");
   if (p.lane_target < 0 || p.lane_target > 64) return fail(LP_ERR_INVALID_ARG, "lane_target must be in [0, 64]");
-  if (p.persistent < -1 || p.persistent > 1) return fail(LP_ERR_INVALID_ARG, "persistent must be -1, 0 or 1");
+  if (p.persistent < -1 || p.persistent > 2) return fail(LP_ERR_INVALID_ARG, "persistent must be -1, 0, 1 or 2");
   if (p.precision < 0 || p.precision > 2) return fail(LP_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
   if (!(p.switch_tol >= 0.0)) return fail(LP_ERR_INVALID_ARG, "switch_tol must be >= 0");
   if (p.fp32_patience < 0) return fail(LP_ERR_INVALID_ARG, "fp32_patience must be >= 0");

@@ -112,14 +112,28 @@ __device__ __forceinline__ void store_block_partials(double (&s)[kNumSums], int 
 // operations per row and per column on the FP64-bound path): at a restart, which the control
 // decides once every many iterations, one extra pass over the four vectors sums them
 // (partials in part_pid) before the PID update.
-template <class V>
+// kRefl: the reflected form of the epilogues (gamma = 1 only; step.cuh), which gathers the
+// reflected points xbar and qy instead of xhat and yhat; a restart then also recomputes
+// A xhat_t by one SpMV (the next row phase takes it as A x and as the anchor's product).
+// kOne: launched as a single block, for LPs whose tiles one block's warps cover in a few
+// passes; its phase barriers are block barriers (no grid-wide barrier: on small LPs the
+// iteration is a chain of dependent steps, and the grid barriers were a large part of it).
+template <class V, bool kRefl, bool kOne>
 __global__ void __launch_bounds__(kThreads, sizeof(V) == sizeof(float) ? 4 : 3)
     k_loop(RowArgsT<V> ra, ColArgsT<V> ca, double* part_rows, double* part_cols, double* part_pid, int32_t iters,
            cudaGraphConditionalHandle cond, int32_t use_cond) {
   cg::grid_group grid = cg::this_grid();
+  // barrier between a phase and the totals of its partials: block-wide for a one-block launch
+  // (a block barrier also orders the block's global stores before its later loads)
+  auto phase_sync = [&]() {
+    if constexpr (kOne) __syncthreads();
+    else grid.sync();
+  };
   __shared__ Ctl sc;
   __shared__ RowStep rst;
   __shared__ ColStepT<V> cst;
+  __shared__ RowStepR rstr;
+  __shared__ ColStepR<V> cstr;
   __shared__ Halpern hw;
   __shared__ int rs;
   if (threadIdx.x == 0) sc = *ra.ctl;
@@ -128,33 +142,56 @@ __global__ void __launch_bounds__(kThreads, sizeof(V) == sizeof(float) ? 4 : 3)
   double* trace = blockIdx.x == 0 ? ra.trace : nullptr;
   for (int32_t it = 0; it < iters && !sc.done; ++it) {
     // ---- row phase
-    if (threadIdx.x == 0) rst = row_step(sc);
-    __syncthreads();
-    const RowStep st = rst;
-    const V* __restrict__ xh = (sc.t & 1) ? ra.xh1 : ra.xh0;
     double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for_each_row_pf(ra.bins, ra.rp, ra.ci, ra.val, xh, pol, s,
-                    [&](int i) {
-                      row_prefetch(ra, st, i);
-                      return NoOperands{};
-                    },
-                    [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) {
-                      row_epilogue<V, false>(ra, st, i, v, acc);
-                    });
-    const int nr = st.check ? 5 : 2;
+    int check;
+    if constexpr (kRefl) {
+      if (threadIdx.x == 0) rstr = row_step_r(sc);
+      __syncthreads();
+      const RowStepR st = rstr;
+      check = st.check;
+      if (check) {  // A xhat_t for the primal residual of the KKT test
+        const V* __restrict__ xc = (sc.t & 1) ? ra.xh1 : ra.xh0;
+        double z[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for_each_row(ra.bins, ra.rp, ra.ci, ra.val, xc, pol, z, [&](int i, V v, double (&)[kNumSums]) { ra.ax[i] = v; });
+        phase_sync();
+      }
+      for_each_row_pf(ra.bins, ra.rp, ra.ci, ra.val, ra.xbar, pol, s,
+                      [&](int i) {
+                        row_prefetch_r(ra, st, i);
+                        return NoOperands{};
+                      },
+                      [&](int i, V w, const NoOperands&, double (&acc)[kNumSums]) {
+                        row_epilogue_r(ra, st, i, w, acc);
+                      });
+    } else {
+      if (threadIdx.x == 0) rst = row_step(sc);
+      __syncthreads();
+      const RowStep st = rst;
+      check = st.check;
+      const V* __restrict__ xh = (sc.t & 1) ? ra.xh1 : ra.xh0;
+      for_each_row_pf(ra.bins, ra.rp, ra.ci, ra.val, xh, pol, s,
+                      [&](int i) {
+                        row_prefetch(ra, st, i);
+                        return NoOperands{};
+                      },
+                      [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) {
+                        row_epilogue<V, false>(ra, st, i, v, acc);
+                      });
+    }
+    const int nr = check ? 5 : 2;
     store_block_partials(s, nr, part_rows);
-    grid.sync();
+    phase_sync();
     // the last warp is idle while warps 0..nr-1 add the totals: it computes the next Halpern
     // weights (two FP64 divisions) so that the serial control does not
     if (threadIdx.x == kThreads - 32) hw = halpern_weights(sc.k, sc.gamma);
     double tot[kNumSums];
     block_totals(part_rows, gridDim.x, nr, &ra.bins, tot);
-    if (threadIdx.x == 0) rs = row_decide(sc, tot, st.check, trace, &hw);
+    if (threadIdx.x == 0) rs = row_decide(sc, tot, check, trace, &hw, kRefl ? 1.0 : 2.0);
     __syncthreads();
     if (rs == 1) {  // the same decision in every block
+      const V* __restrict__ xc = (sc.t & 1) ? ca.xh1 : ca.xh0;  // xhat of this iteration
       double q[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
       if (sc.pid_enabled) {
-        const V* __restrict__ xc = (sc.t & 1) ? ca.xh1 : ca.xh0;  // xhat of this iteration
         const int stride = gridDim.x * kThreads;
         for (int j = blockIdx.x * kThreads + threadIdx.x; j < ca.n; j += stride) {
           const V d = xc[j] - ca.x0[j];
@@ -165,32 +202,61 @@ __global__ void __launch_bounds__(kThreads, sizeof(V) == sizeof(float) ? 4 : 3)
           acc_fma(q[1], d, d);
         }
         store_block_partials(q, 2, part_pid);
-        grid.sync();
+        phase_sync();
         block_totals(part_pid, gridDim.x, 2, nullptr, q);
       }
       if (threadIdx.x == 0) row_restart_weight(sc, q[0], q[1]);
+      if constexpr (kRefl) {
+        // A xhat_t, which the next row phase takes as A x and as the new anchor's product (read
+        // there after the column phase's barrier)
+        double z[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for_each_row(ra.bins, ra.rp, ra.ci, ra.val, xc, pol, z,
+                     [&](int i, V v, double (&)[kNumSums]) { ra.axh[i] = v; });
+      }
       __syncthreads();
     }
     if (sc.done) break;
     // ---- column phase
-    if (threadIdx.x == 0) cst = col_step(sc, ca);
-    __syncthreads();
-    const ColStepT<V> cs = cst;
     double s2[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for_each_row_pf(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, s2,
-                    [&](int j) {
-                      col_prefetch(ca, cs, j);
-                      return NoOperands{};
-                    },
-                    [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) {
-                      col_epilogue<V, false>(ca, cs, j, u, acc);
-                    });
-    const int nc = cs.check ? 5 : 1;
+    if constexpr (kRefl) {
+      if (threadIdx.x == 0) cstr = col_step_r(sc, ca);
+      __syncthreads();
+      const ColStepR<V> cs = cstr;
+      check = cs.check;
+      if (check && !cs.restart) {  // A^T yhat_t for the dual residual of the KKT test
+        double z[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for_each_row(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, z, [&](int j, V u, double (&)[kNumSums]) { ca.aty[j] = u; });
+        phase_sync();
+      }
+      const V* __restrict__ gy = cs.restart ? ca.yh : ca.qy;
+      for_each_row_pf(ca.bins, ca.rp, ca.ci, ca.val, gy, pol, s2,
+                      [&](int j) {
+                        col_prefetch_r(ca, cs, j);
+                        return NoOperands{};
+                      },
+                      [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) {
+                        col_epilogue_r(ca, cs, j, u, acc);
+                      });
+    } else {
+      if (threadIdx.x == 0) cst = col_step(sc, ca);
+      __syncthreads();
+      const ColStepT<V> cs = cst;
+      check = cs.check;
+      for_each_row_pf(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, s2,
+                      [&](int j) {
+                        col_prefetch(ca, cs, j);
+                        return NoOperands{};
+                      },
+                      [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) {
+                        col_epilogue<V, false>(ca, cs, j, u, acc);
+                      });
+    }
+    const int nc = check ? 5 : 1;
     store_block_partials(s2, nc, part_cols);
-    grid.sync();
+    phase_sync();
     double tot2[kNumSums];
     block_totals(part_cols, gridDim.x, nc, &ca.bins, tot2);
-    if (threadIdx.x == 0) col_control(sc, tot2, cs.check);
+    if (threadIdx.x == 0) col_control(sc, tot2, check);
     __syncthreads();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -219,13 +285,14 @@ template <class V>
 __global__ void __launch_bounds__(kThreads) k_init_cols(int32_t n, const V* __restrict__ c,
                                                         const V* __restrict__ lv,
                                                         const V* __restrict__ uv, V* xh0, V* x,
-                                                        V* x0, V* aty, V* aty0, Ctl* ctl,
+                                                        V* x0, V* aty, V* aty0, V* xbar, Ctl* ctl,
                                                         double* partials) {
   const V tau = (V)ctl->tau;
   double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     const V xn = clampd(-tau * c[j], lv[j], uv[j]);
     xh0[j] = xn;
+    if (xbar) xbar[j] = V(2) * xn;  // 2 xhat_0 - x_0 with x_0 = 0
     x[j] = V(0);
     x0[j] = V(0);
     aty[j] = V(0);
@@ -301,8 +368,8 @@ __global__ void __launch_bounds__(kThreads) k_warm_cols(int32_t n, const double*
                                                         const double* __restrict__ uv, double* xh0,
                                                         double* xh1, const double* __restrict__ x,
                                                         const double* __restrict__ aty,
-                                                        double* __restrict__ aty0, Ctl* ctl,
-                                                        double* partials) {
+                                                        double* __restrict__ aty0, double* xbar,
+                                                        Ctl* ctl, double* partials) {
   if (ctl->done) return;  // the FP32 phase ended the solve (NUMERICAL)
   const double tau = ctl->tau;
   double* xh = (ctl->t & 1) ? xh1 : xh0;
@@ -311,6 +378,7 @@ __global__ void __launch_bounds__(kThreads) k_warm_cols(int32_t n, const double*
     const double xj = x[j];
     const double xn = clampd(fma(-tau, c[j] - aty[j], xj), lv[j], uv[j]);
     xh[j] = xn;
+    if (xbar) xbar[j] = fma(2.0, xn, -xj);
     aty0[j] = aty[j];
     const double d = xj - xn;
     s[0] = fma(d, d, s[0]);
@@ -363,7 +431,10 @@ IterKernels<V> iter_kernels() {
   IterKernels<V> k;
   k.rows = k1_rows<V>;
   k.cols = k2_cols<V>;
-  k.loop = k_loop<V>;
+  k.loop = k_loop<V, false, false>;
+  k.loop_refl = k_loop<V, true, false>;
+  k.loop_one = k_loop<V, false, true>;
+  k.loop_refl_one = k_loop<V, true, true>;
   k.init_cols = k_init_cols<V>;
   k.init_rows = k_init_rows<V>;
   return k;

@@ -19,6 +19,11 @@ struct RowArgsT {
   V *y, *y0, *yh, *ax, *ax0, *axh;
   const V *lc, *uc, *inv_dr;
   V *yb0, *yb1;  // FP32 stall guard: yhat at check iterations, two slots (null: guard off)
+  // reflected form of the loop kernel (gamma = 1): qy = 2 yhat - y (the reflected dual point,
+  // gathered by the column phase), w = A xbar of the last row phase, xbar = 2 xhat - x (the
+  // gathered primal point)
+  V *qy, *w;
+  const V* xbar;
   Ctl* ctl;
   double* partials;
   double* trace;
@@ -36,6 +41,10 @@ struct ColArgsT {
   V *x, *x0, *aty, *aty0;
   const V *c, *lv, *uv, *inv_dc;
   V *xb0, *xb1;  // FP32 stall guard: xhat at check iterations, two slots (null: guard off)
+  // reflected form of the loop kernel: xbar = 2 xhat - x (written here, gathered by the row
+  // phase), qy = 2 yhat - y (gathered here)
+  V* xbar;
+  const V* qy;
   Ctl* ctl;
   double* partials;
   BinTable bins;
@@ -60,7 +69,14 @@ struct IterKernels {
   void (*rows)(RowArgsT<V>);
   void (*cols)(ColArgsT<V>);
   void (*loop)(RowArgsT<V>, ColArgsT<V>, double*, double*, double*, int32_t, cudaGraphConditionalHandle, int32_t);
-  void (*init_cols)(int32_t, const V*, const V*, const V*, V*, V*, V*, V*, V*, Ctl*, double*);
+  // the loop kernel in the reflected form (gamma = 1 only), and both forms as one-block launches
+  void (*loop_refl)(RowArgsT<V>, ColArgsT<V>, double*, double*, double*, int32_t, cudaGraphConditionalHandle,
+                    int32_t);
+  void (*loop_one)(RowArgsT<V>, ColArgsT<V>, double*, double*, double*, int32_t, cudaGraphConditionalHandle,
+                   int32_t);
+  void (*loop_refl_one)(RowArgsT<V>, ColArgsT<V>, double*, double*, double*, int32_t,
+                        cudaGraphConditionalHandle, int32_t);
+  void (*init_cols)(int32_t, const V*, const V*, const V*, V*, V*, V*, V*, V*, V*, Ctl*, double*);
   void (*init_rows)(int32_t, V*, V*, V*, V*, V*, V*);
 };
 template <class V>
@@ -81,7 +97,7 @@ __global__ void k_switch_vectors(int32_t n, int32_t m, Ctl* ctl, const float* xh
                                  int32_t fp32_only);
 __global__ void k_warm_cols(int32_t n, const double* c, const double* lv, const double* uv,
                             double* xh0, double* xh1, const double* x, const double* aty,
-                            double* aty0, Ctl* ctl, double* partials);
+                            double* aty0, double* xbar, Ctl* ctl, double* partials);
 
 // setup.cu
 __global__ void k_row_factor(int32_t rows, const int32_t* rp, const double* val, int32_t kind,

@@ -45,7 +45,11 @@ struct lp_solver {
   BinTable binsA{}, binsT{};
   int gridA = 1, gridT = 1, gridV = 1, gridL = 1, gridL32 = 1, max_grid = 1;
   bool loop_active = false;  // the graph body is the cooperative loop kernel
+  bool refl = false;         // the loop kernel runs in the reflected form (gamma = 1)
+  bool one_block = false;    // the loop kernel runs as one block (persistent 2, or small LPs)
+  bool one_small = false;    // each phase has at most kOneBlockTasks tiles
   bool loop_fits = false;    // both phases' grids fit on the device at once
+  int tile_rows_used = 1;    // rows per tile of the bins (lp_params.tile_rows, or the automatic choice)
   // device storage
   int32_t *rpA = nullptr, *ciA = nullptr, *rpT = nullptr, *ciT = nullptr;
   double *valA = nullptr, *valT = nullptr;
@@ -54,6 +58,8 @@ struct lp_solver {
   double *lc = nullptr, *uc = nullptr, *inv_dr = nullptr, *dr = nullptr;
   double *x = nullptr, *x0 = nullptr, *xh0 = nullptr, *xh1 = nullptr, *aty = nullptr, *aty0 = nullptr;
   double *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
+  // reflected form of the loop kernel (gamma = 1): xbar = 2 xhat - x, qy = 2 yhat - y, w = A xbar
+  double *xbar = nullptr, *qy = nullptr, *w = nullptr;
   // FP32 phase of the mixed-precision solve (allocated when precision != 0)
   struct F32 {
     float *valA = nullptr, *valT = nullptr;
@@ -62,6 +68,7 @@ struct lp_solver {
     float *lc = nullptr, *uc = nullptr, *inv_dr = nullptr;
     float *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
     float *xb0 = nullptr, *xb1 = nullptr, *yb0 = nullptr, *yb1 = nullptr;  // stall guard's slots
+    float *xbar = nullptr, *qy = nullptr, *w = nullptr;  // reflected form of the loop kernel
   } f32;
   cudaGraph_t graph32 = nullptr;
   cudaGraphExec_t exec32 = nullptr;
@@ -109,6 +116,10 @@ struct lp_solver {
 
 namespace {
 
+// Tiles per phase up to which the automatic choice runs the loop kernel as one block (4 per
+// warp of the block).
+constexpr int64_t kOneBlockTasks = 4 * kWarps;
+
 // Schedule over rows already sorted by decreasing length class.  The leading rows longer than
 // kLongRowMin become chunk tasks of kChunkNnz entries.  Each remaining length class becomes a
 // bin of tiles shaped by tile_shape: G lanes per row (at most lane_target entries per lane and
@@ -152,6 +163,7 @@ void fill_args(const lp_solver* h, RowArgs& ra, ColArgs& ca) {
   ra.xh0 = h->xh0; ra.xh1 = h->xh1;
   ra.y = h->y; ra.y0 = h->y0; ra.yh = h->yh; ra.ax = h->ax; ra.ax0 = h->ax0; ra.axh = h->axh;
   ra.lc = h->lc; ra.uc = h->uc; ra.inv_dr = h->inv_dr;
+  ra.qy = h->qy; ra.w = h->w; ra.xbar = h->xbar;
   ra.ctl = h->ctl; ra.partials = h->partials; ra.trace = h->trace_cap > 0 ? h->trace : nullptr;
   ra.bins = h->binsA;
   ra.m = h->m;
@@ -160,6 +172,7 @@ void fill_args(const lp_solver* h, RowArgs& ra, ColArgs& ca) {
   ca.xh0 = h->xh0; ca.xh1 = h->xh1;
   ca.x = h->x; ca.x0 = h->x0; ca.aty = h->aty; ca.aty0 = h->aty0;
   ca.c = h->c; ca.lv = h->lv; ca.uv = h->uv; ca.inv_dc = h->inv_dc;
+  ca.xbar = h->xbar; ca.qy = h->qy;
   ca.ctl = h->ctl; ca.partials = h->partials; ca.bins = h->binsT;
   ca.n = h->n;
 }
@@ -172,6 +185,7 @@ void fill_args(const lp_solver* h, RowArgsT<float>& ra, ColArgsT<float>& ca) {
   ra.y = f.y; ra.y0 = f.y0; ra.yh = f.yh; ra.ax = f.ax; ra.ax0 = f.ax0; ra.axh = f.axh;
   ra.lc = f.lc; ra.uc = f.uc; ra.inv_dr = f.inv_dr;
   ra.yb0 = f.yb0; ra.yb1 = f.yb1;
+  ra.qy = f.qy; ra.w = f.w; ra.xbar = f.xbar;
   ra.ctl = h->ctl; ra.partials = h->partials; ra.trace = h->trace_cap > 0 ? h->trace : nullptr;
   ra.bins = h->binsA;
   ra.m = h->m;
@@ -181,6 +195,7 @@ void fill_args(const lp_solver* h, RowArgsT<float>& ra, ColArgsT<float>& ca) {
   ca.x = f.x; ca.x0 = f.x0; ca.aty = f.aty; ca.aty0 = f.aty0;
   ca.c = f.c; ca.lv = f.lv; ca.uv = f.uv; ca.inv_dc = f.inv_dc;
   ca.xb0 = f.xb0; ca.xb1 = f.xb1;
+  ca.xbar = f.xbar; ca.qy = f.qy;
   ca.ctl = h->ctl; ca.partials = h->partials; ca.bins = h->binsT;
   ca.n = h->n;
 }
@@ -189,7 +204,7 @@ template <class V>
 cudaError_t launch_loop(const lp_solver* h, const RowArgsT<V>& ra, const ColArgsT<V>& ca, int32_t iters,
                         cudaGraphConditionalHandle cond, int32_t use_cond, cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)(sizeof(V) == sizeof(float) ? h->gridL32 : h->gridL));
+  cfg.gridDim = dim3(h->one_block ? 1u : (unsigned)(sizeof(V) == sizeof(float) ? h->gridL32 : h->gridL));
   cfg.blockDim = dim3((unsigned)kThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
@@ -198,8 +213,9 @@ cudaError_t launch_loop(const lp_solver* h, const RowArgsT<V>& ra, const ColArgs
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, iter_kernels<V>().loop, ra, ca, h->partials, h->partials2, h->partials3, iters,
-                            cond, use_cond);
+  const IterKernels<V> k = iter_kernels<V>();
+  auto kern = h->one_block ? (h->refl ? k.loop_refl_one : k.loop_one) : (h->refl ? k.loop_refl : k.loop);
+  return cudaLaunchKernelEx(&cfg, kern, ra, ca, h->partials, h->partials2, h->partials3, iters, cond, use_cond);
 }
 
 // Captures the solve loop of one precision: a graph whose conditional while node runs the body
@@ -218,7 +234,7 @@ lp_status build_graph_for(lp_solver* h, cudaGraph_t* graph, cudaGraphExec_t* exe
       cudaGraphDestroy(*graph);
       *graph = nullptr;
     }
-    const bool want = h->prm.persistent == 1 || (h->prm.persistent == -1 && h->loop_fits);
+    const bool want = h->prm.persistent >= 1 || (h->prm.persistent == -1 && (h->loop_fits || h->one_small));
     const bool loop = want && attempt == 0;
     RowArgsT<V> ra{};
     ColArgsT<V> ca{};
@@ -261,6 +277,10 @@ lp_status build_graph_for(lp_solver* h, cudaGraph_t* graph, cudaGraphExec_t* exe
 }
 
 lp_status build_graph(lp_solver* h) {
+  // the reflected form of the loop kernel needs gamma = 1 (2 zhat - z is then both the Halpern
+  // step's reflected point and the extrapolated point of the dual step)
+  h->refl = h->prm.gamma == 1.0;
+  h->one_block = h->prm.persistent == 2 || (h->prm.persistent == -1 && h->one_small);
   lp_status st = build_graph_for<double>(h, &h->graph, &h->exec, &h->loop_active);
   if (st != LP_OK) return st;
   if (h->prm.precision != 0) {
@@ -355,10 +375,10 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   std::vector<int64_t> rlen(m), clen(n, 0);
   for (int32_t i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
   for (int64_t p = 0; p < nnz; ++p) clen[ci[p]]++;
-  order_by_class(rlen, h->row_perm);
+  order_by_length(rlen, h->row_perm);
   {
-    // columns grouped by length class like the rows, and inside a class in the order the
-    // permuted rows first reference them (unreferenced columns last): the entries of one row
+    // columns ordered by decreasing length like the rows, and among equal lengths in the order
+    // the permuted rows first reference them (unreferenced columns last): the entries of one row
     // tile then gather nearby columns, fewer L2 sectors per tile (multicommodity FP64 iteration
     // 286 -> 276 us)
     std::vector<int32_t> seq;
@@ -374,15 +394,12 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
     }
     for (int32_t j = 0; j < n; ++j)
       if (!seen[j]) seq.push_back(j);
-    std::vector<int64_t> count(33, 0), start(33, 0);
-    for (int32_t j = 0; j < n; ++j) count[length_class(clen[j])]++;
-    int64_t acc = 0;
-    for (int c = 32; c >= 0; --c) {
-      start[c] = acc;
-      acc += count[c];
-    }
+    std::vector<int64_t> seq_len(n);
+    for (int32_t q = 0; q < n; ++q) seq_len[q] = clen[seq[q]];
+    std::vector<int32_t> by_len;
+    order_by_length(seq_len, by_len);  // stable: first-reference order among equal lengths
     h->col_perm.assign(n, 0);
-    for (int32_t q = 0; q < n; ++q) h->col_perm[start[length_class(clen[seq[q]])]++] = seq[q];
+    for (int32_t q = 0; q < n; ++q) h->col_perm[q] = seq[by_len[q]];
   }
   std::vector<int32_t> col_inv(n);
   for (int32_t j = 0; j < n; ++j) col_inv[h->col_perm[j]] = j;
@@ -413,8 +430,19 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
     }
   std::vector<int4> chunksA, chunksT;
   const int lt = h->prm.lane_target > 0 ? h->prm.lane_target : 8;  // automatic: 8
-  h->binsA = make_bins(rpA, lt, h->prm.tile_rows > 0 ? h->prm.tile_rows : 1, chunksA);
-  h->binsT = make_bins(rpT, lt, h->prm.tile_rows > 0 ? h->prm.tile_rows : 1, chunksT);
+  int tr = h->prm.tile_rows;
+  if (tr == 0) {
+    // automatic: 32-row tiles (every row epilogue instruction runs in 32 lanes, where one-pass
+    // tiles of rows with G > 1 lanes use 32 / G) when both matrices still give every resident
+    // warp of the loop kernel (3 blocks of kWarps per SM) at least 8 tiles; one-pass tiles
+    // otherwise (latency-bound sizes want many short tasks)
+    const BinTable a32 = make_bins(rpA, lt, 32, chunksA), t32 = make_bins(rpT, lt, 32, chunksT);
+    const int64_t warps = (int64_t)h->num_sms * 3 * kWarps;
+    tr = (a32.ntasks + a32.nchunks >= 8 * warps && t32.ntasks + t32.nchunks >= 8 * warps) ? 32 : 1;
+  }
+  h->tile_rows_used = tr;
+  h->binsA = make_bins(rpA, lt, tr, chunksA);
+  h->binsT = make_bins(rpT, lt, tr, chunksT);
 
   int occA = 0, occT = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, iter_kernels<double>().rows, kThreads, 0));
@@ -428,6 +456,8 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   if (occL < 1) occL = 1;
   h->gridL = h->gridA > h->gridT ? h->gridA : h->gridT;
   h->loop_fits = h->gridL <= occL * h->num_sms;
+  h->one_small = (int64_t)h->binsA.ntasks + h->binsA.nchunks <= kOneBlockTasks &&
+                 (int64_t)h->binsT.ntasks + h->binsT.nchunks <= kOneBlockTasks;
   if (h->gridL > occL * h->num_sms) h->gridL = occL * h->num_sms;  // all blocks co-resident
   if (h->prm.precision != 0) {
     // the FP32 loop kernel has fewer registers (4 blocks per SM): its own grid, sized the same way
@@ -449,9 +479,10 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   CK(h->alloc(&h->rpT, n + 1)); CK(h->alloc(&h->ciT, nnz)); CK(h->alloc(&h->valT, nnz));
   CK(h->alloc(&h->d_row_perm, m)); CK(h->alloc(&h->d_col_perm, n));
   for (double** p : {&h->c, &h->lv, &h->uv, &h->inv_dc, &h->dc, &h->x, &h->x0, &h->xh0, &h->xh1,
-                     &h->aty, &h->aty0})
+                     &h->aty, &h->aty0, &h->xbar})
     CK(h->alloc(p, n));
-  for (double** p : {&h->lc, &h->uc, &h->inv_dr, &h->dr, &h->y, &h->y0, &h->yh, &h->ax, &h->ax0, &h->axh})
+  for (double** p : {&h->lc, &h->uc, &h->inv_dr, &h->dr, &h->y, &h->y0, &h->yh, &h->ax, &h->ax0, &h->axh,
+                     &h->qy, &h->w})
     CK(h->alloc(p, m));
   {
     size_t ob = (size_t)(n > m ? n : m) + 1;
@@ -538,9 +569,10 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
     auto& f = h->f32;
     CK(h->alloc(&f.valA, nnz)); CK(h->alloc(&f.valT, nnz));
     for (float** q : {&f.c, &f.lv, &f.uv, &f.inv_dc, &f.x, &f.x0, &f.xh0, &f.xh1, &f.aty, &f.aty0,
-                      &f.xb0, &f.xb1})
+                      &f.xb0, &f.xb1, &f.xbar})
       CK(h->alloc(q, n));
-    for (float** q : {&f.lc, &f.uc, &f.inv_dr, &f.y, &f.y0, &f.yh, &f.ax, &f.ax0, &f.axh, &f.yb0, &f.yb1})
+    for (float** q : {&f.lc, &f.uc, &f.inv_dr, &f.y, &f.y0, &f.yh, &f.ax, &f.ax0, &f.axh, &f.yb0, &f.yb1,
+                      &f.qy, &f.w})
       CK(h->alloc(q, m));
     const int g = grid_for(nnz > 0 ? nnz : 1, 256, 8 * h->num_sms);
     k_to_float<<<g, 256, 0, s>>>(nnz, h->valA, f.valA);
@@ -687,7 +719,9 @@ lp_status lp_set_params(lp_handle h, const lp_params* p) {
     if (h->trace_cap > 0) CK(h->alloc(&h->trace, (size_t)h->trace_cap * 4));
     return build_graph(h);
   }
-  if (h->prm.unroll != h->graph_unroll || p->persistent != old.persistent) return build_graph(h);
+  if (h->prm.unroll != h->graph_unroll || p->persistent != old.persistent ||
+      (p->gamma == 1.0) != (old.gamma == 1.0))
+    return build_graph(h);
   return LP_OK;
 }
 
@@ -735,6 +769,7 @@ lp_status enqueue_start(lp_solver* h, double tol, int64_t max_iter, cudaStream_t
   fill_args(h, ra, ca);
   iter_kernels<V>().init_rows<<<h->gridV, 256, 0, s>>>(h->m, ra.y, ra.y0, ra.yh, ra.ax, ra.ax0, ra.axh);
   iter_kernels<V>().init_cols<<<h->gridV, kThreads, 0, s>>>(h->n, ca.c, ca.lv, ca.uv, ca.xh0, ca.x, ca.x0, ca.aty, ca.aty0,
+                                               ca.xbar,
                                                h->ctl, h->partials);
   CK(cudaGetLastError());
   return LP_OK;
@@ -750,7 +785,7 @@ lp_status enqueue_switch(lp_solver* h, double tol, int64_t max_iter, cudaStream_
   k_switch_ctl<<<1, 1, 0, s>>>(h->ctl, tol, max_iter);
   k_spmv<<<h->gridA, kThreads, 0, s>>>(h->rpA, h->ciA, h->valA, h->x, h->axh, h->binsA);
   k_spmv<<<h->gridT, kThreads, 0, s>>>(h->rpT, h->ciT, h->valT, h->yh, h->aty, h->binsT);
-  k_warm_cols<<<h->gridV, kThreads, 0, s>>>(h->n, h->c, h->lv, h->uv, h->xh0, h->xh1, h->x, h->aty, h->aty0,
+  k_warm_cols<<<h->gridV, kThreads, 0, s>>>(h->n, h->c, h->lv, h->uv, h->xh0, h->xh1, h->x, h->aty, h->aty0, h->xbar,
                                             h->ctl, h->partials);
   CK(cudaGetLastError());
   return LP_OK;
@@ -844,7 +879,7 @@ lp_status lp_get_info(lp_handle h, double* out9) {
   out7[4] = (double)h->pw_iters;
   out7[5] = ctl.kkt[4];
   out7[6] = ctl.kkt[5];
-  out8[7] = h->loop_active ? 1.0 : 0.0;
+  out8[7] = h->loop_active ? (h->one_block ? 2.0 : 1.0) : 0.0;
   out9[8] = h->prm.precision == 1 ? (double)ctl.iters32 : (h->prm.precision == 2 ? (double)ctl.iters : 0.0);
   return LP_OK;
 }

@@ -192,11 +192,14 @@ __device__ __forceinline__ Halpern halpern_weights(int64_t k, double gamma) {
 // row_decide does all of it but the new primal weight of a restart, and returns the restart flag
 // (1), 0, or -1 once the solve has ended (NUMERICAL); row_restart_weight then applies the PID
 // update (Section 3) from the squared norms |xhat - x0|^2 and |yhat - y0|^2 of the epoch.
+// `cross` scales the summed cross term tot[1]: 2 when it sums (y - yhat)(A x - A xhat) (the
+// plain epilogues), 1 when it sums (y - yhat)(A x - A xbar), which is twice that (the reflected
+// form, xbar = 2 xhat - x).
 __device__ __forceinline__ int row_decide(Ctl& c, const double (&tot)[kNumSums], bool check, double* trace,
-                                          const Halpern* next = nullptr) {
+                                          const Halpern* next = nullptr, double cross = 2.0) {
   const int64_t t = c.t;
   const double om = c.omega;
-  const double r2 = fma(c.w_over_eta, c.sxx, fma(c.inv_eta_w, tot[0], 2.0 * tot[1]));
+  const double r2 = fma(c.w_over_eta, c.sxx, fma(c.inv_eta_w, tot[0], cross * tot[1]));
   const double r = sqrt(r2 > 0.0 ? r2 : 0.0);
   const int64_t k = c.k;
   if (k == 0) c.r0 = r;
@@ -365,6 +368,178 @@ __device__ __forceinline__ void col_prefetch(const ColArgsT<V>& a, const ColStep
   prefetch_l1(a.c + j);
   prefetch_l1(a.lv + j);
   prefetch_l1(a.uv + j);
+}
+
+// ------------------------------------------------ reflected form (gamma = 1)
+//
+// With gamma = 1 the reflected Halpern step of Section 3 is z' = lam (2 zhat - z) + mu z0,
+// lam = (k+1)/(k+2), mu = 1/(k+2): the reflected point 2 zhat - z is the same xbar = 2 xhat - x
+// that the dual step of eq. (pdhg) evaluates A at.  The loop kernel's reflected form keeps the
+// reflected points instead of the iterates:
+//   row phase t:    gathers xbar_t, so its SpMV gives w_t = A xbar_t directly; the iterate
+//                   y_t = lam qy_{t-1} + mu y0 and A x_t = lam w_{t-1} + mu A x0 (after a
+//                   restart: yhat_{t-1} and A xhat_{t-1}); stores yhat_t, qy_t = 2 yhat_t - y_t
+//                   and w_t;
+//   column phase t: gathers qy_t (after a restart decision: yhat_t), so its SpMV gives
+//                   A^T qy_t and A^T y_{t+1} = lam A^T qy_t + mu A^T y0 directly; the iterate
+//                   x_{t+1} = lam xbar_t + mu x0 (after a restart: xhat_t); stores xhat_{t+1}
+//                   and xbar_{t+1} = 2 xhat_{t+1} - x_{t+1}.
+// Nothing else is carried between iterations, so each side reads and writes three vectors
+// fewer than the plain form and spends fewer FP64 operations per entry (12 per row, 9 per
+// column).  The products the plain form has at hand are computed where they are needed, by an
+// SpMV of their own (the exact products, as in the plain form):
+//   A xhat_t before the row phase of a check iteration (the primal residual; stored in ax);
+//   A^T yhat_t before the column phase of a check iteration that does not restart (the dual
+//     residual; stored in aty; after a restart decision the phase's own SpMV gives it);
+//   A xhat_t at a restart (the next row phase's A x and anchor product; stored in axh).
+// The maintained A x and A^T y of the reflected form carry the Halpern recursion's rounding
+// through an epoch, so averages such as (w_t + A x_t) / 2 would move the KKT test's residuals,
+// which near the tolerance are differences of nearly equal products, by up to 1e-3 relative.
+// The fixed-point residual's cross term is summed as (y - yhat)(A x - w) = 2 (y - yhat) A (x - xhat).
+
+struct RowStepR {
+  int mode;  // 0 Halpern combine, 1 restart, 2 first iteration (state is zero)
+  int check;
+  int cand;
+  double lam, mu, sigma, inv_sigma;
+};
+
+__device__ __forceinline__ RowStepR row_step_r(const Ctl& c) {
+  RowStepR st;
+  st.mode = (c.t == 0) ? 2 : c.restart;
+  st.check = is_check(c, c.t) ? 1 : 0;
+  st.cand = c.cand_slot;
+  st.lam = -c.hb;  // gamma = 1: hb = -lam
+  st.mu = c.he;
+  st.sigma = c.sigma;
+  st.inv_sigma = c.inv_sigma;
+  return st;
+}
+
+template <class V>
+__device__ __forceinline__ void row_prefetch_r(const RowArgsT<V>& a, const RowStepR& st, int i) {
+  if (st.mode == 0) {
+    prefetch_l1(a.qy + i);
+    prefetch_l1(a.y0 + i);
+    prefetch_l1(a.w + i);
+    prefetch_l1(a.ax0 + i);
+  } else if (st.mode == 1) {
+    prefetch_l1(a.yh + i);
+    prefetch_l1(a.axh + i);
+  }
+  prefetch_l1(a.lc + i);
+  prefetch_l1(a.uc + i);
+}
+
+// Row epilogue of the reflected form: wv = A xbar_t of row i.
+template <class V>
+__device__ __forceinline__ void row_epilogue_r(const RowArgsT<V>& a, const RowStepR& st, int i, V wv,
+                                               double (&acc)[kNumSums]) {
+  const V sigma = (V)st.sigma, inv_sigma = (V)st.inv_sigma;
+  V yi, axi;
+  if (st.mode == 0) {
+    const V lam = (V)st.lam, mu = (V)st.mu;
+    yi = fmav(lam, a.qy[i], mu * a.y0[i]);
+    axi = fmav(lam, a.w[i], mu * a.ax0[i]);
+  } else if (st.mode == 1) {
+    yi = a.yh[i];
+    axi = a.axh[i];
+    a.y0[i] = yi;
+    a.ax0[i] = axi;
+  } else {
+    yi = V(0);
+    axi = V(0);
+  }
+  const V lo = a.lc[i], hi = a.uc[i];
+  const V sv = fmav(-yi, inv_sigma, wv);
+  const V yn = sigma * (clampd(sv, lo, hi) - sv);
+  const V dy = yi - yn;
+  acc_fma(acc[0], dy, dy);
+  acc_fma(acc[1], dy, axi - wv);
+  if (st.check) {
+    const V v = a.ax[i];  // A xhat_t, by the check iteration's own SpMV
+    const V pr = (v - clampd(v, lo, hi)) * a.inv_dr[i];
+    acc_fma(acc[3], pr, pr);
+    acc[4] += (double)((yn > V(0) ? lo * yn : V(0)) + (yn < V(0) ? hi * yn : V(0)));
+    if (a.yb0) (st.cand ? a.yb1 : a.yb0)[i] = yn;
+  }
+  a.qy[i] = fmav(V(2), yn, -yi);
+  a.yh[i] = yn;
+  a.w[i] = wv;
+}
+
+template <class V>
+struct ColStepR {
+  int restart;
+  int check;  // iteration t is a check iteration
+  int cand;
+  double lam, mu, tau;
+  const V* xc;  // xhat_t
+  V* xn;        // xhat_{t+1}
+};
+
+template <class V>
+__device__ __forceinline__ ColStepR<V> col_step_r(const Ctl& c, const ColArgsT<V>& a) {
+  ColStepR<V> st;
+  st.restart = c.restart;
+  st.check = is_check(c, c.t) ? 1 : 0;
+  st.cand = c.cand_slot;
+  st.lam = -c.hb;
+  st.mu = c.he;
+  st.tau = c.tau;
+  st.xc = (c.t & 1) ? a.xh1 : a.xh0;
+  st.xn = (c.t & 1) ? a.xh0 : a.xh1;
+  return st;
+}
+
+template <class V>
+__device__ __forceinline__ void col_prefetch_r(const ColArgsT<V>& a, const ColStepR<V>& st, int j) {
+  if (st.restart || st.check) prefetch_l1(st.xc + j);
+  if (!st.restart) {
+    prefetch_l1(a.xbar + j);
+    prefetch_l1(a.x0 + j);
+    prefetch_l1(a.aty0 + j);
+  }
+  prefetch_l1(a.c + j);
+  prefetch_l1(a.lv + j);
+  prefetch_l1(a.uv + j);
+}
+
+// Column epilogue of the reflected form: u = A^T qy_t of column j (A^T yhat_t after a restart
+// decision).
+template <class V>
+__device__ __forceinline__ void col_epilogue_r(const ColArgsT<V>& a, const ColStepR<V>& st, int j, V u,
+                                               double (&acc)[kNumSums]) {
+  const V tau = (V)st.tau;
+  V xj, atyj;
+  if (st.restart) {
+    xj = st.xc[j];
+    atyj = u;
+    a.x0[j] = xj;
+    a.aty0[j] = u;
+  } else {
+    const V lam = (V)st.lam, mu = (V)st.mu;
+    xj = fmav(lam, a.xbar[j], mu * a.x0[j]);
+    atyj = fmav(lam, u, mu * a.aty0[j]);
+  }
+  const V cj = a.c[j], lo = a.lv[j], hi = a.uv[j];
+  const V xn = clampd(fmav(-tau, cj - atyj, xj), lo, hi);
+  const V dx = xj - xn;
+  acc_fma(acc[0], dx, dx);
+  if (st.check) {
+    const V xc = st.xc[j];
+    const V atyh = st.restart ? u : a.aty[j];  // A^T yhat_t (the check iteration's own SpMV)
+    acc_fma(acc[2], cj, xc);
+    const V rc = cj - atyh;
+    const bool fl = isfinite(lo), fu = isfinite(hi);
+    const V rr = (fl && fu) ? rc : (fl ? maxv(rc, V(0)) : (fu ? minv(rc, V(0)) : V(0)));
+    const V dd = (rc - rr) * a.inv_dc[j];
+    acc_fma(acc[3], dd, dd);
+    acc[4] += (double)((rr > V(0) ? lo * rr : V(0)) + (rr < V(0) ? hi * rr : V(0)));
+    if (a.xb0) (st.cand ? a.xb1 : a.xb0)[j] = xc;
+  }
+  a.xbar[j] = fmav(V(2), xn, -xj);
+  st.xn[j] = xn;
 }
 
 // Scalar control after the column phase: carries the x-side sums to the next residual, runs

@@ -205,7 +205,8 @@ def test_small_lp_iterates(cuda_device, seed, iters):
                                      dict(check_every=7, unroll=3), dict(lane_target=1), dict(lane_target=16),
                                      dict(persistent=0), dict(persistent=0, check_every=5, unroll=2),
                                      dict(persistent=1, unroll=5), dict(tile_rows=32), dict(tile_rows=4, lane_target=2),
-                                     dict(tile_rows=32, persistent=0)])
+                                     dict(tile_rows=32, persistent=0), dict(persistent=2), dict(persistent=2, gamma=0.5),
+                                     dict(persistent=2, check_every=1, unroll=3), dict(persistent=2, tile_rows=32)])
 def test_variants_iterates(cuda_device, variant):
     compare_fixed(gen.free_and_boxed_mix(3, 300, 450), 400, **variant)
 
@@ -272,7 +273,7 @@ def test_single_iteration_and_degenerate_shapes(cuda_device):
     compare_fixed(gen.ragged_rows(9, 64, 5000), 150)
 
 
-@pytest.mark.parametrize("persistent", [1, 0])
+@pytest.mark.parametrize("persistent", [1, 0, 2])
 def test_deterministic_and_reusable(cuda_device, persistent):
     lp = gen.miplib_like(4, 3000, 6000, 2000)
     with lpx.Solver(lp, persistent=persistent) as s:
@@ -293,6 +294,30 @@ def test_both_drivers_agree(cuda_device):
     assert a["persistent"] and not b["persistent"]
     assert_iterates_close(a["x"], b["x"])
     assert_iterates_close(a["y"], b["y"])
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.5])
+def test_three_drivers_agree_on_a_small_lp(cuda_device, gamma):
+    """The small LP (200 x 500) picks the one-block loop kernel by itself (persistent -1 -> 2,
+    reported as 2 in lp_get_info); the grid-wide loop kernel (1) and one kernel per phase (0)
+    run the same iteration.  With gamma = 1 the loop kernels run the reflected form, the split
+    kernels the plain one."""
+    lp = gen.small_lp(2)
+    eta = oracle_eta(lp)
+    with lpx.Solver(lp, eta=eta, gamma=gamma) as s:
+        auto = s.solve(0.0, 500).result()
+        info = lpx.lp_get_info(s.h)
+    assert info[7] == 2.0
+    runs = {p: gpu_solve(lp, 0.0, 500, eta=eta, gamma=gamma, persistent=p) for p in (0, 1, 2)}
+    o = oracle_solve(lp, 0.0, 500, eta=eta, gamma=gamma, trace=True)
+    tie = first_near_tie(o["trace"])
+    rtol = RTOL_ITER if tie is None else 1e-6
+    if tie is not None:
+        assert tie_is_late(o["trace"], tie), tie
+    for p, g in runs.items():
+        assert_iterates_close(g["x"], o["x"], rtol=rtol)
+        assert_iterates_close(g["y"], o["y"], rtol=rtol)
+    assert np.array_equal(auto["x"], runs[2]["x"]) and np.array_equal(auto["y"], runs[2]["y"])
 
 
 def test_device_inputs_equal_host_inputs(cuda_device):
