@@ -27,6 +27,7 @@ struct Bin {
   int32_t rows_per_tile;  // R: rows per warp task (<= 32)
   int32_t task0;          // index of the bin's first task
   int32_t per_lane;       // most entries a lane reads in one task (ceil(Lc / G))
+  int32_t sliced;         // 1: the bin's tiles are also stored sliced (BinTable::sell_*)
 };
 
 // Rows [0, long_rows) of the permuted order have more than kLongRowMin entries; each is split
@@ -44,6 +45,15 @@ struct BinTable {
   double* part;
   unsigned int* arrivals;
   double* contrib;  // long row r's kNumSums epilogue contributions (added by the last block)
+  // Sliced copy of the one-lane-per-row bins' 32-row tiles: tile task t (counted from the first
+  // tile task) holds P = (sell_off[t + 1] - sell_off[t]) / 32 slots, and entry u of its row L
+  // sits at sell_off[t] + 32 u + L (padding: column index -1), so a warp reads a slot of all 32
+  // rows as one 128-byte line (FP32 values and indices) instead of 32 scattered words.  The
+  // values are those of the matrix in the value type of the kernel that reads them (sell_val
+  // points at doubles for the FP64 kernels, at floats for the FP32 ones).  sell_off NULL: none.
+  const int32_t* sell_off;
+  const int32_t* sell_ci;
+  const void* sell_val;
   Bin bin[kMaxBins];
 };
 
@@ -323,8 +333,12 @@ __device__ __forceinline__ void strided_dot_pair(const int32_t* __restrict__ ci,
 }
 
 // One tile task of a BinTable: its rows, shape, and lane L's row bounds (L < nrows; 0 else).
+// Largest entries per lane for which two tiles run side by side (tile_spmv_pair).
+constexpr int kPairMaxPerLane = 4;
+
 struct TileTask {
   int row0, nrows, lanes, per_lane, b, e;
+  int sliced;  // the tile is read from the sliced copy: b = its first slot, e = its slot count
 };
 
 __device__ __forceinline__ TileTask tile_task(const BinTable& bins, const int32_t* __restrict__ rp, int task,
@@ -335,17 +349,73 @@ __device__ __forceinline__ TileTask tile_task(const BinTable& bins, const int32_
   t.nrows = min(B.rows_per_tile, B.row1 - t.row0);
   t.lanes = B.lanes;
   t.per_lane = B.per_lane;
+  t.sliced = B.sliced && bins.sell_off != nullptr;
   t.b = 0;
   t.e = 0;
-  if (lane < t.nrows) {
+  if (t.sliced) {
+    const int q = task - bins.nchunks;
+    t.b = bins.sell_off[q];
+    t.e = (bins.sell_off[q + 1] - t.b) >> 5;
+  } else if (lane < t.nrows) {
     t.b = rp[t.row0 + lane];
     t.e = rp[t.row0 + lane + 1];
   }
   return t;
 }
 
-// Largest entries per lane for which two tiles run side by side (tile_spmv_pair).
-constexpr int kPairMaxPerLane = 4;
+// Dot products of a sliced tile (TileTask::sliced): lane L returns row L's value.  The lane
+// accumulates its row's entries in entry order, as the CSR tile does, so both give the same
+// bits; every load of a slot is one line for the whole warp.
+template <class V>
+__device__ __forceinline__ V sliced_spmv(const BinTable& bins, const V* __restrict__ xg, const TileTask& a,
+                                         int lane, const LoadPolicy& pol) {
+  const V* __restrict__ sv = static_cast<const V*>(bins.sell_val) + a.b + lane;
+  const int32_t* __restrict__ sc = bins.sell_ci + a.b + lane;
+  return strided_dot_slots<V>(sc, sv, xg, 0, a.e * 32, 32, a.e, pol);
+}
+
+// Two sliced tiles side by side (their loads issued together): lane L returns row L's value of
+// each; each accumulated exactly as sliced_spmv would.
+template <class V>
+__device__ __forceinline__ void sliced_spmv_pair(const BinTable& bins, const V* __restrict__ xg, const TileTask& a,
+                                                 const TileTask& b, int lane, const LoadPolicy& pol, V& va, V& vb) {
+  const V* __restrict__ vals = static_cast<const V*>(bins.sell_val);
+  V acc_a = V(0), acc_b = V(0);
+  const int slots = max(a.e, b.e);
+  for (int u0 = 0; u0 < slots; u0 += kPairMaxPerLane) {
+    V xa[kPairMaxPerLane], xb[kPairMaxPerLane], wa[kPairMaxPerLane], wb[kPairMaxPerLane];
+    int ca[kPairMaxPerLane], cb[kPairMaxPerLane];
+#pragma unroll
+    for (int u = 0; u < kPairMaxPerLane; ++u) {
+      const int ka = a.b + 32 * (u0 + u) + lane, kb = b.b + 32 * (u0 + u) + lane;
+      ca[u] = -1;
+      cb[u] = -1;
+      wa[u] = V(0);
+      wb[u] = V(0);
+      if (u0 + u < a.e) {
+        wa[u] = ld_stream(vals + ka, pol.stream);
+        ca[u] = ld_stream(bins.sell_ci + ka, pol.stream);
+      }
+      if (u0 + u < b.e) {
+        wb[u] = ld_stream(vals + kb, pol.stream);
+        cb[u] = ld_stream(bins.sell_ci + kb, pol.stream);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPairMaxPerLane; ++u) {
+      xa[u] = ca[u] >= 0 ? ld_gather(xg + ca[u], pol.keep) : V(0);
+      xb[u] = cb[u] >= 0 ? ld_gather(xg + cb[u], pol.keep) : V(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kPairMaxPerLane; ++u)
+      if (ca[u] >= 0) acc_a = fma(wa[u], xa[u], acc_a);
+#pragma unroll
+    for (int u = 0; u < kPairMaxPerLane; ++u)
+      if (cb[u] >= 0) acc_b = fma(wb[u], xb[u], acc_b);
+  }
+  va = acc_a;
+  vb = acc_b;
+}
 
 // Two single-pass tiles with the same lanes per row G (nrows * G <= 32 each, per_lane <=
 // kPairMaxPerLane), their SpMVs interleaved: lane L returns row L's value of each (garbage for
@@ -456,7 +526,8 @@ __device__ __forceinline__ void for_each_row_pf(const BinTable& bins, const int3
       const TileTask a = tile_task(bins, rp, task, lane);
       In in{};
       if (lane < a.nrows) in = pre(a.row0 + lane);
-      const V v = tile_spmv_b(ci, val, xg, a.b, a.e, a.nrows, a.lanes, a.per_lane, lane, pol);
+      const V v = a.sliced ? sliced_spmv(bins, xg, a, lane, pol)
+                           : tile_spmv_b(ci, val, xg, a.b, a.e, a.nrows, a.lanes, a.per_lane, lane, pol);
       if (lane < a.nrows) epi(a.row0 + lane, v, in, s);
       continue;
     }
@@ -468,9 +539,17 @@ __device__ __forceinline__ void for_each_row_pf(const BinTable& bins, const int3
     const bool two = task2 < total;
     TileTask b{};
     if (two) b = tile_task(bins, rp, task2, lane);
-    const bool pair = two && a.lanes == b.lanes && a.nrows * a.lanes <= 32 && b.nrows * b.lanes <= 32 &&
-                      a.per_lane <= kPairMaxPerLane && b.per_lane <= kPairMaxPerLane;
-    if (pair) {
+    const bool pair = two && !a.sliced && !b.sliced && a.lanes == b.lanes && a.nrows * a.lanes <= 32 &&
+                      b.nrows * b.lanes <= 32 && a.per_lane <= kPairMaxPerLane && b.per_lane <= kPairMaxPerLane;
+    if (two && a.sliced && b.sliced) {
+      In ia{}, ib{};
+      if (lane < a.nrows) ia = pre(a.row0 + lane);
+      if (lane < b.nrows) ib = pre(b.row0 + lane);
+      V va, vb;
+      sliced_spmv_pair(bins, xg, a, b, lane, pol, va, vb);
+      if (lane < a.nrows) epi(a.row0 + lane, va, ia, s);
+      if (lane < b.nrows) epi(b.row0 + lane, vb, ib, s);
+    } else if (pair) {
       In ia{}, ib{};
       if (lane < a.nrows) ia = pre(a.row0 + lane);
       if (lane < b.nrows) ib = pre(b.row0 + lane);
@@ -482,13 +561,15 @@ __device__ __forceinline__ void for_each_row_pf(const BinTable& bins, const int3
       {
         In in{};
         if (lane < a.nrows) in = pre(a.row0 + lane);
-        const V v = tile_spmv_b(ci, val, xg, a.b, a.e, a.nrows, a.lanes, a.per_lane, lane, pol);
+        const V v = a.sliced ? sliced_spmv(bins, xg, a, lane, pol)
+                             : tile_spmv_b(ci, val, xg, a.b, a.e, a.nrows, a.lanes, a.per_lane, lane, pol);
         if (lane < a.nrows) epi(a.row0 + lane, v, in, s);
       }
       if (two) {
         In in{};
         if (lane < b.nrows) in = pre(b.row0 + lane);
-        const V v = tile_spmv_b(ci, val, xg, b.b, b.e, b.nrows, b.lanes, b.per_lane, lane, pol);
+        const V v = b.sliced ? sliced_spmv(bins, xg, b, lane, pol)
+                             : tile_spmv_b(ci, val, xg, b.b, b.e, b.nrows, b.lanes, b.per_lane, lane, pol);
         if (lane < b.nrows) epi(b.row0 + lane, v, in, s);
       }
     }

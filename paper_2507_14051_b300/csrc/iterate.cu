@@ -105,9 +105,10 @@ __device__ __forceinline__ void store_block_partials(double (&s)[kNumSums], int 
 // identical copy of the scalar state in shared memory: all blocks read the same partials in the
 // same order and run the same control code, so their decisions agree bit for bit and every
 // block leaves the loop at the same barrier.  Block 0 writes the state back, writes the trace,
-// and (if use_cond) sets the device-side loop condition of the enclosing graph.  FP64: 3
-// blocks per SM (80 registers); FP32: 4 (64 registers, no spills), more loads in flight for
-// the memory-bound FP32 phases.
+// and (if use_cond) sets the device-side loop condition of the enclosing graph.  4 blocks per
+// SM (64 registers) in both precisions: more warps keep more loads in flight (FP64 at 3 blocks
+// per SM and 80 registers took 264 us per multicommodity iteration, at 4 with a few spilled
+// registers 250 us).
 // The phases do not accumulate the PID's norms |yhat - y0|^2 and |xhat - x0|^2 (two FP64
 // operations per row and per column on the FP64-bound path): at a restart, which the control
 // decides once every many iterations, one extra pass over the four vectors sums them
@@ -119,7 +120,7 @@ __device__ __forceinline__ void store_block_partials(double (&s)[kNumSums], int 
 // passes; its phase barriers are block barriers (no grid-wide barrier: on small LPs the
 // iteration is a chain of dependent steps, and the grid barriers were a large part of it).
 template <class V, bool kRefl, bool kOne>
-__global__ void __launch_bounds__(kThreads, sizeof(V) == sizeof(float) ? 4 : 3)
+__global__ void __launch_bounds__(kThreads, 4)
     k_loop(RowArgsT<V> ra, ColArgsT<V> ca, double* part_rows, double* part_cols, double* part_pid, int32_t iters,
            cudaGraphConditionalHandle cond, int32_t use_cond) {
   cg::grid_group grid = cg::this_grid();

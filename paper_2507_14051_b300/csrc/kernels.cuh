@@ -108,6 +108,8 @@ __global__ void k_mul_inplace(int32_t len, double* d, const double* f);
 __global__ void k_scale_cols(int32_t n, const double* dc, double* c, double* lv, double* uv,
                              double* inv_dc);
 __global__ void k_scale_rows(int32_t m, const double* dr, double* lc, double* uc, double* inv_dr);
+__global__ void k_sell_gather(int64_t len, const int32_t* src, const int32_t* ci, const double* val,
+                              int32_t* sell_ci, double* sell_val);
 __global__ void k_pw_start(int32_t n, const int32_t* col_perm, uint64_t seed, double* u, PwCtl* pw,
                            double* partials);
 __global__ void k_pw_rows(const int32_t* rp, const int32_t* ci, const double* val, const double* u,

@@ -64,6 +64,18 @@ __global__ void k_mul_inplace(int32_t len, double* __restrict__ d, const double*
     d[i] *= f[i];
 }
 
+// Sliced tile copies (BinTable::sell_*): slot k takes CSR entry src[k], or column -1 and value 0
+// for padding.
+__global__ void k_sell_gather(int64_t len, const int32_t* __restrict__ src, const int32_t* __restrict__ ci,
+                              const double* __restrict__ val, int32_t* __restrict__ sell_ci,
+                              double* __restrict__ sell_val) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < len; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t q = src[k];
+    sell_ci[k] = q >= 0 ? ci[q] : -1;
+    sell_val[k] = q >= 0 ? val[q] : 0.0;
+  }
+}
+
 // Scaled column data: c~ = c d_c, l_v~ = l_v / d_c, u_v~ = u_v / d_c, inv_dc = 1 / d_c.
 __global__ void k_scale_cols(int32_t n, const double* __restrict__ dc, double* c, double* lv,
                              double* uv, double* inv_dc) {

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "lp.h"
@@ -60,6 +61,11 @@ struct lp_solver {
   double *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
   // reflected form of the loop kernel (gamma = 1): xbar = 2 xhat - x, qy = 2 yhat - y, w = A xbar
   double *xbar = nullptr, *qy = nullptr, *w = nullptr;
+  // sliced copies of the one-lane-per-row tiles (BinTable::sell_*) of A and A^T
+  double *sell_valA = nullptr, *sell_valT = nullptr;
+  int32_t *sell_ciA = nullptr, *sell_ciT = nullptr, *sell_offA = nullptr, *sell_offT = nullptr;
+  int32_t *sell_srcA = nullptr, *sell_srcT = nullptr;  // source entry of each slot (-1: padding)
+  int64_t sell_lenA = 0, sell_lenT = 0;
   // FP32 phase of the mixed-precision solve (allocated when precision != 0)
   struct F32 {
     float *valA = nullptr, *valT = nullptr;
@@ -69,6 +75,7 @@ struct lp_solver {
     float *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
     float *xb0 = nullptr, *xb1 = nullptr, *yb0 = nullptr, *yb1 = nullptr;  // stall guard's slots
     float *xbar = nullptr, *qy = nullptr, *w = nullptr;  // reflected form of the loop kernel
+    float *sell_valA = nullptr, *sell_valT = nullptr;      // sliced tiles' values
   } f32;
   cudaGraph_t graph32 = nullptr;
   cudaGraphExec_t exec32 = nullptr;
@@ -157,6 +164,41 @@ BinTable make_bins(const std::vector<int32_t>& rp, int lane_target, int tile_row
   return bt;
 }
 
+// Sliced layout of a bin table's one-lane-per-row bins (32-row tiles; BinTable::sell_*): marks
+// those bins, and returns per tile task (counted from the first tile task) its first slot
+// (off, ntasks + 1 entries) and per slot the CSR entry it holds (src, -1 for padding).  Returns
+// false (and marks nothing) if the slots would not fit 32-bit offsets.
+bool build_sell(const std::vector<int32_t>& rp, BinTable& bt, std::vector<int32_t>& off, std::vector<int32_t>& src) {
+  off.assign((size_t)bt.ntasks + 1, 0);
+  int64_t total = 0;
+  for (int b = 0; b < bt.nbins; ++b) {
+    const Bin& B = bt.bin[b];
+    const bool sl = B.lanes == 1 && B.rows_per_tile == 32;
+    const int32_t ntiles = (B.row1 - B.row0 + B.rows_per_tile - 1) / B.rows_per_tile;
+    for (int32_t t = 0; t < ntiles; ++t) {
+      off[B.task0 + t] = (int32_t)total;
+      if (!sl) continue;
+      const int32_t r0 = B.row0 + t * 32, r1 = r0 + 32 < B.row1 ? r0 + 32 : B.row1;
+      int32_t slots = 0;
+      for (int32_t r = r0; r < r1; ++r) slots = rp[r + 1] - rp[r] > slots ? rp[r + 1] - rp[r] : slots;
+      total += (int64_t)32 * slots;
+      if (total >= (int64_t(1) << 31)) return false;
+    }
+  }
+  off[bt.ntasks] = (int32_t)total;
+  src.assign((size_t)total, -1);
+  for (int b = 0; b < bt.nbins; ++b) {
+    Bin& B = bt.bin[b];
+    if (!(B.lanes == 1 && B.rows_per_tile == 32)) continue;
+    B.sliced = 1;
+    for (int32_t r = B.row0; r < B.row1; ++r) {
+      const int32_t t = B.task0 + (r - B.row0) / 32, L = (r - B.row0) % 32;
+      for (int32_t k = rp[r]; k < rp[r + 1]; ++k) src[(size_t)off[t] + (size_t)32 * (k - rp[r]) + L] = k;
+    }
+  }
+  return true;
+}
+
 void fill_args(const lp_solver* h, RowArgs& ra, ColArgs& ca) {
   ra = RowArgs{};
   ra.rp = h->rpA; ra.ci = h->ciA; ra.val = h->valA;
@@ -188,6 +230,7 @@ void fill_args(const lp_solver* h, RowArgsT<float>& ra, ColArgsT<float>& ca) {
   ra.qy = f.qy; ra.w = f.w; ra.xbar = f.xbar;
   ra.ctl = h->ctl; ra.partials = h->partials; ra.trace = h->trace_cap > 0 ? h->trace : nullptr;
   ra.bins = h->binsA;
+  ra.bins.sell_val = f.sell_valA;
   ra.m = h->m;
   ca = ColArgsT<float>{};
   ca.rp = h->rpT; ca.ci = h->ciT; ca.val = f.valT; ca.yh = f.yh;
@@ -197,6 +240,7 @@ void fill_args(const lp_solver* h, RowArgsT<float>& ra, ColArgsT<float>& ca) {
   ca.xb0 = f.xb0; ca.xb1 = f.xb1;
   ca.xbar = f.xbar; ca.qy = f.qy;
   ca.ctl = h->ctl; ca.partials = h->partials; ca.bins = h->binsT;
+  ca.bins.sell_val = f.sell_valT;
   ca.n = h->n;
 }
 
@@ -443,6 +487,9 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   h->tile_rows_used = tr;
   h->binsA = make_bins(rpA, lt, tr, chunksA);
   h->binsT = make_bins(rpT, lt, tr, chunksT);
+  std::vector<int32_t> sell_offA, sell_offT, sell_srcA, sell_srcT;
+  const bool slA = build_sell(rpA, h->binsA, sell_offA, sell_srcA);
+  const bool slT = build_sell(rpT, h->binsT, sell_offT, sell_srcT);
 
   int occA = 0, occT = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, iter_kernels<double>().rows, kThreads, 0));
@@ -452,9 +499,15 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   h->gridA = grid_for_tasks((int64_t)h->binsA.ntasks + h->binsA.nchunks, h->num_sms, occA * h->num_sms);
   h->gridT = grid_for_tasks((int64_t)h->binsT.ntasks + h->binsT.nchunks, h->num_sms, occT * h->num_sms);
   int occL = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occL, iter_kernels<double>().loop, kThreads, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occL, iter_kernels<double>().loop_refl, kThreads, 0));
   if (occL < 1) occL = 1;
-  h->gridL = h->gridA > h->gridT ? h->gridA : h->gridT;
+  // the loop kernel's grid, sized like the phase kernels' but against its own residency
+  {
+    const int64_t tasks = (int64_t)h->binsA.ntasks + h->binsA.nchunks > (int64_t)h->binsT.ntasks + h->binsT.nchunks
+                              ? (int64_t)h->binsA.ntasks + h->binsA.nchunks
+                              : (int64_t)h->binsT.ntasks + h->binsT.nchunks;
+    h->gridL = grid_for_tasks(tasks, h->num_sms, occL * h->num_sms);
+  }
   h->loop_fits = h->gridL <= occL * h->num_sms;
   h->one_small = (int64_t)h->binsA.ntasks + h->binsA.nchunks <= kOneBlockTasks &&
                  (int64_t)h->binsT.ntasks + h->binsT.nchunks <= kOneBlockTasks;
@@ -515,6 +568,24 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
     bt->contrib = d_contrib;
   }
 
+  // sliced tiles: slot maps now, values and indices gathered after the preconditioning
+  for (auto [ok, bt, offv, srcv, doff, dsrc, dci, dval, len] :
+       {std::make_tuple(slA, &h->binsA, &sell_offA, &sell_srcA, &h->sell_offA, &h->sell_srcA, &h->sell_ciA,
+                        &h->sell_valA, &h->sell_lenA),
+        std::make_tuple(slT, &h->binsT, &sell_offT, &sell_srcT, &h->sell_offT, &h->sell_srcT, &h->sell_ciT,
+                        &h->sell_valT, &h->sell_lenT)}) {
+    *len = ok ? (int64_t)srcv->size() : 0;
+    if (!ok || *len == 0) continue;
+    CK(h->alloc(doff, offv->size()));
+    CK(h->alloc(dsrc, (size_t)*len));
+    CK(h->alloc(dci, (size_t)*len));
+    CK(h->alloc(dval, (size_t)*len));
+    CK(cudaMemcpy(*doff, offv->data(), sizeof(int32_t) * offv->size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(*dsrc, srcv->data(), sizeof(int32_t) * (size_t)*len, cudaMemcpyHostToDevice));
+    bt->sell_off = *doff;
+    bt->sell_ci = *dci;
+    bt->sell_val = *dval;
+  }
   CK(cudaMemcpy(h->rpA, rpA.data(), sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->rpT, rpT.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
   if (nnz > 0) {
@@ -565,6 +636,14 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   if (n > 0) k_scale_cols<<<h->gridV, 256, 0, s>>>(n, h->dc, h->c, h->lv, h->uv, h->inv_dc);
   if (m > 0) k_scale_rows<<<h->gridV, 256, 0, s>>>(m, h->dr, h->lc, h->uc, h->inv_dr);
   CK(cudaGetLastError());
+  // the sliced tiles take the preconditioned entries
+  if (h->sell_lenA > 0)
+    k_sell_gather<<<grid_for(h->sell_lenA, 256, 8 * h->num_sms), 256, 0, s>>>(h->sell_lenA, h->sell_srcA, h->ciA,
+                                                                             h->valA, h->sell_ciA, h->sell_valA);
+  if (h->sell_lenT > 0)
+    k_sell_gather<<<grid_for(h->sell_lenT, 256, 8 * h->num_sms), 256, 0, s>>>(h->sell_lenT, h->sell_srcT, h->ciT,
+                                                                             h->valT, h->sell_ciT, h->sell_valT);
+  CK(cudaGetLastError());
   if (h->prm.precision != 0) {
     auto& f = h->f32;
     CK(h->alloc(&f.valA, nnz)); CK(h->alloc(&f.valT, nnz));
@@ -577,6 +656,14 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
     const int g = grid_for(nnz > 0 ? nnz : 1, 256, 8 * h->num_sms);
     k_to_float<<<g, 256, 0, s>>>(nnz, h->valA, f.valA);
     k_to_float<<<g, 256, 0, s>>>(nnz, h->valT, f.valT);
+    if (h->sell_lenA > 0) {
+      CK(h->alloc(&f.sell_valA, (size_t)h->sell_lenA));
+      k_to_float<<<grid_for(h->sell_lenA, 256, 8 * h->num_sms), 256, 0, s>>>(h->sell_lenA, h->sell_valA, f.sell_valA);
+    }
+    if (h->sell_lenT > 0) {
+      CK(h->alloc(&f.sell_valT, (size_t)h->sell_lenT));
+      k_to_float<<<grid_for(h->sell_lenT, 256, 8 * h->num_sms), 256, 0, s>>>(h->sell_lenT, h->sell_valT, f.sell_valT);
+    }
     for (auto pr : {std::make_pair((const double*)h->c, f.c), std::make_pair((const double*)h->lv, f.lv),
                     std::make_pair((const double*)h->uv, f.uv), std::make_pair((const double*)h->inv_dc, f.inv_dc)})
       k_to_float<<<h->gridV, 256, 0, s>>>(n, pr.first, pr.second);
