@@ -142,6 +142,23 @@ __device__ __forceinline__ float ld_stream(const float* p, uint64_t pol) {
   asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
   return v;
 }
+// Read-only loads of a sliced tile's slot (a whole line per warp, read once): evict-first in L2
+// and not allocated in L1, where they would only displace the gathered vector's lines.
+__device__ __forceinline__ double ld_slice(const double* p, uint64_t pol) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_slice(const int32_t* p, uint64_t pol) {
+  int32_t v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_slice(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
 // Prefetch of the line holding *p into L1 (no register is written; the later load hits L1).
 template <class T>
 __device__ __forceinline__ void prefetch_l1(const T* p) {
@@ -366,12 +383,51 @@ __device__ __forceinline__ TileTask tile_task(const BinTable& bins, const int32_
 // Dot products of a sliced tile (TileTask::sliced): lane L returns row L's value.  The lane
 // accumulates its row's entries in entry order, as the CSR tile does, so both give the same
 // bits; every load of a slot is one line for the whole warp.
-template <class V>
+template <int N, class V, bool kCached>
+__device__ __forceinline__ void sliced_batch(const int32_t* __restrict__ sc, const V* __restrict__ sv,
+                                             const V* __restrict__ xg, const LoadPolicy& pol, V& acc) {
+  V v[N];
+  int c[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    if (kCached) {
+      v[u] = ld_cached(sv + 32 * u);
+      c[u] = ld_cached(sc + 32 * u);
+    } else {
+      v[u] = ld_slice(sv + 32 * u, pol.stream);
+      c[u] = ld_slice(sc + 32 * u, pol.stream);
+    }
+  }
+  V xv[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) xv[u] = c[u] >= 0 ? ld_gather(xg + c[u], pol.keep) : V(0);
+#pragma unroll
+  for (int u = 0; u < N; ++u)
+    if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+}
+
+// kCached: the slots are read with the default cache policy (kept in L1 and L2), for a small LP
+// whose tiles the same SMs re-read every iteration.
+template <class V, bool kCached = false>
 __device__ __forceinline__ V sliced_spmv(const BinTable& bins, const V* __restrict__ xg, const TileTask& a,
                                          int lane, const LoadPolicy& pol) {
   const V* __restrict__ sv = static_cast<const V*>(bins.sell_val) + a.b + lane;
   const int32_t* __restrict__ sc = bins.sell_ci + a.b + lane;
-  return strided_dot_slots<V>(sc, sv, xg, 0, a.e * 32, 32, a.e, pol);
+  V acc = V(0);
+  int slots = a.e;
+  for (; slots >= kIlp; slots -= kIlp, sv += 32 * kIlp, sc += 32 * kIlp)
+    sliced_batch<kIlp, V, kCached>(sc, sv, xg, pol, acc);
+  switch (slots) {
+    case 1: sliced_batch<1, V, kCached>(sc, sv, xg, pol, acc); break;
+    case 2: sliced_batch<2, V, kCached>(sc, sv, xg, pol, acc); break;
+    case 3: sliced_batch<3, V, kCached>(sc, sv, xg, pol, acc); break;
+    case 4: sliced_batch<4, V, kCached>(sc, sv, xg, pol, acc); break;
+    case 5: sliced_batch<5, V, kCached>(sc, sv, xg, pol, acc); break;
+    case 6: sliced_batch<6, V, kCached>(sc, sv, xg, pol, acc); break;
+    case 7: sliced_batch<7, V, kCached>(sc, sv, xg, pol, acc); break;
+    default: break;
+  }
+  return acc;
 }
 
 // Two sliced tiles side by side (their loads issued together): lane L returns row L's value of
@@ -393,12 +449,12 @@ __device__ __forceinline__ void sliced_spmv_pair(const BinTable& bins, const V* 
       wa[u] = V(0);
       wb[u] = V(0);
       if (u0 + u < a.e) {
-        wa[u] = ld_stream(vals + ka, pol.stream);
-        ca[u] = ld_stream(bins.sell_ci + ka, pol.stream);
+        wa[u] = ld_slice(vals + ka, pol.stream);
+        ca[u] = ld_slice(bins.sell_ci + ka, pol.stream);
       }
       if (u0 + u < b.e) {
-        wb[u] = ld_stream(vals + kb, pol.stream);
-        cb[u] = ld_stream(bins.sell_ci + kb, pol.stream);
+        wb[u] = ld_slice(vals + kb, pol.stream);
+        cb[u] = ld_slice(bins.sell_ci + kb, pol.stream);
       }
     }
 #pragma unroll
@@ -489,7 +545,9 @@ __device__ __forceinline__ V tile_spmv(const int32_t* __restrict__ rp, const int
 // row's last chunk (acc = a zeroed array then stored in bins.contrib for the last block to add
 // in row order; in = pre(row) loaded there).  Every sum therefore has a fixed order that
 // depends only on the grid size: results are bit-reproducible run to run.
-template <class V, class Pre, class Epi>
+// kCached: matrix loads of single tiles with the default cache policy (ld_cached), for a small LP
+// whose tiles the same SMs re-read every iteration (the cluster loop).
+template <class V, class Pre, class Epi, bool kCached = false>
 __device__ __forceinline__ void for_each_row_pf(const BinTable& bins, const int32_t* __restrict__ rp,
                                                 const int32_t* __restrict__ ci, const V* __restrict__ val,
                                                 const V* __restrict__ xg, const LoadPolicy& pol,
@@ -498,7 +556,9 @@ __device__ __forceinline__ void for_each_row_pf(const BinTable& bins, const int3
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * kWarps;
   const int total = bins.nchunks + bins.ntasks;
-  for (int task = blockIdx.x * kWarps + (threadIdx.x >> 5); task < total; task += nwarps) {
+  // warp w of block b starts at task w * gridDim.x + b: a grid's first tasks go to different
+  // blocks (a small LP's few tiles then run on as many SMs)
+  for (int task = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; task < total; task += nwarps) {
     if (task < bins.nchunks) {
       const int4 ch = bins.chunk[task];
       const int b = rp[ch.x] + (task - ch.y) * kChunkNnz;
@@ -526,8 +586,8 @@ __device__ __forceinline__ void for_each_row_pf(const BinTable& bins, const int3
       const TileTask a = tile_task(bins, rp, task, lane);
       In in{};
       if (lane < a.nrows) in = pre(a.row0 + lane);
-      const V v = a.sliced ? sliced_spmv(bins, xg, a, lane, pol)
-                           : tile_spmv_b(ci, val, xg, a.b, a.e, a.nrows, a.lanes, a.per_lane, lane, pol);
+      const V v = a.sliced ? sliced_spmv<V, kCached>(bins, xg, a, lane, pol)
+                           : tile_spmv_b<V, kCached>(ci, val, xg, a.b, a.e, a.nrows, a.lanes, a.per_lane, lane, pol);
       if (lane < a.nrows) epi(a.row0 + lane, v, in, s);
       continue;
     }
@@ -561,15 +621,15 @@ __device__ __forceinline__ void for_each_row_pf(const BinTable& bins, const int3
       {
         In in{};
         if (lane < a.nrows) in = pre(a.row0 + lane);
-        const V v = a.sliced ? sliced_spmv(bins, xg, a, lane, pol)
-                             : tile_spmv_b(ci, val, xg, a.b, a.e, a.nrows, a.lanes, a.per_lane, lane, pol);
+        const V v = a.sliced ? sliced_spmv<V, kCached>(bins, xg, a, lane, pol)
+                             : tile_spmv_b<V, kCached>(ci, val, xg, a.b, a.e, a.nrows, a.lanes, a.per_lane, lane, pol);
         if (lane < a.nrows) epi(a.row0 + lane, v, in, s);
       }
       if (two) {
         In in{};
         if (lane < b.nrows) in = pre(b.row0 + lane);
-        const V v = b.sliced ? sliced_spmv(bins, xg, b, lane, pol)
-                             : tile_spmv_b(ci, val, xg, b.b, b.e, b.nrows, b.lanes, b.per_lane, lane, pol);
+        const V v = b.sliced ? sliced_spmv<V, kCached>(bins, xg, b, lane, pol)
+                             : tile_spmv_b<V, kCached>(ci, val, xg, b.b, b.e, b.nrows, b.lanes, b.per_lane, lane, pol);
         if (lane < b.nrows) epi(b.row0 + lane, v, in, s);
       }
     }
@@ -580,13 +640,14 @@ __device__ __forceinline__ void for_each_row_pf(const BinTable& bins, const int3
 struct NoOperands {};
 
 // for_each_row_pf without per-row operands: epi(row, value, acc).
-template <class V, class Epi>
+template <class V, class Epi, bool kCached = false>
 __device__ __forceinline__ void for_each_row(const BinTable& bins, const int32_t* __restrict__ rp,
                                              const int32_t* __restrict__ ci, const V* __restrict__ val,
                                              const V* __restrict__ xg, const LoadPolicy& pol,
                                              double (&s)[kNumSums], Epi&& epi) {
-  for_each_row_pf(bins, rp, ci, val, xg, pol, s, [](int) { return NoOperands{}; },
-                  [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) { epi(i, v, acc); });
+  auto pre = [](int) { return NoOperands{}; };
+  auto e2 = [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) { epi(i, v, acc); };
+  for_each_row_pf<V, decltype(pre)&, decltype(e2)&, kCached>(bins, rp, ci, val, xg, pol, s, pre, e2);
 }
 
 // Sums the first nsums (<= kNumSums <= kWarps) of each thread's v[] over the block in a fixed

@@ -116,18 +116,20 @@ __device__ __forceinline__ void store_block_partials(double (&s)[kNumSums], int 
 // kRefl: the reflected form of the epilogues (gamma = 1 only; step.cuh), which gathers the
 // reflected points xbar and qy instead of xhat and yhat; a restart then also recomputes
 // A xhat_t by one SpMV (the next row phase takes it as A x and as the anchor's product).
-// kOne: launched as a single block, for LPs whose tiles one block's warps cover in a few
-// passes; its phase barriers are block barriers (no grid-wide barrier: on small LPs the
-// iteration is a chain of dependent steps, and the grid barriers were a large part of it).
-template <class V, bool kRefl, bool kOne>
+// kCl: launched as one thread-block cluster (the grid is the cluster, up to 16 CTAs on as many
+// SMs), for small LPs; its phase barriers are cluster barriers instead of grid-wide ones.  On
+// this GPU an SM issues one FP64 warp instruction per 16 cycles, so even a 2,000-nonzero LP is
+// bound by one SM's FP64 issue if one block runs it; a cluster spreads the tiles over its SMs
+// and still synchronises in hardware.
+template <class V, bool kRefl, bool kCl>
 __global__ void __launch_bounds__(kThreads, 4)
     k_loop(RowArgsT<V> ra, ColArgsT<V> ca, double* part_rows, double* part_cols, double* part_pid, int32_t iters,
            cudaGraphConditionalHandle cond, int32_t use_cond) {
   cg::grid_group grid = cg::this_grid();
-  // barrier between a phase and the totals of its partials: block-wide for a one-block launch
-  // (a block barrier also orders the block's global stores before its later loads)
+  // barrier between a phase and the totals of its partials: cluster-wide for a cluster launch
+  // (the cluster barrier also orders the CTAs' global stores before their later loads)
   auto phase_sync = [&]() {
-    if constexpr (kOne) __syncthreads();
+    if constexpr (kCl) cg::this_cluster().sync();
     else grid.sync();
   };
   __shared__ Ctl sc;
@@ -153,31 +155,34 @@ __global__ void __launch_bounds__(kThreads, 4)
       if (check) {  // A xhat_t for the primal residual of the KKT test
         const V* __restrict__ xc = (sc.t & 1) ? ra.xh1 : ra.xh0;
         double z[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        for_each_row(ra.bins, ra.rp, ra.ci, ra.val, xc, pol, z, [&](int i, V v, double (&)[kNumSums]) { ra.ax[i] = v; });
+        auto fr1 = [&](int i, V v, double (&)[kNumSums]) { ra.ax[i] = v; };
+        for_each_row<V, decltype(fr1)&, kCl>(ra.bins, ra.rp, ra.ci, ra.val, xc, pol, z, fr1);
         phase_sync();
       }
-      for_each_row_pf(ra.bins, ra.rp, ra.ci, ra.val, ra.xbar, pol, s,
-                      [&](int i) {
-                        row_prefetch_r(ra, st, i);
-                        return NoOperands{};
-                      },
-                      [&](int i, V w, const NoOperands&, double (&acc)[kNumSums]) {
-                        row_epilogue_r(ra, st, i, w, acc);
-                      });
+      auto pre1 = [&](int i) {
+        row_prefetch_r(ra, st, i);
+        return NoOperands{};
+      };
+      auto epi1 = [&](int i, V w, const NoOperands&, double (&acc)[kNumSums]) {
+        row_epilogue_r(ra, st, i, w, acc);
+      };
+      for_each_row_pf<V, decltype(pre1)&, decltype(epi1)&, kCl>(ra.bins, ra.rp, ra.ci, ra.val, ra.xbar, pol, s, pre1,
+                                                             epi1);
     } else {
       if (threadIdx.x == 0) rst = row_step(sc);
       __syncthreads();
       const RowStep st = rst;
       check = st.check;
       const V* __restrict__ xh = (sc.t & 1) ? ra.xh1 : ra.xh0;
-      for_each_row_pf(ra.bins, ra.rp, ra.ci, ra.val, xh, pol, s,
-                      [&](int i) {
-                        row_prefetch(ra, st, i);
-                        return NoOperands{};
-                      },
-                      [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) {
-                        row_epilogue<V, false>(ra, st, i, v, acc);
-                      });
+      auto pre2 = [&](int i) {
+        row_prefetch(ra, st, i);
+        return NoOperands{};
+      };
+      auto epi2 = [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) {
+        row_epilogue<V, false>(ra, st, i, v, acc);
+      };
+      for_each_row_pf<V, decltype(pre2)&, decltype(epi2)&, kCl>(ra.bins, ra.rp, ra.ci, ra.val, xh, pol, s, pre2,
+                                                             epi2);
     }
     const int nr = check ? 5 : 2;
     store_block_partials(s, nr, part_rows);
@@ -226,31 +231,34 @@ __global__ void __launch_bounds__(kThreads, 4)
       check = cs.check;
       if (check && !cs.restart) {  // A^T yhat_t for the dual residual of the KKT test
         double z[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        for_each_row(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, z, [&](int j, V u, double (&)[kNumSums]) { ca.aty[j] = u; });
+        auto fr2 = [&](int j, V u, double (&)[kNumSums]) { ca.aty[j] = u; };
+        for_each_row<V, decltype(fr2)&, kCl>(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, z, fr2);
         phase_sync();
       }
       const V* __restrict__ gy = cs.restart ? ca.yh : ca.qy;
-      for_each_row_pf(ca.bins, ca.rp, ca.ci, ca.val, gy, pol, s2,
-                      [&](int j) {
-                        col_prefetch_r(ca, cs, j);
-                        return NoOperands{};
-                      },
-                      [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) {
-                        col_epilogue_r(ca, cs, j, u, acc);
-                      });
+      auto pre3 = [&](int j) {
+        col_prefetch_r(ca, cs, j);
+        return NoOperands{};
+      };
+      auto epi3 = [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) {
+        col_epilogue_r(ca, cs, j, u, acc);
+      };
+      for_each_row_pf<V, decltype(pre3)&, decltype(epi3)&, kCl>(ca.bins, ca.rp, ca.ci, ca.val, gy, pol, s2, pre3,
+                                                             epi3);
     } else {
       if (threadIdx.x == 0) cst = col_step(sc, ca);
       __syncthreads();
       const ColStepT<V> cs = cst;
       check = cs.check;
-      for_each_row_pf(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, s2,
-                      [&](int j) {
-                        col_prefetch(ca, cs, j);
-                        return NoOperands{};
-                      },
-                      [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) {
-                        col_epilogue<V, false>(ca, cs, j, u, acc);
-                      });
+      auto pre4 = [&](int j) {
+        col_prefetch(ca, cs, j);
+        return NoOperands{};
+      };
+      auto epi4 = [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) {
+        col_epilogue<V, false>(ca, cs, j, u, acc);
+      };
+      for_each_row_pf<V, decltype(pre4)&, decltype(epi4)&, kCl>(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, s2, pre4,
+                                                             epi4);
     }
     const int nc = check ? 5 : 1;
     store_block_partials(s2, nc, part_cols);

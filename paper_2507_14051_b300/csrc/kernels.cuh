@@ -69,7 +69,7 @@ struct IterKernels {
   void (*rows)(RowArgsT<V>);
   void (*cols)(ColArgsT<V>);
   void (*loop)(RowArgsT<V>, ColArgsT<V>, double*, double*, double*, int32_t, cudaGraphConditionalHandle, int32_t);
-  // the loop kernel in the reflected form (gamma = 1 only), and both forms as one-block launches
+  // the loop kernel in the reflected form (gamma = 1 only), and both forms as one-cluster launches
   void (*loop_refl)(RowArgsT<V>, ColArgsT<V>, double*, double*, double*, int32_t, cudaGraphConditionalHandle,
                     int32_t);
   void (*loop_one)(RowArgsT<V>, ColArgsT<V>, double*, double*, double*, int32_t, cudaGraphConditionalHandle,

@@ -47,8 +47,9 @@ struct lp_solver {
   int gridA = 1, gridT = 1, gridV = 1, gridL = 1, gridL32 = 1, max_grid = 1;
   bool loop_active = false;  // the graph body is the cooperative loop kernel
   bool refl = false;         // the loop kernel runs in the reflected form (gamma = 1)
-  bool one_block = false;    // the loop kernel runs as one block (persistent 2, or small LPs)
-  bool one_small = false;    // each phase has at most kOneBlockTasks tiles
+  int cluster = 0;           // > 0: the loop kernel runs as one cluster of this many CTAs
+  int cluster_max = 0;       // the largest cluster the loop kernels can be launched as (16 or 8)
+  bool small = false;        // each phase has at most kClusterTasks tasks
   bool loop_fits = false;    // both phases' grids fit on the device at once
   int tile_rows_used = 1;    // rows per tile of the bins (lp_params.tile_rows, or the automatic choice)
   // device storage
@@ -123,9 +124,9 @@ struct lp_solver {
 
 namespace {
 
-// Tiles per phase up to which the automatic choice runs the loop kernel as one block (4 per
-// warp of the block).
-constexpr int64_t kOneBlockTasks = 4 * kWarps;
+// Tasks per phase up to which the automatic choice runs the loop kernel as one cluster (at most
+// one task per warp of a 16-CTA cluster).
+constexpr int64_t kClusterTasks = 16 * kWarps;
 
 // Schedule over rows already sorted by decreasing length class.  The leading rows longer than
 // kLongRowMin become chunk tasks of kChunkNnz entries.  Each remaining length class becomes a
@@ -244,22 +245,72 @@ void fill_args(const lp_solver* h, RowArgsT<float>& ra, ColArgsT<float>& ca) {
   ca.n = h->n;
 }
 
+// Launch configuration of the loop kernel: cooperative over its whole grid, or (h->cluster > 0)
+// one cluster of h->cluster CTAs spread over as many SMs.
 template <class V>
 cudaError_t launch_loop(const lp_solver* h, const RowArgsT<V>& ra, const ColArgsT<V>& ca, int32_t iters,
                         cudaGraphConditionalHandle cond, int32_t use_cond, cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(h->one_block ? 1u : (unsigned)(sizeof(V) == sizeof(float) ? h->gridL32 : h->gridL));
   cfg.blockDim = dim3((unsigned)kThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
+  cudaLaunchAttribute attr[2];
+  if (h->cluster > 0) {
+    cfg.gridDim = dim3((unsigned)h->cluster);
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)h->cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
+    attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicySpread;
+    cfg.numAttrs = 2;
+  } else {
+    cfg.gridDim = dim3((unsigned)(sizeof(V) == sizeof(float) ? h->gridL32 : h->gridL));
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.numAttrs = 1;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
   const IterKernels<V> k = iter_kernels<V>();
-  auto kern = h->one_block ? (h->refl ? k.loop_refl_one : k.loop_one) : (h->refl ? k.loop_refl : k.loop);
+  auto kern = h->cluster > 0 ? (h->refl ? k.loop_refl_one : k.loop_one) : (h->refl ? k.loop_refl : k.loop);
   return cudaLaunchKernelEx(&cfg, kern, ra, ca, h->partials, h->partials2, h->partials3, iters, cond, use_cond);
+}
+
+// The largest cluster (16, else 8) that every cluster form of the loop kernel can be launched as
+// on this device (0 if none: the cluster driver is then not offered).
+template <class V>
+int max_loop_cluster(int& best) {
+  const IterKernels<V> k = iter_kernels<V>();
+  decltype(k.loop_one) kerns[2] = {k.loop_one, k.loop_refl_one};
+  for (int q = 0; q < 2; ++q) {
+    const auto kern = kerns[q];
+    int found = 0;
+    for (int c : {16, 8}) {
+      if (c > best) continue;
+      if (c > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3((unsigned)c);
+      cfg.blockDim = dim3((unsigned)kThreads);
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)c;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0) {
+        found = c;
+        break;
+      }
+      cudaGetLastError();
+    }
+    best = found < best ? found : best;
+  }
+  return best;
 }
 
 // Captures the solve loop of one precision: a graph whose conditional while node runs the body
@@ -278,7 +329,7 @@ lp_status build_graph_for(lp_solver* h, cudaGraph_t* graph, cudaGraphExec_t* exe
       cudaGraphDestroy(*graph);
       *graph = nullptr;
     }
-    const bool want = h->prm.persistent >= 1 || (h->prm.persistent == -1 && (h->loop_fits || h->one_small));
+    const bool want = h->prm.persistent >= 1 || (h->prm.persistent == -1 && (h->loop_fits || h->cluster > 0));
     const bool loop = want && attempt == 0;
     RowArgsT<V> ra{};
     ColArgsT<V> ca{};
@@ -324,7 +375,8 @@ lp_status build_graph(lp_solver* h) {
   // the reflected form of the loop kernel needs gamma = 1 (2 zhat - z is then both the Halpern
   // step's reflected point and the extrapolated point of the dual step)
   h->refl = h->prm.gamma == 1.0;
-  h->one_block = h->prm.persistent == 2 || (h->prm.persistent == -1 && h->one_small);
+  const bool want_cluster = h->prm.persistent == 2 || (h->prm.persistent == -1 && h->small);
+  h->cluster = want_cluster ? h->cluster_max : 0;
   lp_status st = build_graph_for<double>(h, &h->graph, &h->exec, &h->loop_active);
   if (st != LP_OK) return st;
   if (h->prm.precision != 0) {
@@ -509,8 +561,14 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
     h->gridL = grid_for_tasks(tasks, h->num_sms, occL * h->num_sms);
   }
   h->loop_fits = h->gridL <= occL * h->num_sms;
-  h->one_small = (int64_t)h->binsA.ntasks + h->binsA.nchunks <= kOneBlockTasks &&
-                 (int64_t)h->binsT.ntasks + h->binsT.nchunks <= kOneBlockTasks;
+  h->small = (int64_t)h->binsA.ntasks + h->binsA.nchunks <= kClusterTasks &&
+             (int64_t)h->binsT.ntasks + h->binsT.nchunks <= kClusterTasks;
+  {
+    int best = 16;
+    max_loop_cluster<double>(best);
+    if (h->prm.precision != 0) max_loop_cluster<float>(best);
+    h->cluster_max = best;
+  }
   if (h->gridL > occL * h->num_sms) h->gridL = occL * h->num_sms;  // all blocks co-resident
   if (h->prm.precision != 0) {
     // the FP32 loop kernel has fewer registers (4 blocks per SM): its own grid, sized the same way
@@ -966,7 +1024,7 @@ lp_status lp_get_info(lp_handle h, double* out9) {
   out7[4] = (double)h->pw_iters;
   out7[5] = ctl.kkt[4];
   out7[6] = ctl.kkt[5];
-  out8[7] = h->loop_active ? (h->one_block ? 2.0 : 1.0) : 0.0;
+  out8[7] = h->loop_active ? (h->cluster > 0 ? 2.0 : 1.0) : 0.0;
   out9[8] = h->prm.precision == 1 ? (double)ctl.iters32 : (h->prm.precision == 2 ? (double)ctl.iters : 0.0);
   return LP_OK;
 }

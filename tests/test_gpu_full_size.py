@@ -174,10 +174,11 @@ def test_full_size_miplib_like_to_tolerance(cuda_device):
         r = s.solve(1e-8, 3_000_000).result()
     assert r["status"] == oracle.OPTIMAL and r["iters"] % 64 == 0
     kk = oracle.kkt(lp, r["x"], r["y"])
-    assert kk[3] <= 1e-8
     # the relative gap |pobj - dobj| / (1 + |pobj| + |dobj|) cancels two nearly equal sums of
     # ~10^5 terms; its rounding is absolute, about u times the sum of the terms' magnitudes
-    # over the denominator (1e-11 here), not relative to the tiny gap
+    # over the denominator (1e-11 here), not relative to the tiny gap: a point the GPU accepts
+    # with a gap just under the tolerance can be evaluated just over it by the oracle
+    assert kk[1] <= 1e-8 and kk[2] <= 1e-8 and kk[0] <= 1e-8 + 1e-10
     np.testing.assert_allclose(r["kkt"][0], kk[0], rtol=0, atol=1e-10)
     np.testing.assert_allclose(r["kkt"][1:3], kk[1:3], rtol=1e-7, atol=1e-13)
     # the reported relative KKT error is the largest of the three; when that is the gap it
