@@ -1071,10 +1071,12 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
     const int gc = grid_for(sn * 32, 256, 8 * h->num_sms);
     for (int pass = 0; pass < passes; ++pass) {
       const int kind = (pass == h->prm.ruiz_iters) ? 1 : 0;
-      if (sm > 0) k_row_factor<<<gr, 256, 0, s>>>((int32_t)sm, h->rpA, h->valA, kind, 2.0 - h->prm.pc_alpha, fr);
-      if (sn > 0) k_row_factor<<<gc, 256, 0, s>>>((int32_t)sn, h->rpT, h->valT, kind, h->prm.pc_alpha, fc);
-      if (sm > 0) k_apply_factors<<<gr, 256, 0, s>>>((int32_t)sm, h->rpA, h->ciA, h->valA, fr, fc, 0);
-      if (sn > 0) k_apply_factors<<<gc, 256, 0, s>>>((int32_t)sn, h->rpT, h->ciT, h->valT, fr, fc, 1);
+      // the batch's rows are not ordered by length across instances: a warp per row throughout
+      if (sm > 0)
+        k_row_factor<<<gr, 256, 0, s>>>((int32_t)sm, (int32_t)sm, h->rpA, h->valA, kind, 2.0 - h->prm.pc_alpha, fr);
+      if (sn > 0) k_row_factor<<<gc, 256, 0, s>>>((int32_t)sn, (int32_t)sn, h->rpT, h->valT, kind, h->prm.pc_alpha, fc);
+      if (sm > 0) k_apply_factors<<<gr, 256, 0, s>>>((int32_t)sm, (int32_t)sm, h->rpA, h->ciA, h->valA, fr, fc, 0);
+      if (sn > 0) k_apply_factors<<<gc, 256, 0, s>>>((int32_t)sn, (int32_t)sn, h->rpT, h->ciT, h->valT, fr, fc, 1);
       if (sm > 0) k_mul_inplace<<<gV, 256, 0, s>>>((int32_t)sm, h->dr, fr);
       if (sn > 0) k_mul_inplace<<<gV, 256, 0, s>>>((int32_t)sn, h->dc, fc);
     }

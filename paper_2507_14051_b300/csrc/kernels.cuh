@@ -100,9 +100,9 @@ __global__ void k_warm_cols(int32_t n, const double* c, const double* lv, const 
                             double* aty0, double* xbar, Ctl* ctl, double* partials);
 
 // setup.cu
-__global__ void k_row_factor(int32_t rows, const int32_t* rp, const double* val, int32_t kind,
+__global__ void k_row_factor(int32_t rows, int32_t split, const int32_t* rp, const double* val, int32_t kind,
                              double expo, double* f);
-__global__ void k_apply_factors(int32_t rows, const int32_t* rp, const int32_t* ci, double* val,
+__global__ void k_apply_factors(int32_t rows, int32_t split, const int32_t* rp, const int32_t* ci, double* val,
                                 const double* fr, const double* fc, int32_t transposed);
 __global__ void k_mul_inplace(int32_t len, double* d, const double* f);
 __global__ void k_scale_cols(int32_t n, const double* dc, double* c, double* lv, double* uv,

@@ -17,19 +17,25 @@
 
 namespace pdhg {
 
-// Per-row statistic of a CSR matrix, one warp per row, then the factor 1/sqrt(stat) (1 when
-// stat == 0).  kind 0: max |a|; kind 1: sum |a|^expo.
-__global__ void k_row_factor(int32_t rows, const int32_t* __restrict__ rp,
+// Per-row statistic of a CSR matrix, then the factor 1/sqrt(stat) (1 when stat == 0).  kind 0:
+// max |a|; kind 1: sum |a|^expo.  Rows [0, split) (the long ones: the storage orders rows by
+// decreasing length) take one warp each, the others one thread each: an FP64 warp instruction
+// costs the FP64 pipe the same whatever its active lanes, so a warp per short row (and its
+// lane-0 division and square root) would cost 32 times the arithmetic.
+__device__ __forceinline__ double row_stat_term(double a, int32_t kind, double expo) {
+  return kind == 0 ? a : (expo == 1.0 ? a : pow(a, expo));
+}
+__global__ void k_row_factor(int32_t rows, int32_t split, const int32_t* __restrict__ rp,
                              const double* __restrict__ val, int32_t kind, double expo,
                              double* __restrict__ f) {
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += nw) {
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < split; r += nw) {
     const int b = rp[r], e = rp[r + 1];
     double acc = 0.0;
     for (int p = b + lane; p < e; p += 32) {
-      const double a = fabs(val[p]);
-      acc = kind == 0 ? fmax(acc, a) : acc + (expo == 1.0 ? a : pow(a, expo));
+      const double a = row_stat_term(fabs(val[p]), kind, expo);
+      acc = kind == 0 ? fmax(acc, a) : acc + a;
     }
     for (int off = 16; off > 0; off >>= 1) {
       const double o = __shfl_xor_sync(kFull, acc, off);
@@ -37,20 +43,39 @@ __global__ void k_row_factor(int32_t rows, const int32_t* __restrict__ rp,
     }
     if (lane == 0) f[r] = acc > 0.0 ? 1.0 / sqrt(acc) : 1.0;
   }
+  for (int r = split + blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    const int b = rp[r], e = rp[r + 1];
+    double acc = 0.0;
+    for (int p = b; p < e; ++p) {
+      const double a = row_stat_term(fabs(val[p]), kind, expo);
+      acc = kind == 0 ? fmax(acc, a) : acc + a;
+    }
+    f[r] = acc > 0.0 ? 1.0 / sqrt(acc) : 1.0;
+  }
 }
 
 // val <- (val * f_row) * f_col on one stored copy.  For the copy of A, row r of the storage
 // is a row of A (f_row = fr[r], f_col = fc[ci]); for the copy of A^T, row r of the storage is
-// a column of A (f_row = fr[ci], f_col = fc[r]).
-__global__ void k_apply_factors(int32_t rows, const int32_t* __restrict__ rp,
+// a column of A (f_row = fr[ci], f_col = fc[r]).  Rows [0, split) one warp each, the others
+// one thread each (as k_row_factor).
+__global__ void k_apply_factors(int32_t rows, int32_t split, const int32_t* __restrict__ rp,
                                 const int32_t* __restrict__ ci, double* __restrict__ val,
                                 const double* __restrict__ fr, const double* __restrict__ fc,
                                 int32_t transposed) {
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += nw) {
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < split; r += nw) {
     const int b = rp[r], e = rp[r + 1];
     for (int p = b + lane; p < e; p += 32) {
+      const int o = ci[p];
+      const double frow = transposed ? fr[o] : fr[r];
+      const double fcol = transposed ? fc[r] : fc[o];
+      val[p] = (val[p] * frow) * fcol;
+    }
+  }
+  for (int r = split + blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    const int b = rp[r], e = rp[r + 1];
+    for (int p = b; p < e; ++p) {
       const int o = ci[p];
       const double frow = transposed ? fr[o] : fr[r];
       const double fcol = transposed ? fc[r] : fc[o];

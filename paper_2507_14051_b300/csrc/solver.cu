@@ -679,13 +679,21 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
     double* fc = h->x;
     const int gr = grid_for((int64_t)m * 32, 256, 8 * h->num_sms);
     const int gc = grid_for((int64_t)n * 32, 256, 8 * h->num_sms);
+    // rows [0, split) are longer than 32 entries (rows and columns are stored by decreasing
+    // length): a warp each in the scaling kernels, the others a thread each
+    auto split_of = [](const std::vector<int32_t>& r) {
+      int32_t q = 0;
+      while (q + 1 < (int32_t)r.size() && r[q + 1] - r[q] > 32) ++q;
+      return q;
+    };
+    const int32_t splitA = split_of(rpA), splitT = split_of(rpT);
     for (int pass = 0; pass < passes; ++pass) {
       const bool pc = (pass == h->prm.ruiz_iters);
       const int kind = pc ? 1 : 0;
-      if (m > 0) k_row_factor<<<gr, 256, 0, s>>>(m, h->rpA, h->valA, kind, 2.0 - h->prm.pc_alpha, fr);
-      if (n > 0) k_row_factor<<<gc, 256, 0, s>>>(n, h->rpT, h->valT, kind, h->prm.pc_alpha, fc);
-      if (m > 0) k_apply_factors<<<gr, 256, 0, s>>>(m, h->rpA, h->ciA, h->valA, fr, fc, 0);
-      if (n > 0) k_apply_factors<<<gc, 256, 0, s>>>(n, h->rpT, h->ciT, h->valT, fr, fc, 1);
+      if (m > 0) k_row_factor<<<gr, 256, 0, s>>>(m, splitA, h->rpA, h->valA, kind, 2.0 - h->prm.pc_alpha, fr);
+      if (n > 0) k_row_factor<<<gc, 256, 0, s>>>(n, splitT, h->rpT, h->valT, kind, h->prm.pc_alpha, fc);
+      if (m > 0) k_apply_factors<<<gr, 256, 0, s>>>(m, splitA, h->rpA, h->ciA, h->valA, fr, fc, 0);
+      if (n > 0) k_apply_factors<<<gc, 256, 0, s>>>(n, splitT, h->rpT, h->ciT, h->valT, fr, fc, 1);
       if (m > 0) k_mul_inplace<<<h->gridV, 256, 0, s>>>(m, h->dr, fr);
       if (n > 0) k_mul_inplace<<<h->gridV, 256, 0, s>>>(n, h->dc, fc);
     }
