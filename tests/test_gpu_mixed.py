@@ -37,14 +37,17 @@ def max_len(lp):
     return int(max(rows, cols))
 
 
+@pytest.mark.parametrize("persistent", [-1, 1])
 @pytest.mark.parametrize("seed", range(4))
 @pytest.mark.parametrize("iters", [1, 64, 400])
-def test_fp32_fixed_map_error_bound(cuda_device, seed, iters):
+def test_fp32_fixed_map_error_bound(cuda_device, seed, iters, persistent):
+    """persistent -1 runs these small LPs on the cluster loop, 1 on the grid-wide loop, whose
+    FP32 form reads the sliced tiles through shared-memory stages filled by bulk copies."""
     lp = gen.small_lp(seed)
     kw = dict(restart_enabled=0, pid_enabled=0, **NO_SCALING)
     eta = oracle.solve(lp, tol=0.0, max_iter=1, **kw)["eta"]
     o = oracle.solve(lp, tol=0.0, max_iter=iters, eta=eta, **kw)
-    g = gpu(lp, 0.0, iters, eta=eta, precision=2, **kw)
+    g = gpu(lp, 0.0, iters, eta=eta, precision=2, persistent=persistent, **kw)
     assert g["iters"] == g["iters_fp32"] == iters
     bound = iters * U32 * (max_len(lp) + 4)
     for a, b in ((g["x"], o["x"]), (g["y"], o["y"])):
@@ -74,7 +77,8 @@ def test_mixed_solve_reaches_fp64_tolerance(cuda_device, seed):
                                   lambda: gen.ragged_rows(5, 400, 3000)])
 def test_mixed_solve_structured(cuda_device, make):
     """Structured LPs with planted optima: the mixed solve meets 1e-6 (oracle-evaluated) and
-    its objective matches the planted optimum."""
+    its objective matches the planted optimum (the MIPLIB-shaped one runs the grid-wide loop,
+    whose FP32 phase stages its sliced tiles)."""
     lp = make()
     g = gpu(lp, 1e-6, 1_000_000, precision=1)
     assert g["status"] == oracle.OPTIMAL
