@@ -54,10 +54,6 @@ struct BinTable {
   const int32_t* sell_off;
   const int32_t* sell_ci;
   const void* sell_val;
-  // set (nonzero) by a kernel whose wait for a staged copy of a sliced tile ran out of time;
-  // the control then ends the solve with an internal error (stage_error may be NULL: no
-  // staging)
-  unsigned int* stage_error;
   Bin bin[kMaxBins];
 };
 
@@ -725,197 +721,6 @@ __device__ __forceinline__ void block_totals(const double* partials, int nblocks
 #pragma unroll
   for (int q = 0; q < kNumSums; ++q) tot[q] = q < nsums ? out[q] : 0.0;
   __syncthreads();
-}
-
-// ------------------------------------------------- staged sliced tiles (FP32 loop kernel)
-//
-// A warp of the FP32 loop kernel reads a sliced tile's slots from shared memory, where a bulk
-// copy (cp.async.bulk, completion on an mbarrier) brought them while the warp was working on
-// its previous tile: the tile's chain of dependent accesses then starts at the gathers, and the
-// copies in flight do not hold registers.  Two stages per warp; a tile with more than
-// kStageSlots slots (lane_target above 8) is read from global memory directly.
-
-constexpr int kStageSlots = 8;
-// one stage: kStageSlots slots of 32 values and 32 column indices (4-byte values)
-constexpr int kStageBytes = kStageSlots * 32 * 8;
-constexpr int kStageWarpBytes = 2 * kStageBytes + 128;  // two stages + two mbarriers, 128-byte aligned
-constexpr int kStageLaunchBytes = kWarps * kStageWarpBytes + 128;  // per block, with room to align
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-struct WarpStages {
-  unsigned char* base;  // stage s at base + s * kStageBytes, its mbarrier at base + 2 kStageBytes + 8 s
-  unsigned phase;       // bit s: parity the next completion of stage s will have
-  __device__ __forceinline__ unsigned char* buf(int st) const { return base + st * kStageBytes; }
-  __device__ __forceinline__ uint64_t* bar(int st) const {
-    return reinterpret_cast<uint64_t*>(base + 2 * kStageBytes) + st;
-  }
-};
-
-// The calling warp's two stages in `base` (kStageWarpBytes, 128-byte aligned); lane 0 sets up
-// the mbarriers (one arrival each: lane 0's expect_tx).
-__device__ __forceinline__ WarpStages warp_stages_init(unsigned char* base, int lane) {
-  WarpStages w;
-  w.base = base;
-  w.phase = 0u;
-  if (lane == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(w.bar(0))) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(w.bar(1))) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncwarp();
-  return w;
-}
-
-// Lane 0: copy slots [off, off + 32 slots) of the sliced tile (values and indices, FP32) into
-// stage st.  off is a multiple of 32 entries and the arrays start on 256-byte boundaries, so
-// both copies start and end on 16-byte boundaries.  Earlier reads of the stage by the warp
-// (generic proxy) are ordered before the copy (async proxy) by the fence.
-template <class V>
-__device__ __forceinline__ void stage_issue(const WarpStages& w, int st, const BinTable& bins, int off,
-                                            int slots) {
-  const unsigned bytes = (unsigned)slots * 32u * (unsigned)sizeof(V);
-  const V* vsrc = static_cast<const V*>(bins.sell_val) + off;
-  const int32_t* csrc = bins.sell_ci + off;
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(w.bar(st))),
-               "r"(2u * bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(w.buf(st))),
-      "l"(vsrc), "r"(bytes), "r"(smem_u32(w.bar(st)))
-      : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(w.buf(st) + kStageBytes / 2)),
-      "l"(csrc), "r"(bytes), "r"(smem_u32(w.bar(st)))
-      : "memory");
-}
-
-// All lanes: wait for stage st's copy (bounded: after ~2^22 polls the wait gives up, raises
-// bins.stage_error and returns false; the tile's value is then not used).
-__device__ __forceinline__ bool stage_wait(WarpStages& w, int st, const BinTable& bins) {
-  const unsigned parity = (w.phase >> st) & 1u;
-  unsigned ok = 0;
-  for (int poll = 0; poll < (1 << 22) && !ok; ++poll) {
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(smem_u32(w.bar(st))), "r"(parity)
-        : "memory");
-  }
-  w.phase ^= 1u << st;
-  if (!ok && bins.stage_error && (threadIdx.x & 31) == 0) atomicOr(bins.stage_error, 1u);
-  return ok != 0;
-}
-
-// Dot products of a staged sliced tile: lane L's row from the stage's slots (same entry order,
-// same bits as sliced_spmv).
-template <class V>
-__device__ __forceinline__ V staged_spmv(const WarpStages& w, int st, const V* __restrict__ xg, int slots,
-                                         int lane, const LoadPolicy& pol) {
-  const V* sv = reinterpret_cast<const V*>(w.buf(st)) + lane;
-  const int32_t* sc = reinterpret_cast<const int32_t*>(w.buf(st) + kStageBytes / 2) + lane;
-  V acc = V(0);
-  for (int u0 = 0; u0 < slots; u0 += 4) {
-    V v[4], xv[4];
-    int c[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      c[u] = u0 + u < slots ? sc[32 * (u0 + u)] : -1;
-      v[u] = u0 + u < slots ? sv[32 * (u0 + u)] : V(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? ld_gather(xg + c[u], pol.keep) : V(0);
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
-  }
-  return acc;
-}
-
-// for_each_row_pf for the FP32 loop kernel with staged sliced tiles: the same tasks, each
-// lane's sums in the same order; one task at a time per warp, the next sliced tile's slots
-// copied into the other stage while this one runs (its slot offsets loaded one task earlier
-// still, so issuing the copy waits on nothing).
-template <class V, class Pre, class Epi>
-__device__ __forceinline__ void for_each_row_staged(const BinTable& bins, const int32_t* __restrict__ rp,
-                                                    const int32_t* __restrict__ ci, const V* __restrict__ val,
-                                                    const V* __restrict__ xg, const LoadPolicy& pol,
-                                                    double (&s)[kNumSums], WarpStages& ws, Pre&& pre, Epi&& epi) {
-  using In = decltype(pre(0));
-  const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * kWarps;
-  const int total = bins.nchunks + bins.ntasks;
-  // slot range of task t if it is a sliced tile that fits a stage (x = first slot, y = slots;
-  // y = 0 otherwise); read by lane 0 only
-  auto staged_range = [&](int t) -> int2 {
-    if (t >= total || t < bins.nchunks || bins.sell_off == nullptr) return make_int2(0, 0);
-    const Bin& B = bins.bin[find_bin(bins, t - bins.nchunks)];
-    if (!B.sliced) return make_int2(0, 0);
-    const int q = t - bins.nchunks;
-    const int o0 = bins.sell_off[q], o1 = bins.sell_off[q + 1];
-    const int slots = (o1 - o0) >> 5;
-    return slots <= kStageSlots ? make_int2(o0, slots) : make_int2(0, 0);
-  };
-  const int t0 = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-  int k = 0;
-  int2 r_cur = make_int2(0, 0), r_next = make_int2(0, 0);
-  if (lane == 0) {
-    r_cur = staged_range(t0);
-    if (r_cur.y > 0) stage_issue<V>(ws, 0, bins, r_cur.x, r_cur.y);
-    r_next = staged_range(t0 + nwarps);
-  }
-  for (int task = t0; task < total; task += nwarps, ++k) {
-    const int st = k & 1;
-    const int cur_slots = __shfl_sync(kFull, r_cur.y, 0);
-    // the next task's copy into the other stage (its offsets were loaded one task ago), then
-    // the offsets of the task after it
-    if (lane == 0) {
-      if (r_next.y > 0) stage_issue<V>(ws, st ^ 1, bins, r_next.x, r_next.y);
-      r_cur = r_next;
-      r_next = staged_range(task + 2 * nwarps);
-    }
-    if (task < bins.nchunks) {
-      const int4 ch = bins.chunk[task];
-      const int b = rp[ch.x] + (task - ch.y) * kChunkNnz;
-      const int e = min(rp[ch.x + 1], b + kChunkNnz);
-      const V v = warp_sum(strided_dot(ci, val, xg, b + lane, e, 32, kChunkNnz / 32, pol));
-      if (lane == 0) {
-        bins.part[task] = (double)v;
-        __threadfence();
-        if (atomicAdd(bins.arrivals + ch.x, 1u) == (unsigned)ch.z - 1u) {
-          __threadfence();
-          double tot = 0.0;
-          for (int q = 0; q < ch.z; ++q) tot += __ldcg(bins.part + ch.y + q);
-          bins.arrivals[ch.x] = 0u;
-          double c[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-          In in = pre(ch.x);
-          epi(ch.x, (V)tot, in, c);
-#pragma unroll
-          for (int q = 0; q < kNumSums; ++q) bins.contrib[ch.x * kNumSums + q] = c[q];
-        }
-      }
-      __syncwarp();
-      continue;
-    }
-    const TileTask a = tile_task(bins, rp, task, lane);
-    In in{};
-    if (lane < a.nrows) in = pre(a.row0 + lane);
-    V v;
-    if (cur_slots > 0) {
-      const bool ok = stage_wait(ws, st, bins);
-      v = ok ? staged_spmv(ws, st, xg, cur_slots, lane, pol) : V(0);
-    } else {
-      v = a.sliced ? sliced_spmv<V>(bins, xg, a, lane, pol)
-                   : tile_spmv_b<V>(ci, val, xg, a.b, a.e, a.nrows, a.lanes, a.per_lane, lane, pol);
-    }
-    if (lane < a.nrows) epi(a.row0 + lane, v, in, s);
-    __syncwarp();  // every lane is done with stage st before a later copy overwrites it
-  }
 }
 
 }  // namespace pdhg

@@ -139,17 +139,6 @@ __global__ void __launch_bounds__(kThreads, 4)
   __shared__ ColStepR<V> cstr;
   __shared__ Halpern hw;
   __shared__ int rs;
-  // FP32 grid loop: each warp's two stages for bulk copies of sliced tiles (dynamic shared
-  // memory, kStageLaunchBytes)
-  constexpr bool kStaged = sizeof(V) == sizeof(float) && !kCl;
-  extern __shared__ __align__(128) unsigned char dyn_smem[];
-  WarpStages ws{};
-  if constexpr (kStaged) {
-    // the launch gives 128 bytes more than the stages need, so they start on a 128-byte boundary
-    unsigned char* base = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(dyn_smem) + 127) & ~static_cast<uintptr_t>(127));
-    ws = warp_stages_init(base + (threadIdx.x >> 5) * kStageWarpBytes, threadIdx.x & 31);
-  }
   if (threadIdx.x == 0) sc = *ra.ctl;
   __syncthreads();
   const LoadPolicy pol = make_policy();
@@ -177,11 +166,8 @@ __global__ void __launch_bounds__(kThreads, 4)
       auto epi1 = [&](int i, V w, const NoOperands&, double (&acc)[kNumSums]) {
         row_epilogue_r(ra, st, i, w, acc);
       };
-      if constexpr (kStaged)
-        for_each_row_staged(ra.bins, ra.rp, ra.ci, ra.val, ra.xbar, pol, s, ws, pre1, epi1);
-      else
-        for_each_row_pf<V, decltype(pre1)&, decltype(epi1)&, kCl>(ra.bins, ra.rp, ra.ci, ra.val, ra.xbar, pol, s,
-                                                                   pre1, epi1);
+      for_each_row_pf<V, decltype(pre1)&, decltype(epi1)&, kCl>(ra.bins, ra.rp, ra.ci, ra.val, ra.xbar, pol, s, pre1,
+                                                             epi1);
     } else {
       if (threadIdx.x == 0) rst = row_step(sc);
       __syncthreads();
@@ -195,11 +181,8 @@ __global__ void __launch_bounds__(kThreads, 4)
       auto epi2 = [&](int i, V v, const NoOperands&, double (&acc)[kNumSums]) {
         row_epilogue<V, false>(ra, st, i, v, acc);
       };
-      if constexpr (kStaged)
-        for_each_row_staged(ra.bins, ra.rp, ra.ci, ra.val, xh, pol, s, ws, pre2, epi2);
-      else
-        for_each_row_pf<V, decltype(pre2)&, decltype(epi2)&, kCl>(ra.bins, ra.rp, ra.ci, ra.val, xh, pol, s, pre2,
-                                                                   epi2);
+      for_each_row_pf<V, decltype(pre2)&, decltype(epi2)&, kCl>(ra.bins, ra.rp, ra.ci, ra.val, xh, pol, s, pre2,
+                                                             epi2);
     }
     const int nr = check ? 5 : 2;
     store_block_partials(s, nr, part_rows);
@@ -260,11 +243,8 @@ __global__ void __launch_bounds__(kThreads, 4)
       auto epi3 = [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) {
         col_epilogue_r(ca, cs, j, u, acc);
       };
-      if constexpr (kStaged)
-        for_each_row_staged(ca.bins, ca.rp, ca.ci, ca.val, gy, pol, s2, ws, pre3, epi3);
-      else
-        for_each_row_pf<V, decltype(pre3)&, decltype(epi3)&, kCl>(ca.bins, ca.rp, ca.ci, ca.val, gy, pol, s2, pre3,
-                                                                   epi3);
+      for_each_row_pf<V, decltype(pre3)&, decltype(epi3)&, kCl>(ca.bins, ca.rp, ca.ci, ca.val, gy, pol, s2, pre3,
+                                                             epi3);
     } else {
       if (threadIdx.x == 0) cst = col_step(sc, ca);
       __syncthreads();
@@ -277,26 +257,15 @@ __global__ void __launch_bounds__(kThreads, 4)
       auto epi4 = [&](int j, V u, const NoOperands&, double (&acc)[kNumSums]) {
         col_epilogue<V, false>(ca, cs, j, u, acc);
       };
-      if constexpr (kStaged)
-        for_each_row_staged(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, s2, ws, pre4, epi4);
-      else
-        for_each_row_pf<V, decltype(pre4)&, decltype(epi4)&, kCl>(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, s2,
-                                                                   pre4, epi4);
+      for_each_row_pf<V, decltype(pre4)&, decltype(epi4)&, kCl>(ca.bins, ca.rp, ca.ci, ca.val, ca.yh, pol, s2, pre4,
+                                                             epi4);
     }
     const int nc = check ? 5 : 1;
     store_block_partials(s2, nc, part_cols);
     phase_sync();
     double tot2[kNumSums];
     block_totals(part_cols, gridDim.x, nc, &ca.bins, tot2);
-    if (threadIdx.x == 0) {
-      col_control(sc, tot2, check);
-      // a staged copy that never completed (read after the barrier: every block sees the same)
-      if (kStaged && ca.bins.stage_error && *(volatile unsigned*)ca.bins.stage_error != 0u) {
-        sc.status = kInternalError;
-        sc.iters = sc.t + 1;
-        sc.done = 1;
-      }
-    }
+    if (threadIdx.x == 0) col_control(sc, tot2, check);
     __syncthreads();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {

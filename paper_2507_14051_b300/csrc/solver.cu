@@ -82,7 +82,6 @@ struct lp_solver {
   cudaGraphExec_t exec32 = nullptr;
   bool loop_active32 = false;
   double* out_buf = nullptr;
-  unsigned int* stage_error = nullptr;  // raised by the FP32 loop kernel if a staged copy times out
   double* partials = nullptr;
   double* partials2 = nullptr;  // column-phase partials of the loop kernel
   double* partials3 = nullptr;  // the loop kernel's restart-time PID norms
@@ -255,8 +254,6 @@ cudaError_t launch_loop(const lp_solver* h, const RowArgsT<V>& ra, const ColArgs
   cfg.blockDim = dim3((unsigned)kThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
-  // the FP32 grid loop stages sliced tiles in dynamic shared memory (two stages per warp)
-  if (sizeof(V) == sizeof(float) && h->cluster == 0) cfg.dynamicSmemBytes = (size_t)kStageLaunchBytes;
   cudaLaunchAttribute attr[2];
   if (h->cluster > 0) {
     cfg.gridDim = dim3((unsigned)h->cluster);
@@ -576,8 +573,7 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   if (h->prm.precision != 0) {
     // the FP32 loop kernel has fewer registers (4 blocks per SM): its own grid, sized the same way
     int occF = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occF, iter_kernels<float>().loop_refl, kThreads,
-                                                     (size_t)kStageLaunchBytes));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occF, iter_kernels<float>().loop, kThreads, 0));
     if (occF < 1) occF = 1;
     const int gA = grid_for_tasks((int64_t)h->binsA.ntasks + h->binsA.nchunks, h->num_sms, occF * h->num_sms);
     const int gT = grid_for_tasks((int64_t)h->binsT.ntasks + h->binsT.nchunks, h->num_sms, occF * h->num_sms);
@@ -608,10 +604,6 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   CK(h->alloc(&h->partials2, (size_t)h->max_grid * kNumSums));
   CK(h->alloc(&h->partials3, (size_t)h->max_grid * kNumSums));
   CK(h->alloc(&h->ctl, 1));
-  CK(h->alloc(&h->stage_error, 1));
-  CK(cudaMemset(h->stage_error, 0, sizeof(unsigned int)));
-  h->binsA.stage_error = h->stage_error;
-  h->binsT.stage_error = h->stage_error;
   CK(h->alloc(&h->pw, 1));
   CK(cudaMemset(h->ctl, 0, sizeof(Ctl)));
   CK(cudaMemset(h->pw, 0, sizeof(PwCtl)));
@@ -925,7 +917,6 @@ lp_status enqueue_start(lp_solver* h, double tol, int64_t max_iter, cudaStream_t
   init.cand_slot = 0;
   init.best_slot = -1;
   k_init_ctl<<<1, 1, 0, s>>>(h->ctl, init);
-  CK(cudaMemsetAsync(h->stage_error, 0, sizeof(unsigned int), s));
   RowArgsT<V> ra;
   ColArgsT<V> ca;
   fill_args(h, ra, ca);

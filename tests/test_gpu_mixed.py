@@ -41,8 +41,7 @@ def max_len(lp):
 @pytest.mark.parametrize("seed", range(4))
 @pytest.mark.parametrize("iters", [1, 64, 400])
 def test_fp32_fixed_map_error_bound(cuda_device, seed, iters, persistent):
-    """persistent -1 runs these small LPs on the cluster loop, 1 on the grid-wide loop, whose
-    FP32 form reads the sliced tiles through shared-memory stages filled by bulk copies."""
+    """persistent -1 runs these small LPs on the cluster loop, 1 on the grid-wide loop."""
     lp = gen.small_lp(seed)
     kw = dict(restart_enabled=0, pid_enabled=0, **NO_SCALING)
     eta = oracle.solve(lp, tol=0.0, max_iter=1, **kw)["eta"]
@@ -77,8 +76,8 @@ def test_mixed_solve_reaches_fp64_tolerance(cuda_device, seed):
                                   lambda: gen.ragged_rows(5, 400, 3000)])
 def test_mixed_solve_structured(cuda_device, make):
     """Structured LPs with planted optima: the mixed solve meets 1e-6 (oracle-evaluated) and
-    its objective matches the planted optimum (the MIPLIB-shaped one runs the grid-wide loop,
-    whose FP32 phase stages its sliced tiles)."""
+    its objective matches the planted optimum (the MIPLIB-shaped one runs the grid-wide
+    loop)."""
     lp = make()
     g = gpu(lp, 1e-6, 1_000_000, precision=1)
     assert g["status"] == oracle.OPTIMAL
