@@ -92,8 +92,22 @@ struct Ctl {
   unsigned int count0, count1, count2, count3;
 };
 
+// An FP64 value's bits as a signed integer with the value's order (IEEE 754 sign-magnitude:
+// negative values have their magnitude bits flipped), so that -inf < ... < -0 < +0 < ... < +inf.
+__device__ __forceinline__ long long ord_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+// min(max(v, lo), hi) by integer compares of ord_key: the same value as fmin(fmax(v, lo), hi)
+// for every non-NaN v (infinite bounds included; -0 orders below +0).  On this GPU an FP64 min or max
+// takes an FP64 pipe slot like an fma, and the loop kernels are bound by that pipe; integer
+// compares and selects run on the integer pipes.  A NaN v goes to hi or lo by its sign bit.
 __device__ __forceinline__ double clampd(double v, double lo, double hi) {
-  return fmin(fmax(v, lo), hi);
+  const long long kv = ord_key(v), kl = ord_key(lo), kh = ord_key(hi);
+  const bool below = kv < kl;
+  const long long kr = below ? kl : kv;
+  const double r = below ? lo : v;
+  return kr > kh ? hi : r;
 }
 __device__ __forceinline__ float clampd(float v, float lo, float hi) {
   return fminf(fmaxf(v, lo), hi);
