@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kThreads, 4)
   __shared__ Ctl sc;
   __shared__ RowStep rst;
   __shared__ ColStepT<V> cst;
-  __shared__ RowStepR rstr;
+  __shared__ RowStepR<V> rstr;
   __shared__ ColStepR<V> cstr;
   __shared__ Halpern hw;
   __shared__ int rs;
@@ -148,9 +148,9 @@ __global__ void __launch_bounds__(kThreads, 4)
     double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
     int check;
     if constexpr (kRefl) {
-      if (threadIdx.x == 0) rstr = row_step_r(sc);
+      if (threadIdx.x == 0) rstr = row_step_r<V>(sc);
       __syncthreads();
-      const RowStepR st = rstr;
+      const RowStepR<V> st = rstr;
       check = st.check;
       if (check) {  // A xhat_t for the primal residual of the KKT test
         const V* __restrict__ xc = (sc.t & 1) ? ra.xh1 : ra.xh0;

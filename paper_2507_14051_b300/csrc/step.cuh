@@ -397,27 +397,30 @@ __device__ __forceinline__ void col_prefetch(const ColArgsT<V>& a, const ColStep
 // which near the tolerance are differences of nearly equal products, by up to 1e-3 relative.
 // The fixed-point residual's cross term is summed as (y - yhat)(A x - w) = 2 (y - yhat) A (x - xhat).
 
+// The scalars in the iterates' type (rounded once per block and iteration, not per row).
+template <class V>
 struct RowStepR {
   int mode;  // 0 Halpern combine, 1 restart, 2 first iteration (state is zero)
   int check;
   int cand;
-  double lam, mu, sigma, inv_sigma;
+  V lam, mu, sigma, inv_sigma;
 };
 
-__device__ __forceinline__ RowStepR row_step_r(const Ctl& c) {
-  RowStepR st;
+template <class V>
+__device__ __forceinline__ RowStepR<V> row_step_r(const Ctl& c) {
+  RowStepR<V> st;
   st.mode = (c.t == 0) ? 2 : c.restart;
   st.check = is_check(c, c.t) ? 1 : 0;
   st.cand = c.cand_slot;
-  st.lam = -c.hb;  // gamma = 1: hb = -lam
-  st.mu = c.he;
-  st.sigma = c.sigma;
-  st.inv_sigma = c.inv_sigma;
+  st.lam = (V)(-c.hb);  // gamma = 1: hb = -lam
+  st.mu = (V)c.he;
+  st.sigma = (V)c.sigma;
+  st.inv_sigma = (V)c.inv_sigma;
   return st;
 }
 
 template <class V>
-__device__ __forceinline__ void row_prefetch_r(const RowArgsT<V>& a, const RowStepR& st, int i) {
+__device__ __forceinline__ void row_prefetch_r(const RowArgsT<V>& a, const RowStepR<V>& st, int i) {
   if (st.mode == 0) {
     prefetch_l1(a.qy + i);
     prefetch_l1(a.y0 + i);
@@ -433,12 +436,12 @@ __device__ __forceinline__ void row_prefetch_r(const RowArgsT<V>& a, const RowSt
 
 // Row epilogue of the reflected form: wv = A xbar_t of row i.
 template <class V>
-__device__ __forceinline__ void row_epilogue_r(const RowArgsT<V>& a, const RowStepR& st, int i, V wv,
+__device__ __forceinline__ void row_epilogue_r(const RowArgsT<V>& a, const RowStepR<V>& st, int i, V wv,
                                                double (&acc)[kNumSums]) {
-  const V sigma = (V)st.sigma, inv_sigma = (V)st.inv_sigma;
+  const V sigma = st.sigma, inv_sigma = st.inv_sigma;
   V yi, axi;
   if (st.mode == 0) {
-    const V lam = (V)st.lam, mu = (V)st.mu;
+    const V lam = st.lam, mu = st.mu;
     yi = fmav(lam, a.qy[i], mu * a.y0[i]);
     axi = fmav(lam, a.w[i], mu * a.ax0[i]);
   } else if (st.mode == 1) {
@@ -473,7 +476,7 @@ struct ColStepR {
   int restart;
   int check;  // iteration t is a check iteration
   int cand;
-  double lam, mu, tau;
+  V lam, mu, tau;  // in the iterates' type
   const V* xc;  // xhat_t
   V* xn;        // xhat_{t+1}
 };
@@ -484,9 +487,9 @@ __device__ __forceinline__ ColStepR<V> col_step_r(const Ctl& c, const ColArgsT<V
   st.restart = c.restart;
   st.check = is_check(c, c.t) ? 1 : 0;
   st.cand = c.cand_slot;
-  st.lam = -c.hb;
-  st.mu = c.he;
-  st.tau = c.tau;
+  st.lam = (V)(-c.hb);
+  st.mu = (V)c.he;
+  st.tau = (V)c.tau;
   st.xc = (c.t & 1) ? a.xh1 : a.xh0;
   st.xn = (c.t & 1) ? a.xh0 : a.xh1;
   return st;
@@ -510,7 +513,7 @@ __device__ __forceinline__ void col_prefetch_r(const ColArgsT<V>& a, const ColSt
 template <class V>
 __device__ __forceinline__ void col_epilogue_r(const ColArgsT<V>& a, const ColStepR<V>& st, int j, V u,
                                                double (&acc)[kNumSums]) {
-  const V tau = (V)st.tau;
+  const V tau = st.tau;
   V xj, atyj;
   if (st.restart) {
     xj = st.xc[j];
@@ -518,7 +521,7 @@ __device__ __forceinline__ void col_epilogue_r(const ColArgsT<V>& a, const ColSt
     a.x0[j] = xj;
     a.aty0[j] = u;
   } else {
-    const V lam = (V)st.lam, mu = (V)st.mu;
+    const V lam = st.lam, mu = st.mu;
     xj = fmav(lam, a.xbar[j], mu * a.x0[j]);
     atyj = fmav(lam, u, mu * a.aty0[j]);
   }
