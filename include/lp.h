@@ -88,11 +88,17 @@ typedef struct {
                               0: automatic (8 for lp_solve; 32 for the batch, whose long rows
                               then take fewer FP64 butterfly additions per row) */
   int32_t persistent;      /* 1: one cooperative kernel runs `unroll` iterations per launch with
-                              grid-wide barriers between phases; 2: the same loop as one block
-                              (block barriers only; for LPs of a few dozen tiles per phase);
-                              0: one kernel per phase; -1: 2 when each phase has at most
-                              4 tiles per warp of one block, else 1 when every block of both
-                              phases fits on the GPU at once, else 0 */
+                              grid-wide barriers between phases; 2: the same loop as one
+                              thread-block cluster of up to 16 CTAs (cluster barriers; for LPs
+                              of a few dozen tiles per phase); 3: the loop as one cluster whose
+                              CTAs hold the whole LP in shared memory for the length of a launch
+                              (gamma = 1 and an LP that fits: no row or column longer than 128
+                              entries, and each CTA's slices plus replicas of the gathered
+                              vectors, about 8 (3n + 2m) bytes, within its shared memory);
+                              0: one kernel per phase; -1: 3 when it applies, else 2 when each
+                              phase has at most 4 tiles per warp of a 16-CTA cluster, else 1
+                              when every block of both phases fits on the GPU at once, else 0.
+                              3 on an LP where it does not apply chooses as -1 does. */
   int32_t precision;       /* 0: FP64 throughout.  1: mixed -- matrix and iterates in FP32 with
                               FP32 SpMV accumulation (reductions, restart test, PID and KKT test in
                               FP64) until the relative KKT error is <= max(tol, switch_tol) or
@@ -191,8 +197,8 @@ LP_API lp_status lp_get(lp_handle h, double* x, double* y, int32_t* solve_status
 /* Extra scalars of the last solve (host doubles): out[0] eta, out[1] final omega,
  * out[2] restarts, out[3] ||A~||_2 from the power iteration (0 if eta was given),
  * out[4] power-iteration steps, out[5] primal objective c^T x, out[6] dual objective,
- * out[7] 1 if the cooperative loop kernel runs the solve (2 if as one block), 0 if one kernel
- * per phase does,
+ * out[7] 1 if the cooperative loop kernel runs the solve, 2 if the cluster loop does, 3 if the
+ * shared-memory cluster loop does, 0 if one kernel per phase does,
  * out[8] iterations done in FP32 (precision 1 or 2; 0 for FP64).
  * Waits like lp_get.  Errors: LP_ERR_INVALID_ARG, LP_ERR_NOT_SOLVED, LP_ERR_CUDA. */
 LP_API lp_status lp_get_info(lp_handle h, double* out9);

@@ -71,7 +71,7 @@ struct Ctl {
   int32_t restart_enabled;
   int64_t t, k, iters, restarts, max_iter, check_every, trace_cap, bodies;
   double tol;
-  double r0, r_prev;
+  double r0, r_prev;  // squared fixed-point residuals r_0^2 and r_{t-1}^2 of the epoch
   double pid_integral, pid_eprev;
   int32_t pid_has_prev;
   int32_t pid_enabled;

@@ -151,7 +151,7 @@ inline lp_status check_params(const lp_params& p) {
   if (p.trace_cap < 0) return fail(LP_ERR_INVALID_ARG, "trace_cap must be >= 0");
   if (p.unroll < 1 || p.unroll > 64) return fail(LP_ERR_INVALID_ARG, "unroll must be in [1, 64]");
   if (p.lane_target < 0 || p.lane_target > 64) return fail(LP_ERR_INVALID_ARG, "lane_target must be in [0, 64]");
-  if (p.persistent < -1 || p.persistent > 2) return fail(LP_ERR_INVALID_ARG, "persistent must be -1, 0, 1 or 2");
+  if (p.persistent < -1 || p.persistent > 3) return fail(LP_ERR_INVALID_ARG, "persistent must be -1, 0, 1, 2 or 3");
   if (p.precision < 0 || p.precision > 2) return fail(LP_ERR_INVALID_ARG, "precision must be 0, 1 or 2");
   if (!(p.switch_tol >= 0.0)) return fail(LP_ERR_INVALID_ARG, "switch_tol must be >= 0");
   if (p.fp32_patience < 0) return fail(LP_ERR_INVALID_ARG, "fp32_patience must be >= 0");

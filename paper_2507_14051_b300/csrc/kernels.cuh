@@ -81,6 +81,60 @@ struct IterKernels {
 };
 template <class V>
 IterKernels<V> iter_kernels();  // instantiated for double and float in iterate.cu
+
+// smem_loop.cu: the loop kernel as one thread-block cluster that holds the whole LP in its CTAs'
+// shared memory.  CTA q owns rows [rs[q], rs[q + 1]) and columns [cs[q], cs[q + 1]) of the
+// solver's (permuted) index space.
+constexpr int kSmMaxCtas = 16;
+struct SmSplit {
+  int32_t rs[kSmMaxCtas + 1];
+  int32_t cs[kSmMaxCtas + 1];
+  int32_t smem_bytes;  // dynamic shared memory per CTA of the launch
+};
+
+// Byte offsets of one CTA's arrays in its dynamic shared memory (each start 16-byte aligned):
+// the table of partial sums (two buffers of kSmMaxCtas x kNumSums doubles), the replicas of
+// the gathered vectors (xbar, xhat in two buffers, n each; qy, yhat, m each), the CTA's rows of
+// A (mr + 1 local offsets, nzr indices and values) with its row-slice vectors, and its rows of
+// A^T (nc + 1 offsets, nzc entries) with its column-slice vectors.  vb: bytes per value.
+struct SmLayout {
+  uint32_t part, xbar, xh0, xh1, qy, yh;
+  uint32_t rp, ci, val, y0, w, ax0, axh, ax, lc, uc, inv_dr;
+  uint32_t rpT, ciT, valT, x0, aty0, aty, c, lv, uv, inv_dc;
+  uint64_t total;  // bytes (the offsets are meaningful only when total fits the launch)
+};
+__host__ __device__ inline uint32_t sm_take(uint64_t& o, uint64_t bytes) {
+  const uint64_t at = o;
+  o += (bytes + 15u) & ~uint64_t(15);
+  return (uint32_t)at;
+}
+__host__ __device__ inline SmLayout sm_layout(int64_t m, int64_t n, int64_t mr, int64_t nc, int64_t nzr,
+                                              int64_t nzc, int vb) {
+  SmLayout L;
+  uint64_t o = 0;
+  L.part = sm_take(o, (uint64_t)2 * kSmMaxCtas * kNumSums * 8);
+  L.xbar = sm_take(o, n * vb);
+  L.xh0 = sm_take(o, n * vb);
+  L.xh1 = sm_take(o, n * vb);
+  L.qy = sm_take(o, m * vb);
+  L.yh = sm_take(o, m * vb);
+  L.rp = sm_take(o, (mr + 1) * 4);
+  L.ci = sm_take(o, nzr * 4);
+  L.val = sm_take(o, nzr * vb);
+  uint32_t* rowv[8] = {&L.y0, &L.w, &L.ax0, &L.axh, &L.ax, &L.lc, &L.uc, &L.inv_dr};
+  for (uint32_t* f : rowv) *f = sm_take(o, mr * vb);
+  L.rpT = sm_take(o, (nc + 1) * 4);
+  L.ciT = sm_take(o, nzc * 4);
+  L.valT = sm_take(o, nzc * vb);
+  uint32_t* colv[7] = {&L.x0, &L.aty0, &L.aty, &L.c, &L.lv, &L.uv, &L.inv_dc};
+  for (uint32_t* f : colv) *f = sm_take(o, nc * vb);
+  L.total = o;
+  return L;
+}
+template <class V>
+using SmLoopFn = void (*)(RowArgsT<V>, ColArgsT<V>, SmSplit, int32_t, cudaGraphConditionalHandle, int32_t);
+template <class V>
+SmLoopFn<V> sm_loop_kernel();  // instantiated for double and float in smem_loop.cu
 __global__ void k_init_ctl(Ctl* dst, Ctl src);
 __global__ void k_set_cond(cudaGraphConditionalHandle h, Ctl* ctl, int32_t unroll);
 __global__ void k_unpermute_scale(int32_t len, const int32_t* perm, const double* v,

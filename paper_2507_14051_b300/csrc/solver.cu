@@ -51,6 +51,12 @@ struct lp_solver {
   int cluster_max = 0;       // the largest cluster the loop kernels can be launched as (16 or 8)
   bool small = false;        // each phase has at most kClusterTasks tasks
   bool loop_fits = false;    // both phases' grids fit on the device at once
+  // the shared-memory cluster loop (smem_loop.cu): CTAs (0: the LP does not fit, driver not
+  // offered), row / column slices, dynamic shared memory per CTA for FP64 [0] and FP32 [1]
+  int sm_ctas = 0;
+  SmSplit sm_split{};
+  int32_t sm_bytes[2] = {0, 0};
+  bool sm_active = false;  // the graph body is the shared-memory cluster loop
   int tile_rows_used = 1;    // rows per tile of the bins (lp_params.tile_rows, or the automatic choice)
   // device storage
   int32_t *rpA = nullptr, *ciA = nullptr, *rpT = nullptr, *ciT = nullptr;
@@ -255,6 +261,21 @@ cudaError_t launch_loop(const lp_solver* h, const RowArgsT<V>& ra, const ColArgs
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[2];
+  if (h->sm_active) {
+    SmSplit sp = h->sm_split;
+    sp.smem_bytes = h->sm_bytes[sizeof(V) == sizeof(float) ? 1 : 0];
+    cfg.gridDim = dim3((unsigned)h->sm_ctas);
+    cfg.dynamicSmemBytes = (size_t)sp.smem_bytes;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)h->sm_ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
+    attr[1].val.clusterSchedulingPolicyPreference = cudaClusterSchedulingPolicySpread;
+    cfg.numAttrs = 2;
+    cfg.attrs = attr;
+    return cudaLaunchKernelEx(&cfg, sm_loop_kernel<V>(), ra, ca, sp, iters, cond, use_cond);
+  }
   if (h->cluster > 0) {
     cfg.gridDim = dim3((unsigned)h->cluster);
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -274,6 +295,89 @@ cudaError_t launch_loop(const lp_solver* h, const RowArgsT<V>& ra, const ColArgs
   const IterKernels<V> k = iter_kernels<V>();
   auto kern = h->cluster > 0 ? (h->refl ? k.loop_refl_one : k.loop_one) : (h->refl ? k.loop_refl : k.loop);
   return cudaLaunchKernelEx(&cfg, kern, ra, ca, h->partials, h->partials2, h->partials3, iters, cond, use_cond);
+}
+
+// Contiguous slices of `rows` rows (offsets rp) for `parts` CTAs, balanced by nonzeros plus
+// kSmRowCost per row (the epilogue's share): bounds[q] = first row of slice q.
+constexpr int64_t kSmRowCost = 12;
+void sm_slices(const std::vector<int32_t>& rp, int parts, int32_t* bounds) {
+  const int64_t rows = (int64_t)rp.size() - 1;
+  const int64_t total = rp[rows] + kSmRowCost * rows;
+  int64_t r = 0;
+  bounds[0] = 0;
+  for (int q = 1; q < parts; ++q) {
+    const int64_t target = total * q / parts;
+    while (r < rows && rp[r] + kSmRowCost * r < target) ++r;
+    bounds[q] = (int32_t)r;
+  }
+  bounds[parts] = (int32_t)rows;
+}
+
+// Longest row (or column) the shared-memory loop takes: it gives each row one thread, whose
+// dependent chain of fmas grows with the row.
+constexpr int32_t kSmMaxLen = 128;
+
+// Sets up the shared-memory cluster loop if the LP fits: the largest cluster (16, else 8) that
+// the kernel can be launched as with the shared memory its slices need, in both precisions the
+// solve uses.  Leaves h->sm_ctas = 0 otherwise.
+void setup_sm_loop(lp_solver* h, const std::vector<int32_t>& rpA, const std::vector<int32_t>& rpT) {
+  h->sm_ctas = 0;
+  if (h->m < 1 || h->n < 1) return;
+  for (size_t i = 0; i + 1 < rpA.size(); ++i)
+    if (rpA[i + 1] - rpA[i] > kSmMaxLen) return;
+  for (size_t j = 0; j + 1 < rpT.size(); ++j)
+    if (rpT[j + 1] - rpT[j] > kSmMaxLen) return;
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const int nprec = h->prm.precision != 0 ? 2 : 1;
+  for (int c : {16, 8}) {
+    SmSplit sp{};
+    sm_slices(rpA, c, sp.rs);
+    sm_slices(rpT, c, sp.cs);
+    int32_t bytes[2] = {0, 0};
+    bool ok = true;
+    for (int pr = 0; pr < nprec && ok; ++pr) {
+      const int vb = pr == 0 ? 8 : 4;
+      uint64_t mx = 0;
+      for (int q = 0; q < c; ++q) {
+        const int32_t a0 = sp.rs[q], a1 = sp.rs[q + 1], b0 = sp.cs[q], b1 = sp.cs[q + 1];
+        const uint64_t t = sm_layout(h->m, h->n, a1 - a0, b1 - b0, rpA[a1] - rpA[a0], rpT[b1] - rpT[b0], vb).total;
+        mx = t > mx ? t : mx;
+      }
+      const void* kern = pr == 0 ? (const void*)sm_loop_kernel<double>() : (const void*)sm_loop_kernel<float>();
+      cudaFuncAttributes fa{};
+      ok = cudaFuncGetAttributes(&fa, kern) == cudaSuccess && mx + fa.sharedSizeBytes <= (uint64_t)optin &&
+           cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx) == cudaSuccess &&
+           (c <= 8 || cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess);
+      if (ok) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)c);
+        cfg.blockDim = dim3((unsigned)kThreads);
+        cfg.dynamicSmemBytes = (size_t)mx;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        ok = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0;
+      }
+      bytes[pr] = (int32_t)mx;
+    }
+    cudaGetLastError();
+    if (ok) {
+      h->sm_ctas = c;
+      h->sm_split = sp;
+      h->sm_bytes[0] = bytes[0];
+      h->sm_bytes[1] = bytes[1];
+      return;
+    }
+  }
 }
 
 // The largest cluster (16, else 8) that every cluster form of the loop kernel can be launched as
@@ -329,7 +433,9 @@ lp_status build_graph_for(lp_solver* h, cudaGraph_t* graph, cudaGraphExec_t* exe
       cudaGraphDestroy(*graph);
       *graph = nullptr;
     }
-    const bool want = h->prm.persistent >= 1 || (h->prm.persistent == -1 && (h->loop_fits || h->cluster > 0));
+    const int pers = h->prm.persistent;
+    const bool want = pers == 1 || pers == 2 || h->sm_active ||
+                      ((pers == -1 || pers == 3) && (h->loop_fits || h->cluster > 0));
     const bool loop = want && attempt == 0;
     RowArgsT<V> ra{};
     ColArgsT<V> ca{};
@@ -375,7 +481,11 @@ lp_status build_graph(lp_solver* h) {
   // the reflected form of the loop kernel needs gamma = 1 (2 zhat - z is then both the Halpern
   // step's reflected point and the extrapolated point of the dual step)
   h->refl = h->prm.gamma == 1.0;
-  const bool want_cluster = h->prm.persistent == 2 || (h->prm.persistent == -1 && h->small);
+  // the shared-memory cluster loop (reflected form only) whenever the LP fits it, for
+  // persistent 3 or -1; persistent 3 on an LP that does not fit takes the choice of -1
+  h->sm_active = h->refl && h->sm_ctas > 0 && (h->prm.persistent == 3 || h->prm.persistent == -1);
+  const bool want_cluster =
+      !h->sm_active && (h->prm.persistent == 2 || ((h->prm.persistent == -1 || h->prm.persistent == 3) && h->small));
   h->cluster = want_cluster ? h->cluster_max : 0;
   lp_status st = build_graph_for<double>(h, &h->graph, &h->exec, &h->loop_active);
   if (st != LP_OK) return st;
@@ -569,6 +679,7 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
     if (h->prm.precision != 0) max_loop_cluster<float>(best);
     h->cluster_max = best;
   }
+  setup_sm_loop(h, rpA, rpT);
   if (h->gridL > occL * h->num_sms) h->gridL = occL * h->num_sms;  // all blocks co-resident
   if (h->prm.precision != 0) {
     // the FP32 loop kernel has fewer registers (4 blocks per SM): its own grid, sized the same way
@@ -1032,7 +1143,7 @@ lp_status lp_get_info(lp_handle h, double* out9) {
   out7[4] = (double)h->pw_iters;
   out7[5] = ctl.kkt[4];
   out7[6] = ctl.kkt[5];
-  out8[7] = h->loop_active ? (h->cluster > 0 ? 2.0 : 1.0) : 0.0;
+  out8[7] = h->loop_active ? (h->sm_active ? 3.0 : (h->cluster > 0 ? 2.0 : 1.0)) : 0.0;
   out9[8] = h->prm.precision == 1 ? (double)ctl.iters32 : (h->prm.precision == 2 ? (double)ctl.iters : 0.0);
   return LP_OK;
 }

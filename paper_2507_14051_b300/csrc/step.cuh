@@ -12,10 +12,14 @@ __device__ __forceinline__ bool is_check(const Ctl& c, int64_t t) {
 }
 
 // Restart test, Section 3: (1) r <= b_s r0; (2) r <= b_n r0 and r > r_prev; (3) k >= b_a T.
-__device__ __forceinline__ int restart_test(const Ctl& c, int64_t k, int64_t t, double r) {
+// Taken on squared residuals (r, r0, r_prev >= 0, so r <= b r0 <=> r^2 <= b^2 r0^2): r2 = r^2,
+// and c.r0, c.r_prev hold r0^2 and r_prev^2.  An FP64 square root is a ~900-cycle dependent
+// chain on this GPU, on the serial control path of every iteration; the squares need none.
+__device__ __forceinline__ int restart_test(const Ctl& c, int64_t k, int64_t t, double r2) {
   if (k < 1) return 0;
-  if (r <= c.beta_s * c.r0) return 1;
-  if (r <= c.beta_n * c.r0 && r > c.r_prev) return 1;
+  const double bs2 = c.beta_s * c.beta_s, bn2 = c.beta_n * c.beta_n;  // independent of r2
+  if (r2 <= bs2 * c.r0) return 1;
+  if (r2 <= bn2 * c.r0 && r2 > c.r_prev) return 1;
   if ((double)k >= c.beta_a * (double)(t + 1)) return 1;
   return 0;
 }
@@ -199,10 +203,10 @@ __device__ __forceinline__ int row_decide(Ctl& c, const double (&tot)[kNumSums],
                                           const Halpern* next = nullptr, double cross = 2.0) {
   const int64_t t = c.t;
   const double om = c.omega;
-  const double r2 = fma(c.w_over_eta, c.sxx, fma(c.inv_eta_w, tot[0], cross * tot[1]));
-  const double r = sqrt(r2 > 0.0 ? r2 : 0.0);
+  const double r2raw = fma(c.w_over_eta, c.sxx, fma(c.inv_eta_w, tot[0], cross * tot[1]));
+  const double r2 = r2raw > 0.0 ? r2raw : 0.0;  // r_t^2 (the test and the state use squares)
   const int64_t k = c.k;
-  if (k == 0) c.r0 = r;
+  if (k == 0) c.r0 = r2;
   if (check) {
     c.pres2 = tot[3];
     c.dobj_y = tot[4];
@@ -211,18 +215,18 @@ __device__ __forceinline__ int row_decide(Ctl& c, const double (&tot)[kNumSums],
   c.restarts_used = c.restarts;
   const bool tr = trace != nullptr && t < c.trace_cap;
   if (tr) {
-    trace[4 * t + 0] = r;
+    trace[4 * t + 0] = sqrt(r2);
     trace[4 * t + 1] = om;
     trace[4 * t + 2] = 0.0;
     trace[4 * t + 3] = (double)k;
   }
-  if (!isfinite(r2)) {
+  if (!isfinite(r2raw)) {
     c.status = kNumerical;
     c.iters = t + 1;
     c.done = 1;
     return -1;
   }
-  const int rs = c.restart_enabled && (t + 1 < c.max_iter) ? restart_test(c, k, t, r) : 0;
+  const int rs = c.restart_enabled && (t + 1 < c.max_iter) ? restart_test(c, k, t, r2) : 0;
   if (rs) {
     c.k = 0;
     c.restarts += 1;
@@ -232,7 +236,7 @@ __device__ __forceinline__ int row_decide(Ctl& c, const double (&tot)[kNumSums],
     c.ha = h.ha;
     c.hb = h.hb;
     c.he = h.he;
-    c.r_prev = r;
+    c.r_prev = r2;
     c.k = k + 1;
   }
   c.restart = rs;
@@ -406,11 +410,13 @@ struct RowStepR {
   V lam, mu, sigma, inv_sigma;
 };
 
+// check: whether iteration c.t is a check iteration, if the caller has it (-1: computed here;
+// the test takes a 64-bit remainder, a long chain on the serial control path).
 template <class V>
-__device__ __forceinline__ RowStepR<V> row_step_r(const Ctl& c) {
+__device__ __forceinline__ RowStepR<V> row_step_r(const Ctl& c, int check = -1) {
   RowStepR<V> st;
   st.mode = (c.t == 0) ? 2 : c.restart;
-  st.check = is_check(c, c.t) ? 1 : 0;
+  st.check = check >= 0 ? check : (is_check(c, c.t) ? 1 : 0);
   st.cand = c.cand_slot;
   st.lam = (V)(-c.hb);  // gamma = 1: hb = -lam
   st.mu = (V)c.he;
@@ -482,10 +488,10 @@ struct ColStepR {
 };
 
 template <class V>
-__device__ __forceinline__ ColStepR<V> col_step_r(const Ctl& c, const ColArgsT<V>& a) {
+__device__ __forceinline__ ColStepR<V> col_step_r(const Ctl& c, const ColArgsT<V>& a, int check = -1) {
   ColStepR<V> st;
   st.restart = c.restart;
-  st.check = is_check(c, c.t) ? 1 : 0;
+  st.check = check >= 0 ? check : (is_check(c, c.t) ? 1 : 0);
   st.cand = c.cand_slot;
   st.lam = (V)(-c.hb);
   st.mu = (V)c.he;

@@ -118,7 +118,7 @@ def test_create_rejects_invalid_arguments():
     assert L.lp_create(lp.m, lp.n, lp.nnz, None, *ptrs[1:], 0, None, C.byref(h)) == lpx.LP_ERR_INVALID_ARG
     assert L.lp_create(lp.m, lp.n, 1 << 31, *ptrs, 0, None, C.byref(h)) == lpx.LP_ERR_TOO_LARGE
     for field, value in (("gamma", 1.5), ("check_every", 0), ("unroll", 0), ("omega0", -1.0),
-                         ("lane_target", -1), ("lane_target", 65), ("pc_alpha", 3.0), ("persistent", 3)):
+                         ("lane_target", -1), ("lane_target", 65), ("pc_alpha", 3.0), ("persistent", 4)):
         p = lpx.lp_default_params(**{field: value})
         with pytest.raises(lpx.LPError) as e:
             _create(lp, arrs, params=p)

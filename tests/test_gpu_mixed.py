@@ -37,11 +37,12 @@ def max_len(lp):
     return int(max(rows, cols))
 
 
-@pytest.mark.parametrize("persistent", [-1, 1])
+@pytest.mark.parametrize("persistent", [-1, 1, 2])
 @pytest.mark.parametrize("seed", range(4))
 @pytest.mark.parametrize("iters", [1, 64, 400])
 def test_fp32_fixed_map_error_bound(cuda_device, seed, iters, persistent):
-    """persistent -1 runs these small LPs on the cluster loop, 1 on the grid-wide loop."""
+    """persistent -1 runs these small LPs on the shared-memory cluster loop, 1 on the grid-wide
+    loop, 2 on the cluster loop."""
     lp = gen.small_lp(seed)
     kw = dict(restart_enabled=0, pid_enabled=0, **NO_SCALING)
     eta = oracle.solve(lp, tol=0.0, max_iter=1, **kw)["eta"]

@@ -206,7 +206,9 @@ def test_small_lp_iterates(cuda_device, seed, iters):
                                      dict(persistent=0), dict(persistent=0, check_every=5, unroll=2),
                                      dict(persistent=1, unroll=5), dict(tile_rows=32), dict(tile_rows=4, lane_target=2),
                                      dict(tile_rows=32, persistent=0), dict(persistent=2), dict(persistent=2, gamma=0.5),
-                                     dict(persistent=2, check_every=1, unroll=3), dict(persistent=2, tile_rows=32)])
+                                     dict(persistent=2, check_every=1, unroll=3), dict(persistent=2, tile_rows=32),
+                                     dict(persistent=3, check_every=1, unroll=3), dict(persistent=3, pid_enabled=0),
+                                     dict(persistent=3, restart_enabled=0, unroll=64), dict(persistent=3, gamma=0.5)])
 def test_variants_iterates(cuda_device, variant):
     compare_fixed(gen.free_and_boxed_mix(3, 300, 450), 400, **variant)
 
@@ -273,7 +275,7 @@ def test_single_iteration_and_degenerate_shapes(cuda_device):
     compare_fixed(gen.ragged_rows(9, 64, 5000), 150)
 
 
-@pytest.mark.parametrize("persistent", [1, 0, 2])
+@pytest.mark.parametrize("persistent", [1, 0, 2, 3])
 def test_deterministic_and_reusable(cuda_device, persistent):
     lp = gen.miplib_like(4, 3000, 6000, 2000)
     with lpx.Solver(lp, persistent=persistent) as s:
@@ -298,17 +300,19 @@ def test_both_drivers_agree(cuda_device):
 
 @pytest.mark.parametrize("gamma", [1.0, 0.5])
 def test_three_drivers_agree_on_a_small_lp(cuda_device, gamma):
-    """The small LP (200 x 500) picks the one-block loop kernel by itself (persistent -1 -> 2,
-    reported as 2 in lp_get_info); the grid-wide loop kernel (1) and one kernel per phase (0)
-    run the same iteration.  With gamma = 1 the loop kernels run the reflected form, the split
-    kernels the plain one."""
+    """The small LP (200 x 500) picks by itself the shared-memory cluster loop (persistent
+    -1 -> 3, reported as 3 in lp_get_info) with gamma = 1, the cluster loop (2) otherwise; the
+    cluster loop, the grid-wide loop kernel (1) and one kernel per phase (0) run the same
+    iteration.  With gamma = 1 the loop kernels run the reflected form, the split kernels the
+    plain one."""
     lp = gen.small_lp(2)
     eta = oracle_eta(lp)
     with lpx.Solver(lp, eta=eta, gamma=gamma) as s:
         auto = s.solve(0.0, 500).result()
         info = lpx.lp_get_info(s.h)
-    assert info[7] == 2.0
-    runs = {p: gpu_solve(lp, 0.0, 500, eta=eta, gamma=gamma, persistent=p) for p in (0, 1, 2)}
+    want = 3 if gamma == 1.0 else 2
+    assert info[7] == float(want)
+    runs = {p: gpu_solve(lp, 0.0, 500, eta=eta, gamma=gamma, persistent=p) for p in (0, 1, 2, 3)}
     o = oracle_solve(lp, 0.0, 500, eta=eta, gamma=gamma, trace=True)
     tie = first_near_tie(o["trace"])
     rtol = RTOL_ITER if tie is None else 1e-6
@@ -317,7 +321,42 @@ def test_three_drivers_agree_on_a_small_lp(cuda_device, gamma):
     for p, g in runs.items():
         assert_iterates_close(g["x"], o["x"], rtol=rtol)
         assert_iterates_close(g["y"], o["y"], rtol=rtol)
-    assert np.array_equal(auto["x"], runs[2]["x"]) and np.array_equal(auto["y"], runs[2]["y"])
+    assert np.array_equal(auto["x"], runs[want]["x"]) and np.array_equal(auto["y"], runs[want]["y"])
+
+
+def test_shared_memory_loop_applies_only_where_it_fits(cuda_device):
+    """persistent 3 runs the shared-memory cluster loop on an LP that fits it (every row and
+    column at most 128 entries); on one with a 2,000-entry row it chooses as -1 does, with the
+    same iterates."""
+    small = gen.small_lp(4)
+    with lpx.Solver(small, persistent=3) as s:
+        s.solve(0.0, 50).result()
+        assert lpx.lp_get_info(s.h)[7] == 3.0
+    big = gen.miplib_like(6, 3000, 6000, 2000)
+    eta = oracle_eta(big)
+    with lpx.Solver(big, persistent=3, eta=eta) as s:
+        a = s.solve(0.0, 200).result()
+        info3 = lpx.lp_get_info(s.h)[7]
+    with lpx.Solver(big, persistent=-1, eta=eta) as s:
+        b = s.solve(0.0, 200).result()
+        info_auto = lpx.lp_get_info(s.h)[7]
+    assert info3 == info_auto and info3 != 3.0
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["y"], b["y"])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_shared_memory_loop_deterministic_and_reusable(cuda_device, seed):
+    """Two solves on one handle of the shared-memory cluster loop give the same bits (its sums
+    have a fixed order), and a solve continued over several launches (unroll 7) matches the
+    oracle like the one-launch solves do."""
+    lp = gen.small_lp(seed)
+    with lpx.Solver(lp, persistent=3) as s:
+        a = s.solve(0.0, 700).result()
+        b = s.solve(0.0, 700).result()
+        assert lpx.lp_get_info(s.h)[7] == 3.0
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["y"], b["y"])
+    assert a["iters"] == b["iters"] == 700
+    compare_fixed(lp, 300, persistent=3, unroll=7)
 
 
 def test_device_inputs_equal_host_inputs(cuda_device):
