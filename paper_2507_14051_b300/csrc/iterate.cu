@@ -139,7 +139,14 @@ __global__ void __launch_bounds__(kThreads, 4)
   __shared__ ColStepR<V> cstr;
   __shared__ Halpern hw;
   __shared__ int rs;
-  if (threadIdx.x == 0) sc = *ra.ctl;
+  // whether iterations t and t + 1 are check iterations (reflected form): the 64-bit remainder
+  // of the test is computed by the last warp while the row totals are added, not by thread 0 on
+  // the serial path at the start of each phase
+  __shared__ int chk_cur, chk_nxt;
+  if (threadIdx.x == 0) {
+    sc = *ra.ctl;
+    chk_cur = is_check(sc, sc.t) ? 1 : 0;
+  }
   __syncthreads();
   const LoadPolicy pol = make_policy();
   double* trace = blockIdx.x == 0 ? ra.trace : nullptr;
@@ -148,7 +155,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
     int check;
     if constexpr (kRefl) {
-      if (threadIdx.x == 0) rstr = row_step_r<V>(sc);
+      if (threadIdx.x == 0) rstr = row_step_r<V>(sc, chk_cur);
       __syncthreads();
       const RowStepR<V> st = rstr;
       check = st.check;
@@ -189,7 +196,10 @@ __global__ void __launch_bounds__(kThreads, 4)
     phase_sync();
     // the last warp is idle while warps 0..nr-1 add the totals: it computes the next Halpern
     // weights (two FP64 divisions) so that the serial control does not
-    if (threadIdx.x == kThreads - 32) hw = halpern_weights(sc.k, sc.gamma);
+    if (threadIdx.x == kThreads - 32) {
+      hw = halpern_weights(sc.k, sc.gamma);
+      chk_nxt = is_check(sc, sc.t + 1) ? 1 : 0;
+    }
     double tot[kNumSums];
     block_totals(part_rows, gridDim.x, nr, &ra.bins, tot);
     if (threadIdx.x == 0) rs = row_decide(sc, tot, check, trace, &hw, kRefl ? 1.0 : 2.0);
@@ -225,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     // ---- column phase
     double s2[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if constexpr (kRefl) {
-      if (threadIdx.x == 0) cstr = col_step_r(sc, ca);
+      if (threadIdx.x == 0) cstr = col_step_r(sc, ca, chk_cur);
       __syncthreads();
       const ColStepR<V> cs = cstr;
       check = cs.check;
@@ -265,7 +275,10 @@ __global__ void __launch_bounds__(kThreads, 4)
     phase_sync();
     double tot2[kNumSums];
     block_totals(part_cols, gridDim.x, nc, &ca.bins, tot2);
-    if (threadIdx.x == 0) col_control(sc, tot2, check);
+    if (threadIdx.x == 0) {
+      col_control(sc, tot2, check);
+      chk_cur = chk_nxt;
+    }
     __syncthreads();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
