@@ -161,6 +161,10 @@ def design_bytes(lp, vb=8, refl=False):
     return rows + cols
 
 
+DRIVERS = {0: "one kernel per phase", 1: "cooperative loop kernel", 2: "cluster loop kernel",
+           3: "shared-memory cluster loop kernel"}
+
+
 def source_digest(kernel: str | None = None) -> str:
     """sha256 prefix of the kernel's sources (TRAFFIC_SOURCES; every CUDA source if None)."""
     files = KERNEL_SOURCES if kernel is None else TRAFFIC_SOURCES[kernel.split("<")[0]]
@@ -180,6 +184,8 @@ def measured_traffic(kernel: str, workload: str, iters_per_launch: int):
         with open(path) as f:
             data = json.load(f)
     except (OSError, ValueError):
+        return None
+    if kernel.split("<")[0] not in TRAFFIC_SOURCES:
         return None
     if data.get("source_digests", {}).get(kernel.split("<")[0]) != source_digest(kernel):
         return None
@@ -350,7 +356,8 @@ def run_ours(args):
         solver.solve(args.tol, args.max_iter, sp)
         lpx.lp_get(solver.h)
     torch.cuda.synchronize()
-    persistent = bool(lpx.lp_get_info(solver.h)[7])
+    driver_code = int(lpx.lp_get_info(solver.h)[7])
+    persistent = driver_code != 0
 
     if world > 1:
         dist.barrier()
@@ -411,7 +418,11 @@ def run_ours(args):
     f_hbm = gbs / hbm_peak
     gops = ops / (ms * 1e-3) / 1e9 if ops is not None else None
     f_alu = gops / FP64_MEASURED_GOPS if ops is not None else 0.0
-    kname = dom if vb == 8 else dom + "<float>"
+    if dom == "k_loop" and driver_code == 3:
+        dom_name = "k_loop_sm"  # the shared-memory cluster loop: the LP stays in shared memory
+    else:
+        dom_name = dom
+    kname = dom_name if vb == 8 else dom_name + "<float>"
     traffic = measured_traffic(kname, wl, int(kt[2]))
     if f_alu > f_hbm:
         roof = {"bound": "alu", "achieved": gops, "peak": FP64_MEASURED_GOPS, "unit": "FP64 Gop/s",
@@ -508,7 +519,7 @@ def run_ours(args):
             "time_to_tol_s": (setup_ms / 1e3 + elapsed_s / args.steps) if solved else None,
             "setup_ms": setup_ms, "eta": float(info[0]), "restarts_last": int(info[2]),
             "iters_fp32_last": int(info[8]),
-            "driver": "cooperative loop kernel" if persistent else "one kernel per phase",
+            "driver": DRIVERS[driver_code],
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
