@@ -11,17 +11,17 @@
 //     t & 1, as in global memory) for the row phase, qy and yhat for the column phase.  After a
 //     phase the owner of a row or column writes its new entries into every other CTA's replica
 //     (distributed shared memory);
-//   * each reduction sums the block (block_reduce), writes the block's sums into every CTA's
-//     table of partials (row = the writer's rank; two tables used alternately), passes one
-//     cluster barrier, then adds the table's rows in rank order by a fixed butterfly, so every
-//     CTA runs the same control on the same bits.
+//   * each reduction sums the block (warp butterflies, then the warps in order), writes the
+//     block's sums into every CTA's table of partials (row = the writer's rank; two tables used
+//     alternately), passes one cluster barrier, then adds the table's rows in rank order by a
+//     fixed butterfly, so every CTA runs the same control on the same bits.
 // So a phase costs its shared-memory SpMV and epilogue, one cluster barrier and the control; the
 // only global traffic inside the loop is the trace and the stall guard's slots.  A launch loads
 // the CTA's data from global memory, runs up to `iters` iterations and writes the CTA's rows and
 // columns of the state back.
 //
-// The SpMV gives each row (and column) to one thread, which adds its entries in order: for rows
-// that the binned kernels give one lane each, the same bits as theirs.
+// The SpMV gives each row (and column) up to 8 lanes, each adding its strided entries in order,
+// then a fixed butterfly (sm_rows): deterministic, though not the binned kernels' order.
 #include <cooperative_groups.h>
 
 #include "step.cuh"
