@@ -472,7 +472,9 @@ __global__ void __launch_bounds__(kThreads) kb_warm(BatchArgs<double> d, int64_t
 }
 
 // Loop for the small instances: a cluster of kCtas CTAs (on kCtas SMs) runs every iteration of
-// one instance.  Each CTA takes every kCtas-th of the instance's warp tasks and sums its
+// one instance, then claims the next unclaimed instance of the list (`next`, zeroed before the
+// launch): the instances' iteration counts are unknown and uneven, so a static assignment could
+// queue two long ones on one cluster.  Which cluster runs an instance does not change its bits.  Each CTA takes every kCtas-th of the instance's warp tasks and sums its
 // threads' epilogue sums (block tree); the CTAs' totals meet in distributed shared memory after
 // a cluster barrier, every CTA adds them in rank order and runs the same control on its own
 // shared-memory copy of the scalar state, so all copies agree bit for bit and the CTAs leave
@@ -500,17 +502,29 @@ __device__ __forceinline__ void cluster_totals(const double* part, int nsums, do
 
 template <class V, int kCtas>
 __global__ void __launch_bounds__(kThreads, 2) kb_cluster_loop(BatchArgs<V> a, const int32_t* __restrict__ list,
-                                                               int32_t nlist, int64_t cap) {
+                                                               int32_t nlist, int32_t* next, int64_t cap) {
   __shared__ Ctl sc;
+  __shared__ int32_t claim;  // the list entry this cluster runs next
   __shared__ RowStep rst;
   __shared__ ColStepT<V> cst;
   __shared__ double part[2][kNumSums];  // this CTA's row-phase and column-phase totals
   const LoadPolicy pol = make_policy();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rank = (int)(blockIdx.x % kCtas);
-  const int cid = (int)(blockIdx.x / kCtas), ncl = (int)(gridDim.x / kCtas);
   const int w0 = rank * kWarps + warp, wstep = kCtas * kWarps;
-  for (int q = cid; q < nlist; q += ncl) {
+  for (;;) {
+    // rank 0 claims an entry and hands it to every CTA of the cluster (each CTA finished the
+    // previous instance before the barrier that ended it, so no CTA still reads `claim`)
+    if (rank == 0 && threadIdx.x == 0) {
+      const int32_t q = atomicAdd(next, 1);
+      for (int r = 0; r < kCtas; ++r) {
+        int32_t* dst = kCtas > 1 ? cg::this_cluster().map_shared_rank(&claim, r) : &claim;
+        *dst = q;
+      }
+    }
+    cluster_barrier<kCtas>();
+    const int q = claim;
+    if (q >= nlist) break;
     const int ii = list[q];
     const BInst I = a.inst[ii];
     ctl_load(&sc, a.ctl + ii);
@@ -729,6 +743,9 @@ template <class V, int kCtas>
 cudaError_t launch_cluster_loop(const lp_batch* h, const BatchArgs<V>& a, const int32_t* list, int32_t n,
                                 int64_t cap, cudaStream_t s) {
   const int clusters = std::max(1, std::min(n, 2 * h->num_sms / kCtas));
+  int32_t* next = h->local_next + (kCtas == 1 ? 1 : 0);
+  const cudaError_t e0 = cudaMemsetAsync(next, 0, sizeof(int32_t), s);
+  if (e0 != cudaSuccess) return e0;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(clusters * kCtas));
   cfg.blockDim = dim3((unsigned)kThreads);
@@ -741,7 +758,7 @@ cudaError_t launch_cluster_loop(const lp_batch* h, const BatchArgs<V>& a, const 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kb_cluster_loop<V, kCtas>, a, list, n, cap);
+  return cudaLaunchKernelEx(&cfg, kb_cluster_loop<V, kCtas>, a, list, n, next, cap);
 }
 
 // The clustered small instances on clusters of k CTAs (8, 4 or 2).
@@ -987,6 +1004,7 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
   CK(cudaMemcpy(h->d_inst, h->inst.data(), sizeof(BInst) * K, cudaMemcpyHostToDevice));
   h->local_host = local;
   CK(h->alloc(&h->local_list, local.size()));
+  CK(h->alloc(&h->local_next, 2));
   if (!local.empty()) CK(cudaMemcpy(h->local_list, local.data(), sizeof(int32_t) * local.size(), cudaMemcpyHostToDevice));
 
   // ---- pass 2 (host threads): permuted CSR of A and A^T with global indices, upload ----

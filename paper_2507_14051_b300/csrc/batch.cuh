@@ -152,6 +152,7 @@ struct lp_batch {
   cudaStream_t side_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int32_t* local_list = nullptr;  // device: the small instances (cluster loop)
+  int32_t* local_next = nullptr;  // device: next unclaimed entry of the wide [0] and tiny [1] lists
   std::vector<int32_t> local_host;  // host copy of local_list
   int grid = 1, grid32 = 1, gridS = 1;  // loop grids (FP64, FP32), block-per-instance grid
   bool solved = false;
