@@ -42,6 +42,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "smem_loop.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -372,11 +373,14 @@ __global__ void __launch_bounds__(kThreads) kb_init(BatchArgs<V> a) {
       a.ra.ax[i] = V(0);
       a.ra.ax0[i] = V(0);
       a.ra.axh[i] = V(0);
+      a.ra.qy[i] = V(0);
+      a.ra.w[i] = V(0);
     }
     double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int j = I.col0 + threadIdx.x; j < I.col0 + I.n; j += kThreads) {
       const V xn = clampd(-tau * a.ca.c[j], a.ca.lv[j], a.ca.uv[j]);
       a.ca.xh0[j] = xn;
+      a.ca.xbar[j] = V(2) * xn;  // 2 xhat_0 - x_0 (x_0 = 0), for the shared-memory loop
       a.ca.x[j] = V(0);
       a.ca.x0[j] = V(0);
       a.ca.aty[j] = V(0);
@@ -451,6 +455,7 @@ __global__ void __launch_bounds__(kThreads) kb_warm(BatchArgs<double> d, int64_t
       const double xj = d.ca.x[j], atyj = d.ca.aty[j];
       const double xn = clampd(fma(-tau, d.ca.c[j] - atyj, xj), d.ca.lv[j], d.ca.uv[j]);
       xh[j] = xn;
+      d.ca.xbar[j] = fma(2.0, xn, -xj);  // for the shared-memory loop (reflected form)
       d.ca.aty0[j] = atyj;
       const double df = xj - xn;
       s[0] = fma(df, df, s[0]);
@@ -585,6 +590,87 @@ __global__ void __launch_bounds__(kThreads, 2) kb_cluster_loop(BatchArgs<V> a, c
     __syncthreads();
     if (rank == 0) ctl_load(a.ctl + ii, &sc);
     cluster_barrier<kCtas>();  // every CTA has read this instance's totals before the next one
+  }
+}
+
+// The small instances in shared memory: a cluster of sm_ctas CTAs claims an entry of the list
+// (`next`, zeroed before the launch), runs its instance to the end with sm_run (the single-LP
+// shared-memory loop, reflected form) from its current state, writes the instance's scalar
+// state back and claims the next entry.  splits[q]: the row / column split of entry q.  An
+// instance's bits do not depend on which cluster runs it.  A split that does not fit, or an
+// instance the control did not end within `cap` iterations, ends with an internal error.
+template <class V>
+__global__ void __launch_bounds__(kThreads, 1)
+    kb_sm_loop(BatchArgs<V> a, const int32_t* __restrict__ list, int32_t nlist, int32_t* next,
+               const SmSplit* __restrict__ splits, int32_t smem_bytes, int64_t cap) {
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Ctl sc;
+  __shared__ int32_t claim;
+  const int rank = (int)cl.block_rank(), nct = (int)cl.num_blocks();
+  const int32_t iters = cap > (int64_t)0x7fffffff ? 0x7fffffff : (int32_t)cap;
+  for (;;) {
+    // every CTA finished the previous instance before the barrier that ended it
+    if (rank == 0 && threadIdx.x == 0) {
+      const int32_t q = atomicAdd(next, 1);
+      for (int r = 0; r < nct; ++r) *cl.map_shared_rank(&claim, (unsigned)r) = q;
+    }
+    cl.sync();
+    const int q = claim;
+    if (q >= nlist) break;
+    const int ii = list[q];
+    const BInst I = a.inst[ii];
+    if (threadIdx.x == 0) sc = a.ctl[ii];
+    __syncthreads();
+    if (!sc.done) {  // the same in every CTA
+      RowArgsT<V> ra = a.ra;
+      ColArgsT<V> ca = a.ca;
+      const int r0 = I.row0, c0 = I.col0;
+      ra.rp += r0;
+      ra.xh0 += c0;
+      ra.xh1 += c0;
+      ra.y += r0;
+      ra.y0 += r0;
+      ra.yh += r0;
+      ra.ax += r0;
+      ra.ax0 += r0;
+      ra.axh += r0;
+      ra.lc += r0;
+      ra.uc += r0;
+      ra.inv_dr += r0;
+      if (ra.yb0) ra.yb0 += r0;
+      if (ra.yb1) ra.yb1 += r0;
+      ra.qy += r0;
+      ra.w += r0;
+      ra.xbar += c0;
+      ra.m = I.m;
+      ca.rp += c0;
+      ca.yh += r0;
+      ca.xh0 += c0;
+      ca.xh1 += c0;
+      ca.x += c0;
+      ca.x0 += c0;
+      ca.aty += c0;
+      ca.aty0 += c0;
+      ca.c += c0;
+      ca.lv += c0;
+      ca.uv += c0;
+      ca.inv_dc += c0;
+      if (ca.xb0) ca.xb0 += c0;
+      if (ca.xb1) ca.xb1 += c0;
+      ca.xbar += c0;
+      ca.qy += r0;
+      ca.n = I.n;
+      const bool ok = sm_run<V>(cl, smem, smem_bytes, sc, ra, ca, splits[q], r0, c0, iters, trace_of(a, ii));
+      if (threadIdx.x == 0 && (!ok || !sc.done)) {
+        sc.status = kInternalError;
+        sc.iters = ok ? sc.t + 1 : sc.t;
+        sc.done = 1;
+      }
+    }
+    __syncthreads();
+    if (rank == 0 && threadIdx.x == 0) a.ctl[ii] = sc;
+    cl.sync();
   }
 }
 
@@ -769,6 +855,35 @@ cudaError_t launch_wide(const lp_batch* h, const BatchArgs<V>& a, int k, int64_t
   return launch_cluster_loop<V, kLocalCtas>(h, a, h->local_list, h->n_wide, cap, s);
 }
 
+// The small instances on the shared-memory loop: as many clusters of sm_ctas CTAs as fit on the
+// device at once, each claiming instances until the list is done.
+template <class V>
+cudaError_t launch_sm_loop(const lp_batch* h, const BatchArgs<V>& a, int64_t cap, cudaStream_t s) {
+  const int C = h->sm_ctas;
+  const int32_t bytes = h->sm_bytes[sizeof(V) == sizeof(float) ? 1 : 0];
+  cudaLaunchConfig_t cfg{};
+  cfg.blockDim = dim3((unsigned)kThreads);
+  cfg.dynamicSmemBytes = (size_t)bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((unsigned)C);
+  int fit = 0;
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&fit, kb_sm_loop<V>, &cfg);
+  if (e != cudaSuccess) return e;
+  const int clusters = std::max(1, std::min(h->n_local, fit));
+  cfg.gridDim = dim3((unsigned)(clusters * C));
+  e = cudaMemsetAsync(h->local_next, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchKernelEx(&cfg, kb_sm_loop<V>, a, (const int32_t*)h->local_list, h->n_local, h->local_next,
+                            (const SmSplit*)h->d_splits, bytes, cap);
+}
+
 // one_wave: clusters of the most CTAs (8, 4, 2) with which every clustered instance has its own
 // cluster at once.  A solve to tolerance keeps 8 (its small stragglers run longest, so each
 // instance's own speed decides); the schedule solve of the differentiable map runs exactly K
@@ -776,6 +891,9 @@ cudaError_t launch_wide(const lp_batch* h, const BatchArgs<V>& a, int k, int64_t
 template <class V>
 cudaError_t launch_local(const lp_batch* h, const BatchArgs<V>& a, int64_t cap, cudaStream_t s,
                          bool one_wave = false) {
+  // a solve runs the small instances in shared memory when they fit; the schedule solve of the
+  // differentiable map keeps the plain-form loops, whose schedule its adjoint replays
+  if (h->sm_ctas > 0 && !one_wave) return launch_sm_loop<V>(h, a, cap, s);
   const int32_t n_tiny = h->n_local - h->n_wide;
   int k = kLocalCtas;
   if (one_wave)
@@ -874,6 +992,81 @@ lp_status batch_power_iteration(lp_batch* h) {
   for (int32_t k = 0; k < h->count; ++k) {
     const double nrm = std::sqrt(pw[k].lam);
     h->eta[k] = nrm > 0.0 ? 0.998 / nrm : 1.0;
+  }
+  return LP_OK;
+}
+
+// Sets up the shared-memory loop for the small instances (`local`, with their host build data B)
+// if every one of them fits it (gamma = 1, the reflected form; no row or column longer than
+// kSmMaxLen; each CTA's slices and replicas within its shared memory): the smallest cluster
+// (4, 8 or 16 CTAs) that takes them all, their splits uploaded in list order.  Leaves
+// h->sm_ctas = 0 (the cluster and single-CTA loops) otherwise.
+lp_status setup_batch_sm(lp_batch* h, const std::vector<Built>& B, const std::vector<int32_t>& local) {
+  h->sm_ctas = 0;
+  if (local.empty() || h->prm.gamma != 1.0) return LP_OK;
+  for (int32_t k : local) {
+    const Built& b = B[k];
+    for (size_t i = 0; i + 1 < b.rlen_perm.size(); ++i)
+      if (b.rlen_perm[i + 1] - b.rlen_perm[i] > kSmMaxLen) return LP_OK;
+    for (size_t j = 0; j + 1 < b.clen_perm.size(); ++j)
+      if (b.clen_perm[j + 1] - b.clen_perm[j] > kSmMaxLen) return LP_OK;
+  }
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    return LP_OK;
+  }
+  const int nprec = h->prm.precision != 0 ? 2 : 1;
+  std::vector<SmSplit> sp(local.size());
+  for (int C : {4, 8, 16}) {
+    uint64_t mx[2] = {0, 0};
+    for (size_t q = 0; q < local.size(); ++q) {
+      const Built& b = B[local[q]];
+      SmSplit& s = sp[q];
+      s = SmSplit{};
+      sm_slices(b.rlen_perm, C, s.rs);
+      sm_slices(b.clen_perm, C, s.cs);
+      const int64_t mk = (int64_t)b.rlen_perm.size() - 1, nk = (int64_t)b.clen_perm.size() - 1;
+      for (int r = 0; r < C; ++r) {
+        const int32_t a0 = s.rs[r], a1 = s.rs[r + 1], c0 = s.cs[r], c1 = s.cs[r + 1];
+        for (int pr = 0; pr < nprec; ++pr) {
+          const uint64_t t = sm_layout(mk, nk, a1 - a0, c1 - c0, b.rlen_perm[a1] - b.rlen_perm[a0],
+                                       b.clen_perm[c1] - b.clen_perm[c0], pr == 0 ? 8 : 4).total;
+          mx[pr] = t > mx[pr] ? t : mx[pr];
+        }
+      }
+    }
+    bool ok = true;
+    for (int pr = 0; pr < nprec && ok; ++pr) {
+      const void* kern = pr == 0 ? (const void*)kb_sm_loop<double> : (const void*)kb_sm_loop<float>;
+      cudaFuncAttributes fa{};
+      ok = cudaFuncGetAttributes(&fa, kern) == cudaSuccess && mx[pr] + fa.sharedSizeBytes <= (uint64_t)optin &&
+           cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx[pr]) == cudaSuccess &&
+           (C <= 8 || cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess);
+      if (ok) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)C);
+        cfg.blockDim = dim3((unsigned)kThreads);
+        cfg.dynamicSmemBytes = (size_t)mx[pr];
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        ok = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0;
+      }
+    }
+    cudaGetLastError();
+    if (!ok) continue;
+    CK(h->alloc(&h->d_splits, sp.size()));
+    CK(cudaMemcpy(h->d_splits, sp.data(), sizeof(SmSplit) * sp.size(), cudaMemcpyHostToDevice));
+    h->sm_ctas = C;
+    h->sm_bytes[0] = (int32_t)mx[0];
+    h->sm_bytes[1] = (int32_t)mx[1];
+    return LP_OK;
   }
   return LP_OK;
 }
@@ -983,9 +1176,11 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
   CK(h->alloc(&h->rpA, sm + 1)); CK(h->alloc(&h->ciA, snz)); CK(h->alloc(&h->valA, snz));
   CK(h->alloc(&h->rpT, sn + 1)); CK(h->alloc(&h->ciT, snz)); CK(h->alloc(&h->valT, snz));
   CK(h->alloc(&h->row_perm, sm)); CK(h->alloc(&h->col_perm, sn));
-  for (double** p : {&h->c, &h->lv, &h->uv, &h->inv_dc, &h->dc, &h->x, &h->x0, &h->xh0, &h->xh1, &h->aty, &h->aty0})
+  for (double** p : {&h->c, &h->lv, &h->uv, &h->inv_dc, &h->dc, &h->x, &h->x0, &h->xh0, &h->xh1, &h->aty, &h->aty0,
+                     &h->xbar})
     CK(h->alloc(p, sn));
-  for (double** p : {&h->lc, &h->uc, &h->inv_dr, &h->dr, &h->y, &h->y0, &h->yh, &h->ax, &h->ax0, &h->axh})
+  for (double** p : {&h->lc, &h->uc, &h->inv_dr, &h->dr, &h->y, &h->y0, &h->yh, &h->ax, &h->ax0, &h->axh,
+                     &h->qy, &h->w})
     CK(h->alloc(p, sm));
   {
     int64_t mx = 1;
@@ -1112,6 +1307,10 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
   h->grid32 = std::max(1, occ32) * h->num_sms;
   h->gridS = std::max(1, std::min<int>(K, 8 * h->num_sms));
 
+  // ---- the small instances' shared-memory loop ----
+  st = setup_batch_sm(h, B, local);
+  if (st != LP_OK) return st;
+
   // ---- step sizes ----
   h->eta.assign(K, 0.0);
   if (eta) {
@@ -1170,9 +1369,11 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
   if (h->prm.precision != 0) {
     auto& f = h->f32;
     CK(h->alloc(&f.valA, snz)); CK(h->alloc(&f.valT, snz));
-    for (float** q : {&f.c, &f.lv, &f.uv, &f.inv_dc, &f.x, &f.x0, &f.xh0, &f.xh1, &f.aty, &f.aty0, &f.xb0, &f.xb1})
+    for (float** q : {&f.c, &f.lv, &f.uv, &f.inv_dc, &f.x, &f.x0, &f.xh0, &f.xh1, &f.aty, &f.aty0, &f.xb0, &f.xb1,
+                      &f.xbar})
       CK(h->alloc(q, sn));
-    for (float** q : {&f.lc, &f.uc, &f.inv_dr, &f.y, &f.y0, &f.yh, &f.ax, &f.ax0, &f.axh, &f.yb0, &f.yb1})
+    for (float** q : {&f.lc, &f.uc, &f.inv_dr, &f.y, &f.y0, &f.yh, &f.ax, &f.ax0, &f.axh, &f.yb0, &f.yb1,
+                      &f.qy, &f.w})
       CK(h->alloc(q, sm));
     const int g = grid_for(std::max<int64_t>(snz, 1), 256, 8 * h->num_sms);
     k_to_float<<<g, 256, 0, s>>>(snz, h->valA, f.valA);

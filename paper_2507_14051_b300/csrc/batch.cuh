@@ -167,6 +167,9 @@ struct lp_batch {
   double *x = nullptr, *x0 = nullptr, *xh0 = nullptr, *xh1 = nullptr, *aty = nullptr, *aty0 = nullptr;
   double *lc = nullptr, *uc = nullptr, *inv_dr = nullptr, *dr = nullptr;
   double *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
+  // reflected form of the small instances' shared-memory loop: qy = 2 yhat - y, w = A xbar,
+  // xbar = 2 xhat - x
+  double *qy = nullptr, *w = nullptr, *xbar = nullptr;
   double* out_buf = nullptr;
   struct F32 {
     float *valA = nullptr, *valT = nullptr;
@@ -175,7 +178,13 @@ struct lp_batch {
     float *lc = nullptr, *uc = nullptr, *inv_dr = nullptr;
     float *y = nullptr, *y0 = nullptr, *yh = nullptr, *ax = nullptr, *ax0 = nullptr, *axh = nullptr;
     float *xb0 = nullptr, *xb1 = nullptr, *yb0 = nullptr, *yb1 = nullptr;
+    float *qy = nullptr, *w = nullptr, *xbar = nullptr;
   } f32;
+  // the small instances' shared-memory loop (kb_sm_loop): CTAs per cluster (0: not used),
+  // dynamic shared memory per CTA (FP64, FP32), and per entry of local_list its split
+  int sm_ctas = 0;
+  int32_t sm_bytes[2] = {0, 0};
+  SmSplit* d_splits = nullptr;
   int4 *tasksA = nullptr, *tasksT = nullptr;
   BInst* d_inst = nullptr;
   Ctl *ctl = nullptr, *ctl_init = nullptr;
@@ -231,6 +240,7 @@ inline void fill_batch_args<double>(const lp_batch* h, BatchArgs<double>& a) {
   a.ca.xh0 = h->xh0; a.ca.xh1 = h->xh1;
   a.ca.x = h->x; a.ca.x0 = h->x0; a.ca.aty = h->aty; a.ca.aty0 = h->aty0;
   a.ca.c = h->c; a.ca.lv = h->lv; a.ca.uv = h->uv; a.ca.inv_dc = h->inv_dc;
+  a.ra.qy = h->qy; a.ra.w = h->w; a.ra.xbar = h->xbar; a.ca.xbar = h->xbar; a.ca.qy = h->qy;
   a.tasksA = h->tasksA; a.tasksT = h->tasksT; a.inst = h->d_inst; a.count = h->count;
   a.ctl = h->ctl; a.rstep = h->rstep; a.cstep = h->cstep; a.done = h->done;
   a.tpartA = h->tpartA; a.tpartT = h->tpartT; a.bc = h->bc;
@@ -251,6 +261,7 @@ inline void fill_batch_args<float>(const lp_batch* h, BatchArgs<float>& a) {
   a.ca.x = f.x; a.ca.x0 = f.x0; a.ca.aty = f.aty; a.ca.aty0 = f.aty0;
   a.ca.c = f.c; a.ca.lv = f.lv; a.ca.uv = f.uv; a.ca.inv_dc = f.inv_dc;
   a.ca.xb0 = f.xb0; a.ca.xb1 = f.xb1;
+  a.ra.qy = f.qy; a.ra.w = f.w; a.ra.xbar = f.xbar; a.ca.xbar = f.xbar; a.ca.qy = f.qy;
   a.tasksA = h->tasksA; a.tasksT = h->tasksT; a.inst = h->d_inst; a.count = h->count;
   a.ctl = h->ctl; a.rstep = h->rstep; a.cstep = h->cstep; a.done = h->done;
   a.tpartA = h->tpartA; a.tpartT = h->tpartT; a.bc = h->bc;

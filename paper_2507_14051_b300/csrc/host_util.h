@@ -174,4 +174,24 @@ inline double rescale_ratio(const double* c, int64_t n, const double* lc, const 
   return gamma / beta;
 }
 
+// Contiguous slices of `rows` rows (offsets rp) for `parts` CTAs, balanced by nonzeros plus
+// kSmRowCost per row (the epilogue's share): bounds[q] = first row of slice q.
+constexpr int64_t kSmRowCost = 12;
+inline void sm_slices(const std::vector<int32_t>& rp, int parts, int32_t* bounds) {
+  const int64_t rows = (int64_t)rp.size() - 1;
+  const int64_t total = rp[rows] + kSmRowCost * rows;
+  int64_t r = 0;
+  bounds[0] = 0;
+  for (int q = 1; q < parts; ++q) {
+    const int64_t target = total * q / parts;
+    while (r < rows && rp[r] + kSmRowCost * r < target) ++r;
+    bounds[q] = (int32_t)r;
+  }
+  bounds[parts] = (int32_t)rows;
+}
+
+// Longest row (or column) the shared-memory loop takes: a row gets at most 8 lanes, so its
+// chain of dependent fmas grows with its length.
+constexpr int32_t kSmMaxLen = 128;
+
 }  // namespace pdhg_host

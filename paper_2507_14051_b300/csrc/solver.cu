@@ -297,26 +297,6 @@ cudaError_t launch_loop(const lp_solver* h, const RowArgsT<V>& ra, const ColArgs
   return cudaLaunchKernelEx(&cfg, kern, ra, ca, h->partials, h->partials2, h->partials3, iters, cond, use_cond);
 }
 
-// Contiguous slices of `rows` rows (offsets rp) for `parts` CTAs, balanced by nonzeros plus
-// kSmRowCost per row (the epilogue's share): bounds[q] = first row of slice q.
-constexpr int64_t kSmRowCost = 12;
-void sm_slices(const std::vector<int32_t>& rp, int parts, int32_t* bounds) {
-  const int64_t rows = (int64_t)rp.size() - 1;
-  const int64_t total = rp[rows] + kSmRowCost * rows;
-  int64_t r = 0;
-  bounds[0] = 0;
-  for (int q = 1; q < parts; ++q) {
-    const int64_t target = total * q / parts;
-    while (r < rows && rp[r] + kSmRowCost * r < target) ++r;
-    bounds[q] = (int32_t)r;
-  }
-  bounds[parts] = (int32_t)rows;
-}
-
-// Longest row (or column) the shared-memory loop takes: it gives each row one thread, whose
-// dependent chain of fmas grows with the row.
-constexpr int32_t kSmMaxLen = 128;
-
 // Sets up the shared-memory cluster loop if the LP fits: the largest cluster (16, else 8) that
 // the kernel can be launched as with the shared memory its slices need, in both precisions the
 // solve uses.  Leaves h->sm_ctas = 0 otherwise.
