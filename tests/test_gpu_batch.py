@@ -51,24 +51,35 @@ def mixed_shapes():
 @pytest.mark.parametrize("iters", [1, 100, 600])
 @pytest.mark.parametrize("make", [lambda: small_batch(0), mixed_shapes])
 def test_batch_fixed_iterations_match_oracle(cuda_device, make, iters, local):
-    lps = make()
+    check_fixed_iterations(make(), iters, batch_local_nnz=local)
+
+
+@pytest.mark.parametrize("local", [4000, 10 ** 9])
+def test_batch_fixed_iterations_other_gamma(cuda_device, local):
+    """gamma = 0.5: the small instances run on the plain-form cluster and single-CTA loops (the
+    shared-memory loop runs the reflected form, gamma = 1 only)."""
+    check_fixed_iterations(small_batch(3), 300, batch_local_nnz=local, gamma=0.5)
+
+
+def check_fixed_iterations(lps, iters, **params):
     etas = [o_eta(lp) for lp in lps]
     traces, cut = [], []
+    oparams = {k: v for k, v in params.items() if k != "batch_local_nnz"}
     for lp, e in zip(lps, etas):
-        o = o_solve(lp, 0.0, iters, trace=True, eta=e)
+        o = o_solve(lp, 0.0, iters, trace=True, eta=e, **oparams)
         tie = first_near_tie(o["trace"])
         if tie is not None and tie < iters - 1:  # the harness's floor on a cut comparison
             assert tie + 1 >= 0.9 * iters or tie_is_late(o["trace"], tie), (tie, iters)
         cut.append(iters if tie is None or tie >= iters - 1 else tie + 1)
         traces.append(o)
-    with lpx.BatchSolver(lps, eta=etas, batch_local_nnz=local) as b:
+    with lpx.BatchSolver(lps, eta=etas, **params) as b:
         for T in sorted(set(cut)):
             b.solve(0.0, T)
             summ = b.summary()
             for k, lp in enumerate(lps):
                 if cut[k] != T:
                     continue
-                o = traces[k] if T == iters else o_solve(lp, 0.0, T, eta=etas[k])
+                o = traces[k] if T == iters else o_solve(lp, 0.0, T, eta=etas[k], **oparams)
                 g = b.get(k)
                 assert g["status"] == o["status"] == oracle.ITER_LIMIT, k
                 assert g["iters"] == o["iters"] == T, k
