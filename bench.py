@@ -691,10 +691,10 @@ def batch_launches(sm, where, precision):
     """Kernel launches of one lp_batch_solve: kb_init_ctl + kb_init; per stage, one kb_loop
     launch (16 iterations) per body of the graph's while loop -- as many as the stage's slowest
     grid instance needs, plus the body that sees every instance done -- and one launch per kind
-    of small instance (cluster, single block); between the stages of precision 1, kb_switch,
-    two kb_spmv and kb_warm (precision 2: kb_switch alone)."""
+    of small instance (shared-memory cluster loop, or cluster and single block); between the
+    stages of precision 1, kb_switch, two kb_spmv and kb_warm (precision 2: kb_switch alone)."""
     grid = where == 0
-    kinds = int(np.any(where == 1)) + int(np.any(where == 2))
+    kinds = int(np.any(where == 1)) + int(np.any(where == 2)) + int(np.any(where == 3))
     it64 = sm["iters"] - sm["iters_fp32"]
     stages = {0: [sm["iters"]], 1: [sm["iters_fp32"], it64], 2: [sm["iters_fp32"]]}[precision]
     n = 2 + {0: 0, 1: 4, 2: 1}[precision]
@@ -880,7 +880,7 @@ def diff_launches(K, C, where):
     (kd_fwd_loop if any grid instance, kd_fwd_cluster if any small one) + 2 scatters; vjp 2
     gathers + per segment the forward and the adjoint kernels + 3 scatters."""
     nck = -(-K // C)
-    kinds = int(np.any(where == 1)) + int(np.any(where == 2))
+    kinds = int(np.any(where == 1)) + int(np.any(where == 2)) + int(np.any(where == 3))
     grid = -(-K // 16) if np.any(where == 0) else 0
     per = int(np.any(where == 0)) + int(np.any(where != 0))
     return 9 + (2 + grid + kinds + 1 + nck * per + 2) + (2 + 2 * nck * per + 3)

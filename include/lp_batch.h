@@ -114,10 +114,15 @@ LP_API lp_status lp_tune_schedule(int32_t m, int32_t n, int64_t nnz, const int64
 
 /*
  * Where each instance runs, fixed at lp_batch_create: where[k] (HOST int32[count]) is 0 for the
- * cooperative grid loop (nnz[k] > p->batch_local_nnz), 1 for a cluster of 8 blocks and 2 for a
- * single block (a small instance with at most two row tiles and two column tiles per warp of a
- * block).  Small instances of both kinds run in two kernels launched side by side, one launch
- * per kind present per solve stage.  Errors: LP_ERR_INVALID_ARG (NULL handle or where).
+ * cooperative grid loop (nnz[k] > p->batch_local_nnz).  The small instances (the others) run,
+ * with gamma = 1 and when every one of them fits it (no row or column longer than 128 entries,
+ * each CTA's slices and replicas of the gathered vectors within its shared memory), on the
+ * shared-memory cluster loop: 3, clusters of 4 (else 8, 16) blocks holding an instance in shared
+ * memory, each claiming instances until all are done.  Otherwise 1 for a cluster of 8 blocks and
+ * 2 for a single block (a small instance with at most two row tiles and two column tiles per
+ * warp of a block), in two kernels launched side by side.  The schedule solve of the
+ * differentiable layer (lp_diff.h) runs small instances on the loops of codes 1 and 2.
+ * Errors: LP_ERR_INVALID_ARG (NULL handle or where).
  */
 LP_API lp_status lp_batch_schedule(lp_batch_handle h, int32_t* where);
 

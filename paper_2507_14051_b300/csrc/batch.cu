@@ -1704,8 +1704,9 @@ lp_status lp_batch_schedule(lp_batch_handle hh, int32_t* where) {
   lp_batch* h = checked(hh);
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!where) return fail(LP_ERR_INVALID_ARG, "NULL output");
-  for (int32_t k = 0; k < h->count; ++k) where[k] = h->inst[k].local ? 1 : 0;
-  for (int32_t q = h->n_wide; q < h->n_local; ++q) where[h->local_host[q]] = 2;
+  for (int32_t k = 0; k < h->count; ++k) where[k] = h->inst[k].local ? (h->sm_ctas > 0 ? 3 : 1) : 0;
+  if (h->sm_ctas == 0)
+    for (int32_t q = h->n_wide; q < h->n_local; ++q) where[h->local_host[q]] = 2;
   return LP_OK;
 }
 

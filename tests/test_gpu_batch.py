@@ -249,17 +249,24 @@ def test_batch_with_per_instance_schedules_matches_oracle(cuda_device, local):
 
 
 def test_batch_schedule_classes(cuda_device):
-    """lp_batch_schedule: the grid loop for instances above batch_local_nnz, single CTAs for tiny
-    small instances (two row tiles and two column tiles at most per warp of a CTA), clusters for
-    the other small ones."""
+    """lp_batch_schedule: the grid loop for instances above batch_local_nnz; the small ones on the
+    shared-memory cluster loop when all of them fit it, else single CTAs for tiny small instances
+    (two row tiles and two column tiles at most per warp of a CTA) and clusters for the others."""
     lps = [gen.small_lp(0, m=30, n=50, density=0.2),        # 297 nonzeros, 1-2 tiles per side
            gen.small_lp(1, m=3000, n=3000, density=0.0005),  # 4,642 nonzeros, ~94 row tiles
            gen.small_lp(2, m=400, n=800, density=0.1)]       # 31,926 nonzeros
+    long_row = gen.ragged_rows(3, 80, 600)                  # a row of more than 128 entries
+    assert np.max(np.diff(long_row.row_ptr)) > 128
     with lpx.BatchSolver(lps) as b:
-        assert b.schedule().tolist() == [2, 1, 0]
+        assert b.schedule().tolist() == [3, 3, 0]
         b.solve(1e-6, 20000)
         assert np.all(b.summary()["status"] == oracle.OPTIMAL)
     with lpx.BatchSolver(lps, batch_local_nnz=0) as b:
         assert b.schedule().tolist() == [0, 0, 0]
     with lpx.BatchSolver(lps, batch_local_nnz=10 ** 9) as b:
-        assert b.schedule().tolist() == [2, 1, 1]
+        assert b.schedule().tolist() == [3, 3, 3]
+    with lpx.BatchSolver(lps + [long_row], batch_local_nnz=10 ** 9) as b:
+        where = b.schedule().tolist()
+        assert where[:3] == [2, 1, 1] and where[3] in (1, 2)
+        b.solve(1e-6, 20000)
+        assert np.all(b.summary()["status"] == oracle.OPTIMAL)

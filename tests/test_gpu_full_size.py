@@ -89,9 +89,10 @@ def test_full_size_batch_mixed_to_tolerance(cuda_device, batch512):
 
 
 def test_full_size_batch_sampled_instances(cuda_device, batch512):
-    """The 512-instance benchmark batch with the default schedule: after 30 iterations, a
-    single-CTA instance, a clustered one, a mid-size grid-loop one and the largest one equal the
-    oracle's 30 iterations (with the batch's own step sizes) element by element."""
+    """The 512-instance benchmark batch with the default schedule: after 30 iterations, the
+    smallest and the largest small instance (the shared-memory cluster loop), a mid-size
+    grid-loop one and the largest one equal the oracle's 30 iterations (with the batch's own step
+    sizes) element by element."""
     lps = batch512
     T = 30
     with lpx.BatchSolver(lps) as b:
@@ -100,7 +101,9 @@ def test_full_size_batch_sampled_instances(cuda_device, batch512):
         summ = b.summary()
         nnz = np.array([lp.nnz for lp in lps])
         grid = np.nonzero(where == 0)[0]
-        picks = [int(np.nonzero(where == 2)[0][0]), int(np.nonzero(where == 1)[0][0]),
+        small = np.nonzero(where != 0)[0]
+        assert np.all(where[small] == 3)
+        picks = [int(small[np.argmin(nnz[small])]), int(small[np.argmax(nnz[small])]),
                  int(grid[np.argsort(nnz[grid])[len(grid) // 2]]), int(np.argmax(nnz))]
         got = {k: b.get(k) for k in picks}
     assert np.all(summ["status"] == oracle.ITER_LIMIT) and np.all(summ["iters"] == T)
