@@ -85,8 +85,9 @@ typedef struct {
   int64_t trace_cap;       /* > 0: record (r_t, omega_t, restart_t, k_t) for t < trace_cap */
   int32_t unroll;          /* iterations per body of the device-side loop (1..64) */
   int32_t lane_target;     /* SpMV schedule: at most this many nonzeros per lane and task (1..64);
-                              0: automatic (8 for lp_solve; 32 for the batch, whose long rows
-                              then take fewer FP64 butterfly additions per row) */
+                              0: automatic (32: rows of up to 32 entries are read one lane per
+                              row, in sliced tiles, and longer rows take fewer FP64 butterfly
+                              additions) */
   int32_t persistent;      /* 1: one cooperative kernel runs `unroll` iterations per launch with
                               grid-wide barriers between phases; 2: the same loop as one
                               thread-block cluster of up to 16 CTAs (cluster barriers; for LPs

@@ -615,7 +615,9 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
       valT[pos] = valA[q];
     }
   std::vector<int4> chunksA, chunksT;
-  const int lt = h->prm.lane_target > 0 ? h->prm.lane_target : 8;  // automatic: 8
+  // automatic: 32 (rows of up to 32 entries one lane each, in sliced tiles): against 8, the
+  // multicommodity FP64 iteration 215 -> 211 us, FP32 143 -> 140 us, MIPLIB-shaped 28.9 -> 27.6 us
+  const int lt = h->prm.lane_target > 0 ? h->prm.lane_target : 32;
   int tr = h->prm.tile_rows;
   if (tr == 0) {
     // automatic: 32-row tiles (every row epilogue instruction runs in 32 lanes, where one-pass
