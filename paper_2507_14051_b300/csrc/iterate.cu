@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kThreads, 4)
   // of the test is computed by the last warp while the row totals are added, not by thread 0 on
   // the serial path at the start of each phase
   __shared__ int chk_cur, chk_nxt;
+  __shared__ RestartPre rpre;  // the restart test's thresholds, taken with the Halpern weights
   if (threadIdx.x == 0) {
     sc = *ra.ctl;
     chk_cur = is_check(sc, sc.t) ? 1 : 0;
@@ -195,14 +196,16 @@ __global__ void __launch_bounds__(kThreads, 4)
     store_block_partials(s, nr, part_rows);
     phase_sync();
     // the last warp is idle while warps 0..nr-1 add the totals: it computes the next Halpern
-    // weights (two FP64 divisions) so that the serial control does not
+    // weights (two FP64 divisions), whether t + 1 is a check iteration and the restart test's
+    // thresholds, so that the serial control does not
     if (threadIdx.x == kThreads - 32) {
       hw = halpern_weights(sc.k, sc.gamma);
       chk_nxt = is_check(sc, sc.t + 1) ? 1 : 0;
+      rpre = restart_pre(sc);
     }
     double tot[kNumSums];
     block_totals(part_rows, gridDim.x, nr, &ra.bins, tot);
-    if (threadIdx.x == 0) rs = row_decide(sc, tot, check, trace, &hw, kRefl ? 1.0 : 2.0);
+    if (threadIdx.x == 0) rs = row_decide(sc, tot, check, trace, &hw, kRefl ? 1.0 : 2.0, &rpre);
     __syncthreads();
     if (rs == 1) {  // the same decision in every block
       const V* __restrict__ xc = (sc.t & 1) ? ca.xh1 : ca.xh0;  // xhat of this iteration

@@ -193,6 +193,7 @@ __device__ __forceinline__ bool sm_run(cg::cluster_group& cl, unsigned char* sme
   __shared__ ColStepR<V> cstr;
   __shared__ Halpern hw;
   __shared__ int rs, chk_cur, chk_nxt;
+  __shared__ RestartPre rpre;
   const int tid = threadIdx.x;
   const int me = (int)cl.block_rank(), nctas = (int)cl.num_blocks();
   const int m = ra.m, n = ca.n;
@@ -318,10 +319,13 @@ __device__ __forceinline__ bool sm_run(cg::cluster_group& cl, unsigned char* sme
     __syncthreads();
     publish(cl, qy_r, yh_r, r0, mr, me, nctas);
     // the last warp computes, during the barrier, the Halpern weights that row_decide takes
-    // (two FP64 divisions)
-    sums(s, check ? 5 : 2, Gr, wr, detach, [&]() { hw = halpern_weights(sc.k, sc.gamma); });
+    // (two FP64 divisions) and the restart test's thresholds
+    sums(s, check ? 5 : 2, Gr, wr, detach, [&]() {
+      hw = halpern_weights(sc.k, sc.gamma);
+      rpre = restart_pre(sc);
+    });
     __syncthreads();
-    if (tid == 0) rs = row_decide(sc, s, check, trace, &hw, 1.0);
+    if (tid == 0) rs = row_decide(sc, s, check, trace, &hw, 1.0, &rpre);
     __syncthreads();
     if (rs == 1) {  // the same decision in every CTA
       const V* xc = (sc.t & 1) ? xh_r1 : xh_r0;  // xhat of this iteration

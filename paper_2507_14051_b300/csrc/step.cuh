@@ -24,6 +24,31 @@ __device__ __forceinline__ int restart_test(const Ctl& c, int64_t k, int64_t t, 
   return 0;
 }
 
+// What the restart test takes from the state before the totals are known, computed off the
+// control's serial path (by a warp that waits for the totals anyway): the thresholds
+// beta_s^2 r0^2 and beta_n^2 r0^2 (c.r0 holds r0^2), r_{t-1}^2, the artificial condition
+// k >= beta_a (t + 1), and whether restarts are allowed at t.  restart_test_pre with them
+// decides as restart_test does, bit for bit.
+struct RestartPre {
+  double thr_s, thr_n, r_prev;
+  int art, allow;
+};
+__device__ __forceinline__ RestartPre restart_pre(const Ctl& c) {
+  RestartPre p;
+  p.thr_s = (c.beta_s * c.beta_s) * c.r0;
+  p.thr_n = (c.beta_n * c.beta_n) * c.r0;
+  p.r_prev = c.r_prev;
+  p.art = (double)c.k >= c.beta_a * (double)(c.t + 1) ? 1 : 0;
+  p.allow = (c.restart_enabled && c.t + 1 < c.max_iter) ? 1 : 0;
+  return p;
+}
+__device__ __forceinline__ int restart_test_pre(const RestartPre& p, int64_t k, double r2) {
+  if (k < 1) return 0;
+  if (r2 <= p.thr_s) return 1;
+  if (r2 <= p.thr_n && r2 > p.r_prev) return 1;
+  return p.art;
+}
+
 // PID primal weight update, Section 3: e = log(sqrt(w)|dx| / (|dy|/sqrt(w))),
 // log w <- log w - (K_P e + K_I sum e + K_D (e - e_prev)); skipped when a norm is 0 or not
 // finite; log w kept in [-23, 23].
@@ -199,8 +224,10 @@ __device__ __forceinline__ Halpern halpern_weights(int64_t k, double gamma) {
 // `cross` scales the summed cross term tot[1]: 2 when it sums (y - yhat)(A x - A xhat) (the
 // plain epilogues), 1 when it sums (y - yhat)(A x - A xbar), which is twice that (the reflected
 // form, xbar = 2 xhat - x).
+// pre (or NULL): restart_pre(c) taken before this call, off the serial path.
 __device__ __forceinline__ int row_decide(Ctl& c, const double (&tot)[kNumSums], bool check, double* trace,
-                                          const Halpern* next = nullptr, double cross = 2.0) {
+                                          const Halpern* next = nullptr, double cross = 2.0,
+                                          const RestartPre* pre = nullptr) {
   const int64_t t = c.t;
   const double om = c.omega;
   const double r2raw = fma(c.w_over_eta, c.sxx, fma(c.inv_eta_w, tot[0], cross * tot[1]));
@@ -226,7 +253,8 @@ __device__ __forceinline__ int row_decide(Ctl& c, const double (&tot)[kNumSums],
     c.done = 1;
     return -1;
   }
-  const int rs = c.restart_enabled && (t + 1 < c.max_iter) ? restart_test(c, k, t, r2) : 0;
+  const int rs = pre ? (pre->allow ? restart_test_pre(*pre, k, r2) : 0)
+                     : (c.restart_enabled && (t + 1 < c.max_iter) ? restart_test(c, k, t, r2) : 0);
   if (rs) {
     c.k = 0;
     c.restarts += 1;
