@@ -256,7 +256,12 @@ __device__ __forceinline__ bool sm_run(cg::cluster_group& cl, unsigned char* sme
   copy_in(lv_s, ca.lv + c0, nc);
   copy_in(uv_s, ca.uv + c0, nc);
   copy_in(idc_s, ca.inv_dc + c0, nc);
-  if (tid == 0) chk_cur = is_check(sc, sc.t) ? 1 : 0;
+  // thread 0 prepares each phase's step scalars at the end of the control before it (so a phase
+  // starts without a serial step and a block barrier)
+  if (tid == 0) {
+    chk_cur = is_check(sc, sc.t) ? 1 : 0;
+    rstr = row_step_r<V>(sc, chk_cur);
+  }
   // the epilogues' argument blocks over shared memory (the LP's row / column indices)
   RowArgsT<V> rl = ra;
   rl.xh0 = xh_r0;
@@ -306,8 +311,6 @@ __device__ __forceinline__ bool sm_run(cg::cluster_group& cl, unsigned char* sme
   for (int32_t it = 0; it < iters && !sc.done; ++it) {
     // ---- row phase (rows r0 .. r0 + mr)
     double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (tid == 0) rstr = row_step_r<V>(sc, chk_cur);
-    __syncthreads();
     const RowStepR<V> st = rstr;
     const int check = st.check;
     if (check) {  // A xhat_t for the primal residual of the KKT test (read by the same lane)
@@ -325,7 +328,10 @@ __device__ __forceinline__ bool sm_run(cg::cluster_group& cl, unsigned char* sme
       rpre = restart_pre(sc);
     });
     __syncthreads();
-    if (tid == 0) rs = row_decide(sc, s, check, trace, &hw, 1.0, &rpre);
+    if (tid == 0) {
+      rs = row_decide(sc, s, check, trace, &hw, 1.0, &rpre);
+      if (rs != 1) cstr = col_step_r(sc, cl_, chk_cur);
+    }
     __syncthreads();
     if (rs == 1) {  // the same decision in every CTA
       const V* xc = (sc.t & 1) ? xh_r1 : xh_r0;  // xhat of this iteration
@@ -341,7 +347,10 @@ __device__ __forceinline__ bool sm_run(cg::cluster_group& cl, unsigned char* sme
         }
         sums(q, 2, 1, kWarps, false, nothing);
       }
-      if (tid == 0) row_restart_weight(sc, q[0], q[1]);
+      if (tid == 0) {
+        row_restart_weight(sc, q[0], q[1]);
+        cstr = col_step_r(sc, cl_, chk_cur);  // with the new primal weight's tau
+      }
       // A xhat_t: the next row phase takes it as A x and as the new anchor's product
       sm_rows(rp_s, ci_s, val_s, xc, mr, Gr, [&](int li, V v) { axh_s[li] = v; });
       __syncthreads();
@@ -349,8 +358,6 @@ __device__ __forceinline__ bool sm_run(cg::cluster_group& cl, unsigned char* sme
     if (sc.done) break;
     // ---- column phase (columns c0 .. c0 + nc)
     double s2[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (tid == 0) cstr = col_step_r(sc, cl_, chk_cur);
-    __syncthreads();
     const ColStepR<V> cs = cstr;
     const int ccheck = cs.check;
     if (ccheck && !cs.restart)  // A^T yhat_t for the dual residual of the KKT test
@@ -365,6 +372,7 @@ __device__ __forceinline__ bool sm_run(cg::cluster_group& cl, unsigned char* sme
     if (tid == 0) {
       col_control(sc, s2, ccheck);
       chk_cur = chk_nxt;
+      rstr = row_step_r<V>(sc, chk_cur);
     }
     __syncthreads();
   }
