@@ -144,9 +144,12 @@ __global__ void __launch_bounds__(kThreads, 4)
   // the serial path at the start of each phase
   __shared__ int chk_cur, chk_nxt;
   __shared__ RestartPre rpre;  // the restart test's thresholds, taken with the Halpern weights
+  // reflected form: thread 0 prepares each phase's step scalars at the end of the control
+  // before it (a phase then starts without a serial step and a block barrier)
   if (threadIdx.x == 0) {
     sc = *ra.ctl;
     chk_cur = is_check(sc, sc.t) ? 1 : 0;
+    if constexpr (kRefl) rstr = row_step_r<V>(sc, chk_cur);
   }
   __syncthreads();
   const LoadPolicy pol = make_policy();
@@ -156,8 +159,6 @@ __global__ void __launch_bounds__(kThreads, 4)
     double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
     int check;
     if constexpr (kRefl) {
-      if (threadIdx.x == 0) rstr = row_step_r<V>(sc, chk_cur);
-      __syncthreads();
       const RowStepR<V> st = rstr;
       check = st.check;
       if (check) {  // A xhat_t for the primal residual of the KKT test
@@ -205,7 +206,11 @@ __global__ void __launch_bounds__(kThreads, 4)
     }
     double tot[kNumSums];
     block_totals(part_rows, gridDim.x, nr, &ra.bins, tot);
-    if (threadIdx.x == 0) rs = row_decide(sc, tot, check, trace, &hw, kRefl ? 1.0 : 2.0, &rpre);
+    if (threadIdx.x == 0) {
+      rs = row_decide(sc, tot, check, trace, &hw, kRefl ? 1.0 : 2.0, &rpre);
+      if constexpr (kRefl)
+        if (rs != 1) cstr = col_step_r(sc, ca, chk_cur);
+    }
     __syncthreads();
     if (rs == 1) {  // the same decision in every block
       const V* __restrict__ xc = (sc.t & 1) ? ca.xh1 : ca.xh0;  // xhat of this iteration
@@ -224,7 +229,10 @@ __global__ void __launch_bounds__(kThreads, 4)
         phase_sync();
         block_totals(part_pid, gridDim.x, 2, nullptr, q);
       }
-      if (threadIdx.x == 0) row_restart_weight(sc, q[0], q[1]);
+      if (threadIdx.x == 0) {
+        row_restart_weight(sc, q[0], q[1]);
+        if constexpr (kRefl) cstr = col_step_r(sc, ca, chk_cur);  // with the new tau
+      }
       if constexpr (kRefl) {
         // A xhat_t, which the next row phase takes as A x and as the new anchor's product (read
         // there after the column phase's barrier)
@@ -238,8 +246,6 @@ __global__ void __launch_bounds__(kThreads, 4)
     // ---- column phase
     double s2[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if constexpr (kRefl) {
-      if (threadIdx.x == 0) cstr = col_step_r(sc, ca, chk_cur);
-      __syncthreads();
       const ColStepR<V> cs = cstr;
       check = cs.check;
       if (check && !cs.restart) {  // A^T yhat_t for the dual residual of the KKT test
@@ -281,6 +287,7 @@ __global__ void __launch_bounds__(kThreads, 4)
     if (threadIdx.x == 0) {
       col_control(sc, tot2, check);
       chk_cur = chk_nxt;
+      if constexpr (kRefl) rstr = row_step_r<V>(sc, chk_cur);
     }
     __syncthreads();
   }
