@@ -223,8 +223,8 @@ LP_API const char* lp_last_error(void);
  * lp_solve).
  *   persistent = 0: ms_out[0] / ms_out[1] mean duration of the row kernel (A x, dual step,
  *     restart control) and of the column kernel (A^T y, primal step, KKT test), ms_out[2] = 1;
- *   persistent = 1: ms_out[0] mean duration of one launch of the loop kernel, ms_out[1] = 0,
- *     ms_out[2] = iterations per launch (unroll).
+ *   a loop kernel (persistent 1, 2 or 3, or -1 choosing one): ms_out[0] mean duration of one
+ *     launch of the loop kernel, ms_out[1] = 0, ms_out[2] = iterations per launch (unroll).
  * ms_out[3] = launches timed.  Synchronous.  Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
  */
 LP_API lp_status lp_time_kernels(lp_handle h, int64_t iters, void* stream, double* ms_out);
