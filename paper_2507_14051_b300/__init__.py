@@ -437,7 +437,8 @@ class BatchSolver:
         return dict(status=st, kkt=kkt, iters=it, iters_fp32=it32, eta=eta)
 
     def schedule(self):
-        """Where each instance runs: 0 grid loop, 1 cluster of 8 blocks, 2 one block."""
+        """Where each instance runs: 0 grid loop, 1 cluster of 8 blocks, 2 one block, 3 the
+        shared-memory cluster loop (include/lp_batch.h, lp_batch_schedule)."""
         where = np.zeros(self.count, np.int32)
         _check(load().lp_batch_schedule(self.h, where.ctypes.data), "lp_batch_schedule")
         return where

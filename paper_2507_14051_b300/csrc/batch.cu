@@ -1276,6 +1276,9 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
     if (sn > 0) CK(cudaMemcpy(h->dc, ones.data(), sizeof(double) * sn, cudaMemcpyHostToDevice));
     if (sm > 0) CK(cudaMemcpy(h->dr, ones.data(), sizeof(double) * sm, cudaMemcpyHostToDevice));
   }
+  // a copy from pageable memory returns once its source is staged, possibly before its last
+  // transfer lands, and the setup stream does not wait on the default stream: wait here
+  CK(cudaDeviceSynchronize());
   const int passes = h->prm.ruiz_iters + (h->prm.pc_enabled ? 1 : 0);
   if (passes > 0 && snz > 0) {
     double* fr = h->y;
@@ -1312,13 +1315,13 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
   if (st != LP_OK) return st;
 
   // ---- step sizes ----
+  CK(cudaStreamSynchronize(s));  // the scaled data below is read back by the host
   h->eta.assign(K, 0.0);
   if (eta) {
     for (int32_t k = 0; k < K; ++k) h->eta[k] = eta[k];
   } else if (h->prm.eta > 0.0) {
     for (int32_t k = 0; k < K; ++k) h->eta[k] = h->prm.eta;
   } else {
-    CK(cudaStreamSynchronize(s));
     st = batch_power_iteration(h);
     if (st != LP_OK) return st;
   }
@@ -1386,7 +1389,7 @@ lp_status batch_create_impl(lp_batch* h, const int32_t* m, const int32_t* n, con
       k_to_float<<<gV, 256, 0, s>>>(sm, pr.first, pr.second);
     CK(cudaGetLastError());
   }
-  CK(cudaStreamSynchronize(s));
+  CK(cudaDeviceSynchronize());  // the setup stream's work and the state templates' copy
 
   st = build_batch_graph<double>(h, &h->graph64, &h->exec64);
   if (st != LP_OK) return st;

@@ -465,7 +465,7 @@ lp_status diff_buffers(lp_batch* h) {
     CK(h->alloc(&h->d_eta, h->count));
     CK(cudaMemcpy(h->d_eta, h->eta.data(), sizeof(double) * h->count, cudaMemcpyHostToDevice));
   }
-  CK(cudaStreamSynchronize(h->setup_stream));
+  CK(cudaDeviceSynchronize());  // the setup stream's kernel and the step sizes' copy
   return LP_OK;
 }
 

@@ -763,6 +763,9 @@ lp_status create_impl(lp_solver* h, int32_t m, int32_t n, int64_t nnz, const int
   }
   if (m > 0) CK(cudaMemcpy(h->d_row_perm, h->row_perm.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
   if (n > 0) CK(cudaMemcpy(h->d_col_perm, h->col_perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  // a copy from pageable memory returns once its source is staged, possibly before its last
+  // transfer lands, and the setup stream does not wait on the default stream: wait here
+  CK(cudaDeviceSynchronize());
 
   // ---- diagonal preconditioning (device) ----
   cudaStream_t s = h->setup_stream;
