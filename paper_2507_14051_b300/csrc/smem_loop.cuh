@@ -78,6 +78,21 @@ __device__ __forceinline__ void sm_rows(const int32_t* rp, const int32_t* ci, co
   }
 }
 
+// One pass of sm_rows without the epilogue (cnt * G <= the calling warps' threads; the calling
+// warps are whole and the first ones of the block): the value of row li = threadIdx.x / G, in
+// the same order as sm_rows, ends in every lane of the row's group.
+template <class V>
+__device__ __forceinline__ V sm_dot(const int32_t* rp, const int32_t* ci, const V* val, const V* xg, int cnt, int G) {
+  const int li = (int)threadIdx.x / G, sub = (int)threadIdx.x - li * G;
+  V acc = V(0);
+  if (li < cnt) {
+    const int e = rp[li + 1];
+    for (int k = rp[li] + sub; k < e; k += G) acc = fmav(val[k], xg[ci[k]], acc);
+  }
+  for (int off = G >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+  return acc;
+}
+
 template <class T>
 __device__ __forceinline__ void copy_in(T* dst, const T* __restrict__ src, int len) {
   for (int k = threadIdx.x; k < len; k += kThreads) dst[k] = src[k];
@@ -119,7 +134,10 @@ __device__ __forceinline__ void sync_but_last() { asm volatile("bar.sync 1, %0;"
 // With `detach` (the last warp holds no sums) that thread runs it between its arrival at the
 // cluster barrier and its wait, off everyone's path; otherwise before the sums.  The whole
 // cluster must call it, each CTA with its own table buffer in the same alternation.
-template <int NS, class Side>
+// kLast: the last warp adds the table instead of warp 0 and the totals end in thread
+// kThreads - 32's v[]; the other warps return right after the cluster barrier (free to work
+// while the last warp adds and runs the control).
+template <int NS, bool kLast = false, class Side>
 __device__ __forceinline__ void cluster_sums(cg::cluster_group& cl, double (&v)[kNumSums], int G, int warps,
                                              bool detach, double* tab, int me, int nctas, Side&& side) {
   __shared__ double wsum[kWarps][kNumSums];
@@ -158,7 +176,7 @@ __device__ __forceinline__ void cluster_sums(cg::cluster_group& cl, double (&v)[
   cluster_arrive();
   if (detach && last && lane == 0) side();
   cluster_wait();
-  if (threadIdx.x < 32) {
+  if (kLast ? last : threadIdx.x < 32) {
     int width = 1;
     while (width < nctas) width <<= 1;
     double t[NS];
@@ -308,7 +326,105 @@ __device__ __forceinline__ bool sm_run(cg::cluster_group& cl, unsigned char* sme
     ++red;
   };
   auto nothing = []() {};
-  for (int32_t it = 0; it < iters && !sc.done; ++it) {
+  // the same reductions with the table added by the last warp (totals in thread ctl's v[])
+  auto sums_last = [&](double (&v)[kNumSums], int nsums, int G, int warps, auto&& side) {
+    double* tab = part + (red & 1) * (kSmMaxCtas * kNumSums);
+    if (nsums == 1) cluster_sums<1, true>(cl, v, G, warps, true, tab, me, nctas, side);
+    else if (nsums == 2) cluster_sums<2, true>(cl, v, G, warps, true, tab, me, nctas, side);
+    else cluster_sums<kNumSums, true>(cl, v, G, warps, true, tab, me, nctas, side);
+    ++red;
+  };
+  if (detach) {
+    // Overlapped form (every row and column slice fits one SpMV pass in the first kWarps - 1
+    // warps): after each phase's cluster barrier, the last warp adds the table and its first
+    // thread runs the control while the other warps already take the next phase's dot
+    // products (they read only replicas the barrier published; a column phase that turns out
+    // to restart recomputes its dot products from yhat).  Same operations, same order, same
+    // bits as the loop below.
+    const int ctl = kThreads - 32;
+    const bool work = tid < ctl;
+    const int lr = tid / Gr, lc = tid / Gc;
+    const bool row_first = work && lr < mr && tid - lr * Gr == 0;
+    const bool col_first = work && lc < nc && tid - lc * Gc == 0;
+    V rv = V(0), rax = V(0);
+    if (work) {
+      rv = sm_dot(rp_s, ci_s, val_s, (const V*)xbar_r, mr, Gr);
+      if (rstr.check) rax = sm_dot(rp_s, ci_s, val_s, (const V*)((sc.t & 1) ? xh_r1 : xh_r0), mr, Gr);
+    }
+    for (int32_t it = 0; it < iters && !sc.done; ++it) {
+      // ---- row phase: epilogues from the dot products taken during the last control
+      double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      const RowStepR<V> st = rstr;
+      const int check = st.check;
+      if (row_first) {
+        if (check) ax_s[lr] = rax;
+        row_epilogue_r(rl, st, r0 + lr, rv, s);
+      }
+      __syncthreads();
+      publish(cl, qy_r, yh_r, r0, mr, me, nctas);
+      // during the barrier: the Halpern weights, the restart test's thresholds and whether
+      // t + 1 is a check iteration
+      sums_last(s, check ? 5 : 2, Gr, wr, [&]() {
+        hw = halpern_weights(sc.k, sc.gamma);
+        rpre = restart_pre(sc);
+        chk_nxt = is_check(sc, sc.t + 1) ? 1 : 0;
+      });
+      const int ccheck = chk_cur;
+      V cv = V(0), caty = V(0);
+      if (work) {  // the column phase's dot products, assuming no restart
+        cv = sm_dot(rpT_s, ciT_s, valT_s, (const V*)qy_r, nc, Gc);
+        if (ccheck) caty = sm_dot(rpT_s, ciT_s, valT_s, (const V*)yh_r, nc, Gc);
+      } else if (tid == ctl) {
+        rs = row_decide(sc, s, check, trace, &hw, 1.0, &rpre);
+        if (rs != 1) cstr = col_step_r(sc, cl_, chk_cur);
+      }
+      __syncthreads();
+      if (rs == 1) {  // the same decision in every CTA
+        const V* xc = (sc.t & 1) ? xh_r1 : xh_r0;  // xhat of this iteration
+        double q[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        if (sc.pid_enabled) {
+          for (int lj = tid; lj < nc; lj += kThreads) {
+            const V d = xc[c0 + lj] - x0_s[lj];
+            acc_fma(q[0], d, d);
+          }
+          for (int li = tid; li < mr; li += kThreads) {
+            const V d = yh_r[r0 + li] - y0_s[li];
+            acc_fma(q[1], d, d);
+          }
+          sums(q, 2, 1, kWarps, false, nothing);
+        }
+        if (tid == 0) {
+          row_restart_weight(sc, q[0], q[1]);
+          cstr = col_step_r(sc, cl_, chk_cur);  // with the new primal weight's tau
+        }
+        // A xhat_t: the next row phase takes it as A x and as the new anchor's product
+        sm_rows(rp_s, ci_s, val_s, xc, mr, Gr, [&](int li, V v) { axh_s[li] = v; });
+        if (work) cv = sm_dot(rpT_s, ciT_s, valT_s, (const V*)yh_r, nc, Gc);  // a restart gathers yhat
+        __syncthreads();
+      }
+      if (sc.done) break;
+      // ---- column phase
+      double s2[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      const ColStepR<V> cs = cstr;
+      if (col_first) {
+        if (cs.check && !cs.restart) aty_s[lc] = caty;
+        col_epilogue_r(cl_, cs, c0 + lc, cv, s2);
+      }
+      __syncthreads();
+      publish(cl, xbar_r, cs.xn, c0, nc, me, nctas);
+      sums_last(s2, cs.check ? 5 : 1, Gc, wc, nothing);
+      if (work) {  // the next row phase's dot products
+        rv = sm_dot(rp_s, ci_s, val_s, (const V*)xbar_r, mr, Gr);
+        if (chk_nxt) rax = sm_dot(rp_s, ci_s, val_s, (const V*)cs.xn, mr, Gr);
+      } else if (tid == ctl) {
+        col_control(sc, s2, cs.check);
+        chk_cur = chk_nxt;
+        rstr = row_step_r<V>(sc, chk_cur);
+      }
+      __syncthreads();
+    }
+  }
+  for (int32_t it = 0; !detach && it < iters && !sc.done; ++it) {
     // ---- row phase (rows r0 .. r0 + mr)
     double s[kNumSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
     const RowStepR<V> st = rstr;
