@@ -359,11 +359,11 @@ def test_shared_memory_loop_deterministic_and_reusable(cuda_device, seed):
     compare_fixed(lp, 300, persistent=3, unroll=7)
 
 
-@pytest.mark.parametrize("shape", [(200, 500, 0.02), (4000, 4000, 0.001)])
+@pytest.mark.parametrize("shape", [(200, 500, 0.02), (1000, 2000, 0.01), (4000, 4000, 0.001)])
 def test_shared_memory_loop_both_orders(cuda_device, shape):
     """The shared-memory cluster loop runs its overlapped order (each CTA's rows and columns in
-    one SpMV pass of seven warps: the 200 x 500 LP) and its plain order (250 rows per CTA: the
-    4000 x 4000 LP); both match the oracle element by element."""
+    one SpMV pass of seven warps: the 200 x 500 and 1000 x 2000 LPs) and its plain order (250
+    rows per CTA: the 4000 x 4000 LP); all match the oracle element by element."""
     m, n, dens = shape
     lp = gen.small_lp(7, m, n, dens)
     with lpx.Solver(lp, persistent=3) as s:
